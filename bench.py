@@ -1,0 +1,305 @@
+"""Benchmark: exact DBSCAN throughput on one GB300 (or N replicas).
+
+Default workload: seed-spreader d=3, n=10,000,000, eps=500 (eps2=250000),
+MinPts=20, int32 coordinates in [0, 1e5)^3, seeded, synthetic.  One step is
+one full exact-DBSCAN run (every stage of the hot path) on device-resident
+points, through the C ABI.  L2 is flushed (a 256 MB device write) before every
+timed step, outside the timed events.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+(the paper's grid method in plain C, all host cores) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpts/s exact DBSCAN d=3 n=10M; batched vs looped inst/s; serve p99"
+WORKLOADS = {
+    "ss3d_10m": "seed-spreader d=3 n=10,000,000 eps=500 MinPts=20 (+0.01% uniform noise)",
+    "ss3d_2m": "seed-spreader d=3 n=2,000,000 eps=500 MinPts=20 (+0.01% uniform noise)",
+    "skew5d_10m": "skewed mix d=5 n=10,000,000 eps=1000 MinPts=100 (50% in one eps-ball + 20 blobs)",
+    "tiny": "blobs d=2 n=20,000 eps=800 MinPts=10 (10 blobs sigma=1500 + 5% noise)",
+}
+L2_FLUSH_BYTES = 256 << 20
+# Algorithmic bytes per point of one radix-sort pass: read key (8) + value (4),
+# write key (8) + value (4).
+SORT_PASS_BYTES_PER_PT = 24
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model or os.uname().machine
+
+
+def time_oracle(workload: str, seed: int, n_sample: int | None):
+    """One oracle run on a bounded sample of the workload; returns (s, n, threads)."""
+    import oracle
+    from paper_2210_07580_gb300 import synth
+    X, eps2, minpts = synth.workload(workload, seed=seed, n=n_sample)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.grid(X, eps2, minpts)
+    return time.perf_counter() - t0, len(X), oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    ns = args.cpu_sample
+    times, n, thr = [], 0, 1
+    for i in range(args.warmup + args.steps):
+        t, n, thr = time_oracle(args.workload, 1, ns)
+        if i >= args.warmup:
+            times.append(t)
+    s_per_step = sum(times) / len(times)
+    value = n / s_per_step / 1e6
+    sample = f"{WORKLOADS[args.workload]}" + (f", first {n} points of the walk" if ns else ", full size")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(s_per_step * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": n},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpts/s", "cores": thr, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_info()},
+        "e2e": {"value": round(value, 3), "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2210_07580_gb300 import Context, synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # each rank clusters its own independent instance (replicas, weak scaling)
+    X, eps2, minpts = synth.workload(args.workload, seed=1 + rank)
+    n, d = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    core = torch.empty(n, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    sampler = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_acc = {}
+    launches = 0
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k + 2)  # L2 flush, outside the timed events
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        for name, ms in ctx.stage_times().items():
+            stage_acc[name] = stage_acc.get(name, 0.0) + ms
+        launches += ctx.last_sizes()["launches"]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    sizes = ctx.last_sizes()
+    stages = {k: round(v / args.steps, 4) for k, v in stage_acc.items()}
+    ctx.set_timing(False)
+
+    # end to end through the host-buffer entry point: pinned X in, labels and
+    # core flags out, every step
+    Xh = torch.from_numpy(X).pin_memory()
+    Lh = torch.empty(n, dtype=torch.int32).pin_memory()
+    Ch = torch.empty(n, dtype=torch.uint8).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    ctx.dbscan_host(Xh, eps2, minpts, labels=Lh, is_core=Ch, stream=stream)
+    torch.cuda.synchronize()
+    e_ms = []
+    for k in range(e2e_steps):
+        flush.fill_(k + 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.dbscan_host(Xh, eps2, minpts, labels=Lh, is_core=Ch, stream=stream)
+        e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = sum(e_ms) / len(e_ms)
+    e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e_t.item())
+
+    if rank == 0:
+        total_pts = n * ws
+        value = total_pts / (ms_max / 1e3) / 1e6
+        peak, peak_kind = peaks()
+        # dominant kernel family: the radix sort (hist + scatter per pass);
+        # algorithmic bytes of its scatter passes over the stage time
+        passes = -(-sizes["key_bits"] // 8)
+        sort_ms = stages.get("sort", 0.0)
+        sort_bytes = passes * SORT_PASS_BYTES_PER_PT * n
+        achieved = sort_bytes / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else None
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": n, "d": d, "eps2": eps2, "minpts": minpts,
+                       "grids": sizes["grids"], "neighbour_entries": sizes["nnbr"], "key_bits": sizes["key_bits"],
+                       "l2": "flushed before every timed step (256 MB write, outside the timed events)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "clocks": clocks,
+            "e2e": {"value": round(total_pts / (e2e_ms / 1e3) / 1e6, 3), "unit": "Mpts/s",
+                    "ms_per_step": round(e2e_ms, 3), "h2d_bytes_per_step": int(X.nbytes),
+                    "d2h_bytes_per_step": int(n * 4 + n)},
+            "gpu_launches": int(launches),
+            "stages_ms": stages,
+            "roofline": {"bound": "hbm", "kernel": "radix sort (hist + scatter, all passes)",
+                         "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                         "algorithmic_bytes": int(sort_bytes)},
+            "wall_s_timed": round(t_wall, 3),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            t, ns, thr = time_oracle(args.workload, 1, args.cpu_sample)
+            line["cpu_baseline"] = {"value": round(ns / t / 1e6, 3), "unit": "Mpts/s", "cores": thr,
+                                    "kind": "oracle", "cpu": cpu_info(),
+                                    "sample": f"{WORKLOADS[args.workload]}, "
+                                              + (f"first {ns} points of the walk" if args.cpu_sample else "full size")
+                                              + f", one run, {t:.1f} s"}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gdbscan", "reference"], default="gdbscan")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ss3d_10m")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="points of the workload the CPU oracle times (default: all)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

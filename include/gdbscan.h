@@ -1,0 +1,131 @@
+/*
+ * gdbscan -- exact Euclidean DBSCAN on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library libgdbscan.so.  The method is GriT-DBSCAN
+ * (Huang, Ma, Liu, Liu: "GriT-DBSCAN: A Spatial Clustering Algorithm for Very
+ * Large Databases", arXiv 2210.07580): integer grid (Eq. 1, Alg. 1), grid-tree
+ * neighbour query (Alg. 2-3), core identification as in G13 (Section 3.2),
+ * core-grid merging decided by MinDist <= eps (Def. 6-7; Alg. 4-5) joined by
+ * union-find (the LDF variant, Section 5.2) and border assignment (Alg. 6).
+ *
+ * Result definition (Section 3.1, Defs. 1-5), computed exactly:
+ *   - N_eps(p) = { q : dist(p,q) <= eps }, p included; p is core iff
+ *     |N_eps(p)| >= minpts.
+ *   - Clusters are the connected components of the core points under
+ *     dist <= eps.  A cluster's id is the smallest input index among its
+ *     core points.
+ *   - A non-core point within eps of a core point is a border point and takes
+ *     the smallest id among the clusters of those core points; any other
+ *     point is noise, label -1.
+ *
+ * Arithmetic: coordinates are int32; every comparison is the exact int64
+ * squared distance against eps2.  For a real radius eps pass
+ * eps2 = floor(eps^2): for integer points dist <= eps <=> dist2 <= eps2.
+ *
+ * Layout: points are row-major int32 [n][d] (point i at X[i*d .. i*d+d-1]).
+ * labels is int32 [n], is_core is uint8 [n] (0/1), both in input order.
+ *
+ * Ownership: the caller owns X, labels and is_core.  A gd_ctx owns its device
+ * workspace (grown on demand with cudaMalloc and kept for reuse), a small
+ * pinned host staging area and timing events; gd_destroy frees them.  A
+ * context is not thread-safe: use one per host thread.
+ *
+ * Errors: every entry point returns a gd_status; no exception or abort crosses
+ * the ABI.  On an error other than GD_OK the outputs are unspecified and
+ * gd_last_error() describes the failure.
+ */
+#ifndef GDBSCAN_H
+#define GDBSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gd_ctx gd_ctx;
+
+/* A CUDA stream handle (cudaStream_t); NULL means the legacy default stream. */
+typedef void *gd_stream_t;
+
+typedef enum {
+    GD_OK = 0,
+    GD_EINVAL = 1,   /* bad argument: d outside [1,8], n < 0 or n >= 2^31,
+                        eps2 < 0, minpts < 1, NULL pointer with n > 0 */
+    GD_ERANGE = 2,   /* d * (max_j (max x_j - min x_j))^2 >= 2^62, or the
+                        packed grid key would need more than 128 bits */
+    GD_ENOMEM = 3,   /* device or pinned host allocation failed */
+    GD_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed */
+    GD_ETIMEOUT = 5, /* a bounded device-side retry loop hit its limit */
+    GD_EBUSY = 6     /* reserved */
+} gd_status;
+
+/* Create a context on CUDA device `device` (made current by the call).
+ * *out receives the context, or NULL on failure. */
+gd_status gd_create(gd_ctx **out, int device);
+
+/* Free the context and everything it owns.  NULL is ignored. */
+void gd_destroy(gd_ctx *ctx);
+
+/* Upper bound, in bytes, of the device workspace gd_dbscan needs for n points
+ * in d dimensions before neighbour lists (which depend on the data: the
+ * context grows them on demand).  Used for admission control. */
+size_t gd_workspace_bytes(int64_t n, int d);
+
+/* Exact DBSCAN of the device-resident points X (Section 4.4, Alg. 6).
+ * X, labels and is_core are device pointers (is_core may be NULL).  Work is
+ * issued on `stream`; the call returns after the result is complete on that
+ * stream (it synchronises with it to size data-dependent buffers).  n == 0 is
+ * a no-op returning GD_OK. */
+gd_status gd_dbscan(gd_ctx *ctx, const int32_t *X, int64_t n, int d, int64_t eps2,
+                    int32_t minpts, int32_t *labels, uint8_t *is_core, gd_stream_t stream);
+
+/* As gd_dbscan, with X, labels and is_core in HOST memory (pinned memory
+ * makes the copies asynchronous and fast).  The call copies X to the device,
+ * clusters, and copies the results back before returning. */
+gd_status gd_dbscan_host(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, int64_t eps2,
+                         int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
+                         gd_stream_t stream);
+
+/* Static text for a status code. */
+const char *gd_status_str(gd_status s);
+
+/* Text of the last error seen by this context ("" if none). */
+const char *gd_last_error(const gd_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Introspection of the last gd_dbscan call on a context (tests, tuning).
+ * The arrays stay valid until the next call on the context.
+ * ------------------------------------------------------------------- */
+
+typedef enum {
+    GD_VIEW_PERM = 0,        /* int32 [n]: input index of the k-th point in grid order */
+    GD_VIEW_CELL_START = 1,  /* int32 [C+1]: first grid-order point of each grid */
+    GD_VIEW_CELL_COORD = 2,  /* int32 [C][d]: grid identifiers (Eq. 1, relative to the minimum) */
+    GD_VIEW_NBR_START = 3,   /* int32 [C+1]: CSR offsets of Nei(g) */
+    GD_VIEW_NBR = 4,         /* int32 [nnbr]: neighbour grid indices, g itself included */
+    GD_VIEW_CORE_SORTED = 5, /* uint8 [n]: core flags in grid order */
+    GD_VIEW_CELL_CID = 6     /* int32 [C]: cluster id of each grid's core points, -1 if none */
+} gd_view;
+
+/* Sizes of the last run: out[0]=n, out[1]=d, out[2]=C (non-empty grids),
+ * out[3]=nnbr (neighbour list length), out[4]=cell side s, out[5]=key bits,
+ * out[6]=kernel launches of the run, out[7]=candidate merge pairs.  Returns GD_EINVAL before any run. */
+gd_status gd_last_sizes(const gd_ctx *ctx, int64_t out[8]);
+
+/* Copy `bytes` bytes of an internal array of the last run into host memory
+ * (synchronous).  GD_EINVAL if bytes exceeds the array's size. */
+gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes);
+
+/* Per-stage device timing (CUDA events around each stage of gd_dbscan).
+ * Off by default; when on, gd_stage_times fills up to max entries of
+ * milliseconds and names for the last run and returns the count. */
+gd_status gd_set_timing(gd_ctx *ctx, int enable);
+int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDBSCAN_H */

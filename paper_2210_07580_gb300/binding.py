@@ -1,0 +1,194 @@
+"""ctypes binding of libgdbscan (include/gdbscan.h).
+
+Argument marshalling only: every step of the clustering runs in the CUDA
+library.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing or fails to load, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgdbscan.so")
+
+GD_OK, GD_EINVAL, GD_ERANGE, GD_ENOMEM, GD_ECUDA, GD_ETIMEOUT, GD_EBUSY = range(7)
+VIEW_PERM, VIEW_CELL_START, VIEW_CELL_COORD, VIEW_NBR_START, VIEW_NBR, VIEW_CORE_SORTED, VIEW_CELL_CID = range(7)
+
+
+class GdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gdbscan error {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libgdbscan.so (built by paper_2210_07580_gb300._build).  Raises if
+    it is absent: the clustering has no other implementation."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libgdbscan.so not found at {p}: build it first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        lib.gd_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        lib.gd_create.restype = ctypes.c_int
+        lib.gd_destroy.argtypes = [vp]
+        lib.gd_destroy.restype = None
+        lib.gd_workspace_bytes.argtypes = [i64, ctypes.c_int]
+        lib.gd_workspace_bytes.restype = ctypes.c_size_t
+        lib.gd_dbscan.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
+        lib.gd_dbscan.restype = ctypes.c_int
+        lib.gd_dbscan_host.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
+        lib.gd_dbscan_host.restype = ctypes.c_int
+        lib.gd_status_str.argtypes = [ctypes.c_int]
+        lib.gd_status_str.restype = ctypes.c_char_p
+        lib.gd_last_error.argtypes = [vp]
+        lib.gd_last_error.restype = ctypes.c_char_p
+        lib.gd_last_sizes.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.gd_last_sizes.restype = ctypes.c_int
+        lib.gd_copy_view.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
+        lib.gd_copy_view.restype = ctypes.c_int
+        lib.gd_set_timing.argtypes = [vp, ctypes.c_int]
+        lib.gd_set_timing.restype = ctypes.c_int
+        lib.gd_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.c_int]
+        lib.gd_stage_times.restype = ctypes.c_int
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def eps2_from_eps(eps) -> int:
+    """floor(eps^2) computed exactly: for integer points dist <= eps exactly
+    when dist^2 <= floor(eps^2).  Accepts int, float, Fraction or a decimal
+    string."""
+    f = Fraction(eps) if not isinstance(eps, float) else Fraction(eps)
+    if f < 0:
+        raise ValueError("eps must be >= 0")
+    sq = f * f
+    return sq.numerator // sq.denominator
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Context:
+    """One gd_ctx: a device workspace reused across calls.  Not thread-safe."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load_library()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        st = self._lib.gd_create(ctypes.byref(h), self.device)
+        if st != GD_OK:
+            raise GdError(st, self._lib.gd_status_str(st).decode())
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != GD_OK:
+            msg = self._lib.gd_last_error(self._h).decode() or self._lib.gd_status_str(st).decode()
+            raise GdError(st, msg)
+
+    # -- clustering
+    def dbscan(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
+        """Cluster the device tensor X (torch.int32, [n, d], contiguous, on this
+        context's device).  Returns (labels int32 [n], is_core bool [n]) as
+        device tensors (or fills the given ones; is_core must be uint8/bool)."""
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
+            raise TypeError("X must be a CUDA int32 tensor of shape [n, d]")
+        X = X.contiguous()
+        n, d = X.shape
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32, device=X.device)
+        if is_core is None:
+            is_core = torch.empty(n, dtype=torch.uint8, device=X.device)
+        st = self._lib.gd_dbscan(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
+                                 is_core.data_ptr(), _stream_handle(stream))
+        self._check(st)
+        return labels, is_core.view(torch.bool) if is_core.dtype == torch.uint8 else is_core
+
+    def dbscan_host(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
+        """Cluster host points (numpy or CPU torch int32 [n, d]; pinned memory
+        is fastest).  Copies in, clusters and copies the results out."""
+        import torch
+        if isinstance(X, np.ndarray):
+            X = torch.from_numpy(np.ascontiguousarray(X, dtype=np.int32))
+        if X.is_cuda or X.dtype != torch.int32 or X.dim() != 2:
+            raise TypeError("X must be a host int32 array of shape [n, d]")
+        X = X.contiguous()
+        n, d = X.shape
+        if labels is None:
+            labels = torch.empty(n, dtype=torch.int32)
+        if is_core is None:
+            is_core = torch.empty(n, dtype=torch.uint8)
+        st = self._lib.gd_dbscan_host(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
+                                      is_core.data_ptr(), _stream_handle(stream))
+        self._check(st)
+        return labels, is_core
+
+    # -- introspection
+    def last_sizes(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        self._check(self._lib.gd_last_sizes(self._h, out))
+        keys = ["n", "d", "grids", "nnbr", "side", "key_bits", "launches", "pairs"]
+        return {k: int(v) for k, v in zip(keys, out)}
+
+    def copy_view(self, which: int, dtype, count: int) -> np.ndarray:
+        a = np.empty(count, dtype=dtype)
+        self._check(self._lib.gd_copy_view(self._h, int(which), a.ctypes.data, a.nbytes))
+        return a
+
+    def set_timing(self, enable: bool):
+        self._check(self._lib.gd_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        ms = (ctypes.c_float * 32)()
+        names = (ctypes.c_char_p * 32)()
+        k = self._lib.gd_stage_times(self._h, ms, names, 32)
+        return {names[i].decode(): float(ms[i]) for i in range(k)}
+
+
+def workspace_bytes(n: int, d: int) -> int:
+    return int(load_library().gd_workspace_bytes(int(n), int(d)))
+
+
+_default: dict[int, Context] = {}
+
+
+def dbscan(X, eps2: int, minpts: int, stream=None):
+    """Exact DBSCAN of a CUDA int32 [n, d] tensor with a per-device default
+    context.  Returns (labels, is_core) device tensors."""
+    dev = X.device.index if X.device.index is not None else 0
+    ctx = _default.get(dev)
+    if ctx is None:
+        ctx = _default[dev] = Context(dev)
+    return ctx.dbscan(X, eps2, minpts, stream=stream)

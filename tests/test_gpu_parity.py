@@ -1,0 +1,208 @@
+"""CUDA path against the CPU oracle, through the C ABI (needs a GB300).
+
+Labels and core flags are integers decided by exact int64 comparisons, so the
+bar is bit-exactness: every label, every core flag, and the intermediate grid
+structure (sorted permutation, non-empty grids, neighbour lists) equal the
+oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2210_07580_gb300 import Context, GdError, binding, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, X, eps2, minpts):
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.int32)).cuda()
+    lab, core = ctx.dbscan(Xd, eps2, minpts)
+    torch.cuda.synchronize()
+    return lab.cpu().numpy(), core.cpu().numpy()
+
+
+def assert_same(got, want, what=""):
+    gl, gc = got
+    wl, wc = want
+    if not np.array_equal(gc, wc):
+        raise AssertionError(f"{what}: core flags differ at {int((gc != wc).sum())} points")
+    if not np.array_equal(gl, wl):
+        idx = np.flatnonzero(gl != wl)
+        raise AssertionError(f"{what}: labels differ at {len(idx)} points, first {idx[:5]}: "
+                             f"got {gl[idx[:5]]} want {wl[idx[:5]]}")
+
+
+def rand_points(rng, n, d, hi, lattice=1):
+    return np.ascontiguousarray((rng.integers(0, hi // lattice, size=(n, d)) * lattice).astype(np.int32))
+
+
+# ------------------------------------------------------------ small cases
+
+def test_tiny_workload_vs_bruteforce(ctx):
+    X, eps2, minpts = synth.workload("tiny")
+    assert_same(run_gpu(ctx, X, eps2, minpts), oracle.bruteforce(X, eps2, minpts), "tiny")
+
+
+@pytest.mark.parametrize("name", ["border_tie_2d.txt", "chain_dup_1d.txt"])
+def test_golden_fixtures(ctx, name):
+    from golden_io import load_labels_case
+    X, eps2, minpts, want_l, want_c = load_labels_case(name)
+    gl, gc = run_gpu(ctx, X, eps2, minpts)
+    np.testing.assert_array_equal(gc, want_c)
+    np.testing.assert_array_equal(gl, want_l)
+
+
+RANDOM_CASES = [
+    # d, n, hi, lattice, eps2, minpts
+    (1, 3000, 20000, 1, 400, 4),
+    (2, 5000, 4000, 10, 900, 5),
+    (2, 7000, 30000, 1, 250000, 12),
+    (3, 6000, 3000, 20, 6400, 6),
+    (3, 9000, 100000, 1, 250000, 20),
+    (4, 5000, 1000, 10, 4000, 5),
+    (5, 5000, 500, 10, 3000, 4),
+    (6, 4000, 200, 10, 900, 3),
+    (7, 4000, 120, 10, 700, 3),
+    (8, 3000, 90, 10, 500, 3),
+    (2, 2000, 60, 1, 0, 2),          # eps = 0: duplicates only
+    (3, 3000, 500, 1, 10**7, 50),    # huge eps: one cluster
+    (3, 3000, 100000, 1, 1, 2),      # eps below the spacing: all noise
+    (2, 4000, 2000, 1, 2500, 1),     # MinPts = 1: every point core
+    (3, 5000, 50000, 1, 90000, 200), # MinPts above most grid sizes
+]
+
+
+@pytest.mark.parametrize("d,n,hi,lattice,eps2,minpts", RANDOM_CASES)
+def test_random_cases_vs_oracle(ctx, d, n, hi, lattice, eps2, minpts):
+    rng = np.random.default_rng(7919 * d + n + minpts)
+    X = rand_points(rng, n, d, hi, lattice)
+    X[: n // 25] = X[n // 25: 2 * (n // 25)]  # exact duplicates
+    want = oracle.grid(X, eps2, minpts)
+    assert_same(run_gpu(ctx, X, eps2, minpts), want, f"d={d} n={n} eps2={eps2} M={minpts}")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 4095, 4096, 4097, 70001])
+def test_ragged_sizes(ctx, n):
+    """Sizes around the warp, sort-tile and scan-tile boundaries."""
+    rng = np.random.default_rng(n)
+    X = rand_points(rng, n, 3, 3000, 1)
+    want = oracle.grid(X, 40000, 4)
+    assert_same(run_gpu(ctx, X, 40000, 4), want, f"n={n}")
+
+
+def test_two_word_keys(ctx):
+    """d=7 with eps=200: identifiers need 77 bits, the 128-bit key path."""
+    rng = np.random.default_rng(5)
+    centres = rng.integers(0, 100000, size=(20, 7))
+    X = (centres[rng.integers(0, 20, 6000)] + rng.normal(0, 120, size=(6000, 7))).clip(0, 99999)
+    X = np.ascontiguousarray(np.vstack([X, rng.integers(0, 100000, size=(1, 7)) * 0 + 99999,
+                                        np.zeros((1, 7))]).astype(np.int32))
+    want = oracle.grid(X, 200 ** 2, 5)
+    assert_same(run_gpu(ctx, X, 200 ** 2, 5), want, "two-word keys")
+    assert ctx.last_sizes()["key_bits"] > 64
+
+
+def test_negative_and_offset_coordinates(ctx):
+    rng = np.random.default_rng(17)
+    X = rand_points(rng, 5000, 3, 20000, 1) - 10000 - 2**30
+    want = oracle.grid(X, 250000, 6)
+    assert_same(run_gpu(ctx, X, 250000, 6), want, "offset")
+
+
+# ------------------------------------------------- intermediate structure
+
+def test_grid_structure_matches_oracle(ctx):
+    """Sorted permutation (stable), non-empty grids and Nei(g) per grid."""
+    X, eps2, minpts = synth.workload("tiny", n=8000, seed=2)
+    run_gpu(ctx, X, eps2, minpts)
+    sz = ctx.last_sizes()
+    gs = oracle.grid_structure(X, eps2)
+    C = sz["grids"]
+    assert C == len(gs["cell_start"]) - 1
+    assert sz["side"] == oracle.cell_side(eps2, 2)
+    perm = ctx.copy_view(binding.VIEW_PERM, np.int32, len(X))
+    np.testing.assert_array_equal(perm, gs["order"])
+    np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_CELL_START, np.int32, C + 1), gs["cell_start"])
+    np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_CELL_COORD, np.int32, C * 2).reshape(C, 2),
+                                  gs["cell_coord"])
+    ns = ctx.copy_view(binding.VIEW_NBR_START, np.int32, C + 1)
+    np.testing.assert_array_equal(ns, gs["nei_start"])
+    nb = ctx.copy_view(binding.VIEW_NBR, np.int32, int(ns[-1]))
+    for c in range(C):
+        assert sorted(nb[ns[c]:ns[c + 1]]) == sorted(gs["nei"][gs["nei_start"][c]:gs["nei_start"][c + 1]])
+
+
+def test_worked_example_neighbours(ctx):
+    from golden_io import load_grid_case
+    case = load_grid_case("fig2_neighbors_2d.txt")
+    run_gpu(ctx, case["X"], case["eps2"], case["minpts"])
+    sz = ctx.last_sizes()
+    assert sz["grids"] == 9 and sz["side"] == 11
+    coord = ctx.copy_view(binding.VIEW_CELL_COORD, np.int32, 18).reshape(9, 2)
+    assert [tuple(c) for c in coord] == [case["grids"][k] for k in range(1, 10)]
+    ns = ctx.copy_view(binding.VIEW_NBR_START, np.int32, 10)
+    nb = ctx.copy_view(binding.VIEW_NBR, np.int32, int(ns[-1]))
+    q, want = case["query"]
+    assert sorted(int(v) + 1 for v in nb[ns[q - 1]:ns[q]]) == want
+
+
+# ------------------------------------------------------------ ABI paths
+
+def test_host_entry_point_matches_device(ctx):
+    X, eps2, minpts = synth.workload("tiny", n=12000, seed=4)
+    dev = run_gpu(ctx, X, eps2, minpts)
+    hl, hc = ctx.dbscan_host(torch.from_numpy(X).pin_memory(), eps2, minpts)
+    np.testing.assert_array_equal(hl.numpy(), dev[0])
+    np.testing.assert_array_equal(hc.numpy().astype(bool), dev[1])
+
+
+def test_errors_and_empty(ctx):
+    Xd = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    lab, core = ctx.dbscan(Xd, 10, 3)
+    assert lab.numel() == 0
+    with pytest.raises(GdError) as e:
+        ctx.dbscan(torch.zeros((5, 9), dtype=torch.int32, device="cuda"), 10, 3)
+    assert e.value.status == binding.GD_EINVAL
+    with pytest.raises(GdError) as e:
+        ctx.dbscan(torch.zeros((5, 2), dtype=torch.int32, device="cuda"), -1, 3)
+    assert e.value.status == binding.GD_EINVAL
+    big = torch.tensor([[-2**31], [2**31 - 1]], dtype=torch.int32, device="cuda")
+    with pytest.raises(GdError) as e:
+        ctx.dbscan(big, 10, 1)
+    assert e.value.status == binding.GD_ERANGE
+    wide = torch.from_numpy(np.array([[0] * 8, [99999] * 8], np.int32)).cuda()
+    with pytest.raises(GdError) as e:  # 8 x 17 identifier bits > 128
+        ctx.dbscan(wide, 0, 1)
+    assert e.value.status == binding.GD_ERANGE
+    # the context stays usable after errors
+    X, eps2, minpts = synth.workload("tiny", n=3000)
+    assert_same(run_gpu(ctx, X, eps2, minpts), oracle.grid(X, eps2, minpts), "after errors")
+
+
+def test_context_reuse_across_sizes(ctx):
+    for n, seed in [(50000, 1), (2000, 2), (120000, 3), (7000, 4)]:
+        X, eps2, minpts = synth.workload("tiny", n=n, seed=seed)
+        assert_same(run_gpu(ctx, X, eps2, minpts), oracle.grid(X, eps2, minpts), f"n={n}")
+
+
+# ------------------------------------------------ full-size workloads
+
+@pytest.mark.parametrize("name", ["ss3d_2m", "ss3d_10m", "skew5d_10m"])
+def test_full_size_workloads(ctx, name):
+    """The benchmark's workloads at full size, every label against the grid
+    oracle (which is itself pinned to brute force on small inputs)."""
+    X, eps2, minpts = synth.workload(name)
+    got = run_gpu(ctx, X, eps2, minpts)
+    want = oracle.grid(X, eps2, minpts)
+    assert_same(got, want, name)
