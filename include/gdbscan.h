@@ -124,6 +124,39 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
 gd_status gd_set_timing(gd_ctx *ctx, int enable);
 int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
 
+/* ---------------------------------------------------------------------
+ * Clustering without any device allocation (no counterpart in the paper).
+ *
+ * Some callers cannot call cudaMalloc when they need a clustering: a plugin
+ * inside an application whose memory manager owns the whole device pool, a
+ * real-time loop that forbids allocation (and the device-wide synchronisation
+ * cudaFree implies) on its hot path, or a process whose allocator is already
+ * exhausted.  gd_dbscan_noalloc serves them for small inputs.  It needs no
+ * gd_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or other
+ * allocating routine: every scratch buffer is carved from one file-scope
+ * device array of GD_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads
+ * this library holds until the process exits.  The caller still provides X,
+ * labels and is_core (device pointers, as for gd_dbscan), and the result is
+ * bit-identical to gd_dbscan's.
+ *
+ *   - n above GD_NOALLOC_MAX_POINTS, or data whose neighbour lists do not fit
+ *     in what the array has left, returns GD_ENOMEM (nothing is written);
+ *     malformed arguments return GD_EINVAL as for gd_dbscan.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address with cudaGetSymbolAddress; make that first call
+ *     before any stream capture on the device.
+ *   - All calls share the one array and it keeps the previous call's
+ *     contents; the pipeline clears whatever must start at zero.  Calls that
+ *     overlapped on the GPU would race on the array: this function takes a
+ *     process-wide lock and returns only after its work on `stream` has
+ *     finished, so calls made through it do not overlap.
+ * --------------------------------------------------------------------- */
+#define GD_NOALLOC_MAX_POINTS 65536
+#define GD_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+gd_status gd_dbscan_noalloc(const int32_t *X, int64_t n, int d, int64_t eps2, int32_t minpts,
+                            int32_t *labels, uint8_t *is_core, gd_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

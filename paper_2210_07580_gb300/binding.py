@@ -66,6 +66,8 @@ def load_library(path: str | None = None):
         lib.gd_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.c_int]
         lib.gd_stage_times.restype = ctypes.c_int
+        lib.gd_dbscan_noalloc.argtypes = [vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
+        lib.gd_dbscan_noalloc.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
@@ -175,6 +177,32 @@ class Context:
         names = (ctypes.c_char_p * 32)()
         k = self._lib.gd_stage_times(self._h, ms, names, 32)
         return {names[i].decode(): float(ms[i]) for i in range(k)}
+
+
+NOALLOC_MAX_POINTS = 65536
+
+
+def dbscan_noalloc(X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
+    """gd_dbscan_noalloc: cluster a CUDA int32 [n, d] tensor (n at most
+    NOALLOC_MAX_POINTS) with the library's fixed static scratch instead of any
+    device allocation.  The output tensors are allocated here by torch unless
+    given; the library call itself allocates nothing."""
+    import torch
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
+        raise TypeError("X must be a CUDA int32 tensor of shape [n, d]")
+    lib = load_library()
+    X = X.contiguous()
+    n, d = X.shape
+    if labels is None:
+        labels = torch.empty(n, dtype=torch.int32, device=X.device)
+    if is_core is None:
+        is_core = torch.empty(n, dtype=torch.uint8, device=X.device)
+    with torch.cuda.device(X.device):
+        st = lib.gd_dbscan_noalloc(X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
+                                   is_core.data_ptr(), _stream_handle(stream))
+    if st != GD_OK:
+        raise GdError(st, lib.gd_status_str(st).decode())
+    return labels, is_core
 
 
 def workspace_bytes(n: int, d: int) -> int:
