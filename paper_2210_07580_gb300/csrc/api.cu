@@ -22,7 +22,16 @@ const char* const kStageNames[kStages] = {"bounds", "quantise", "sort",  "compac
                                           "core",   "core_pack", "pairs", "merge",   "labels"};
 
 // Small device block: mnmx[16], then scalar counters.
-enum SmallSlot { kMnmx = 0, kNumCells = 16, kStatus = 17, kLevelCount = 24, kSmallInts = 64 };
+enum SmallSlot {
+    kMnmx = 0,        // [16] per-dimension min then max
+    kNumCells = 16,   // C
+    kStatus = 17,     // device status bits
+    kMaxCell = 18,    // largest grid
+    kLevelCount = 24, // [8] nodes per grid-tree level
+    kRange = 32,      // [4] merge wave ranges
+    kHardCnt = 36,    // [2] pairs handed to FastMerging per wave
+    kSmallInts = 64
+};
 
 struct Work {
     void* keyA;
@@ -41,6 +50,7 @@ struct Work {
     int* core_start;
     int* bbox;
     int* pair_start;
+    int* pair_start_f;
     int* parent;
     int* cid_root;
     int* cell_cid;
@@ -78,6 +88,7 @@ size_t carve(Work* w, char* base, int64_t n, int d, int key_words) {
     w->core_start = (int*)take((N + 1) * 4);
     w->bbox = (int*)take(N * 2 * d * 4);
     w->pair_start = (int*)take((N + 1) * 4);
+    w->pair_start_f = (int*)take((N + 1) * 4);
     w->parent = (int*)take(N * 4);
     w->cid_root = (int*)take(N * 4);
     w->cell_cid = (int*)take(N * 4);
@@ -120,7 +131,7 @@ struct DevBuf {
 
 struct gd_ctx {
     int device = 0;
-    DevBuf arena, nbr, pairs, io;
+    DevBuf arena, nbr, pairs, hard, mscratch, io;
     int* small = nullptr;       // device
     int* host_small = nullptr;  // pinned host mirror
     cudaEvent_t ev[kStages + 1] = {};
@@ -264,6 +275,7 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
                            ctx->small + kNumCells, st));
     GD_TRY(readback(ctx, ctx->small + kNumCells, 1, st));
     const int C = ctx->host_small[0];
+    GD_CUDA(launch_cell_max(w.cell_start, C, ctx->small + kMaxCell, st));
 
     // --- grid tree levels (Alg. 2) and Nei(g) (Alg. 3)
     mark(4);
@@ -286,34 +298,46 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
 
     // --- core points (G13 rule)
     mark(6);
-    GD_CUDA(launch_core(p, w.Xs, w.cell_start, w.pt_cell, C, w.nbr_start, nbr, w.core_s, st));
+    GD_CUDA(launch_core(p, w.Xs, w.cell_start, w.pt_cell, w.cell_coord, C, w.nbr_start, nbr, w.core_s, st));
 
     // --- core point sets s_i and their boxes
     mark(7);
-    GD_CUDA(launch_core_count(p, w.core_s, w.cell_start, C, w.core_start, st));
+    GD_CUDA(launch_core_count(p, w.core_s, w.cell_start, C, w.core_start, w.bbox, st));
     GD_CUDA(scan_exclusive(w.core_start, w.core_start, C, w.tmp, st));
-    GD_CUDA(launch_core_compact(p, w.Xs, w.core_s, w.cell_start, w.core_start, C, w.Xc, w.bbox, st));
+    GD_CUDA(launch_core_pack(p, w.Xs, w.core_s, w.pt_cell, w.cell_start, w.core_start, w.Xc, w.bbox, st));
 
-    // --- candidate pairs of neighbouring core grids (at most nnbr of them)
+    // --- candidate pairs of neighbouring core grids (at most nnbr of them):
+    //     touching grids first, then the others
     mark(8);
     GD_TRY(ensure(ctx, ctx->pairs, (size_t)nnbr * 8 + 16, st));
+    GD_TRY(ensure(ctx, ctx->hard, (size_t)nnbr * 8 + 16, st));
     int2* pairs = (int2*)ctx->pairs.ptr;
-    GD_CUDA(launch_pair_count(w.nbr_start, nbr, w.core_start, C, w.pair_start, st));
+    int2* hard = (int2*)ctx->hard.ptr;
+    GD_CUDA(launch_pair_count(p, w.nbr_start, nbr, w.core_start, w.cell_coord, C, w.pair_start, w.pair_start_f, st));
     GD_CUDA(scan_exclusive(w.pair_start, w.pair_start, C, w.tmp, st));
-    GD_CUDA(launch_pair_fill(w.nbr_start, nbr, w.core_start, C, w.pair_start, pairs, st));
+    GD_CUDA(scan_exclusive(w.pair_start_f, w.pair_start_f, C, w.tmp, st));
+    GD_CUDA(launch_pair_fill(p, w.nbr_start, nbr, w.core_start, w.cell_coord, C, w.pair_start, w.pair_start_f, pairs,
+                             st));
 
-    // --- merging (Def. 6-7) with union-find
+    // --- merging (Def. 6-7): two waves, each a warp-level test then
+    //     FastMerging (Alg. 5) on the pairs left undecided
     mark(9);
+    GD_TRY(readback(ctx, ctx->small + kMaxCell, 1, st));
+    const int wpb = (ctx->host_small[0] + 31) / 32 + 1;
+    GD_TRY(ensure(ctx, ctx->mscratch, (size_t)merge_fm_blocks() * 2 * wpb * 4, st));
     GD_CUDA(cudaMemsetAsync(ctx->small + kStatus, 0, sizeof(int), st));
     GD_CUDA(launch_uf_init(w.parent, C, st));
-    GD_CUDA(launch_merge(p, pairs, w.pair_start + C, (int)nnbr, w.Xc, w.core_start, w.bbox, w.parent,
-                         (unsigned*)(ctx->small + kStatus), st));
+    GD_CUDA(launch_merge_ranges(w.pair_start, w.pair_start_f, C, ctx->small + kRange, ctx->small + kHardCnt, st));
+    for (int wave = 0; wave < 2; ++wave)
+        GD_CUDA(launch_merge_wave(p, wave, pairs, ctx->small + kRange, (int)nnbr, w.Xc, w.core_start, w.bbox, w.parent,
+                                  (unsigned*)(ctx->small + kStatus), hard, ctx->small + kHardCnt,
+                                  (unsigned*)ctx->mscratch.ptr, wpb, st));
 
     // --- cluster ids, border points, labels
     mark(10);
     GD_CUDA(launch_cluster_ids(p, w.parent, w.core_start, w.cell_start, w.core_s, perm, C, w.cid_root, w.cell_cid,
                                st, (unsigned*)(ctx->small + kStatus)));
-    GD_CUDA(launch_labels(p, w.Xs, w.cell_start, w.pt_cell, w.core_s, w.nbr_start, nbr, w.core_start, w.Xc,
+    GD_CUDA(launch_labels(p, w.Xs, w.cell_start, w.pt_cell, w.core_s, w.nbr_start, nbr, w.core_start, w.Xc, w.bbox,
                           w.cell_cid, perm, labels, is_core, st));
     mark(11);
     GD_TRY(readback(ctx, ctx->small, kSmallInts, st));
@@ -325,8 +349,7 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
         ctx->nstages = kStages;
     }
     // remember the last run for introspection
-    GD_TRY(readback(ctx, w.pair_start + C, 1, st));
-    const int npairs = ctx->host_small[0];
+    const int npairs = ctx->host_small[kRange + 3];
     ctx->sizes[0] = n;
     ctx->sizes[1] = d;
     ctx->sizes[2] = C;
@@ -380,7 +403,7 @@ void gd_destroy(gd_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    for (DevBuf* b : {&ctx->arena, &ctx->nbr, &ctx->pairs, &ctx->io})
+    for (DevBuf* b : {&ctx->arena, &ctx->nbr, &ctx->pairs, &ctx->hard, &ctx->mscratch, &ctx->io})
         if (b->ptr) cudaFree(b->ptr);
     if (ctx->small) cudaFree(ctx->small);
     if (ctx->host_small) cudaFreeHost(ctx->host_small);

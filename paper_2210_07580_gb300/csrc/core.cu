@@ -16,14 +16,16 @@ __global__ void core_full_kernel(int n, int minpts, const int* __restrict__ cell
 }
 
 // One warp per grid with fewer than MinPts points.  Lane t holds own point t
-// (groups of 32).  The neighbour grids' points are streamed as one flat
-// sequence, 32 at a time (lane k takes the k-th), so that small grids still
-// fill the warp; each own point is broadcast in turn and its count grows by
-// the popcount of the ballot of hits.  The warp stops once every own point
-// has reached MinPts.
+// (groups of 32).  Neighbour grids whose box lies farther than eps from the
+// box of the group's points cannot contribute and are dropped.  The remaining
+// grids' points are streamed as one flat sequence, 32 at a time (lane k takes
+// the k-th), so that small grids still fill the warp; each own point is
+// broadcast in turn and its count grows by the popcount of the ballot of
+// hits.  The warp stops once every own point has reached MinPts.
 template <int D, int DP>
 __global__ void __launch_bounds__(256) core_sparse_kernel(Params p, const int* __restrict__ Xs,
-                                                          const int* __restrict__ cell_start, int C,
+                                                          const int* __restrict__ cell_start,
+                                                          const int* __restrict__ coord, int C,
                                                           const int* __restrict__ nbr_start,
                                                           const int* __restrict__ nbr,
                                                           unsigned char* __restrict__ core_s) {
@@ -40,6 +42,17 @@ __global__ void __launch_bounds__(256) core_sparse_kernel(Params p, const int* _
             int own[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) own[j] = lane < mg ? Xs[(long long)(g0 + lane) * DP + j] : 0;
+            long long olo[D], ohi[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                int lo = lane < mg ? own[j] : 0x7fffffff, hi = lane < mg ? own[j] : (int)0x80000000;
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+                    hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+                }
+                olo[j] = lo;
+                ohi[j] = hi;
+            }
             int cnt = 0;
             bool all_done = false;
             for (int t0 = t_begin; t0 < t_end && !all_done; t0 += 32) {
@@ -47,8 +60,20 @@ __global__ void __launch_bounds__(256) core_sparse_kernel(Params p, const int* _
                 int st = 0, sz = 0;
                 if (lane < nb) {
                     const int cc = nbr[t0 + lane];
-                    st = cell_start[cc];
-                    sz = cell_start[cc + 1] - st;
+                    long long g2 = 0;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        const long long clo = (long long)p.mn[j] + (long long)coord[(long long)cc * D + j] * p.s;
+                        const long long chi = clo + p.s - 1;
+                        long long g = 0;
+                        if (clo > ohi[j]) g = clo - ohi[j];
+                        else if (olo[j] > chi) g = olo[j] - chi;
+                        g2 += g * g;
+                    }
+                    if (g2 <= eps2) {
+                        st = cell_start[cc];
+                        sz = cell_start[cc + 1] - st;
+                    }
                 }
                 const int incl = warp_inclusive_scan(sz);
                 const int total = __shfl_sync(kFull, incl, 31);
@@ -93,31 +118,32 @@ __global__ void __launch_bounds__(256) core_sparse_kernel(Params p, const int* _
 }
 
 template <int D>
-static void core_sparse_launch(const Params& p, const int* Xs, const int* cell_start, int C, const int* nbr_start,
-                               const int* nbr, unsigned char* core_s, cudaStream_t st) {
+static void core_sparse_launch(const Params& p, const int* Xs, const int* cell_start, const int* coord, int C,
+                               const int* nbr_start, const int* nbr, unsigned char* core_s, cudaStream_t st) {
     constexpr int DP = D == 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
     long long blocks = ((long long)C * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    core_sparse_kernel<D, DP><<<(int)blocks, 256, 0, st>>>(p, Xs, cell_start, C, nbr_start, nbr, core_s);
+    core_sparse_kernel<D, DP><<<(int)blocks, 256, 0, st>>>(p, Xs, cell_start, coord, C, nbr_start, nbr, core_s);
     GD_COUNT_LAUNCH();
 }
 
-cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell, int C,
-                        const int* nbr_start, const int* nbr, unsigned char* core_s, cudaStream_t st) {
+cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
+                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, unsigned char* core_s,
+                        cudaStream_t st) {
     int blocks = (p.n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     core_full_kernel<<<blocks, 256, 0, st>>>(p.n, p.minpts, cell_start, pt_cell, core_s);
     GD_COUNT_LAUNCH();
     switch (p.d) {
-        case 1: core_sparse_launch<1>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 2: core_sparse_launch<2>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 3: core_sparse_launch<3>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 4: core_sparse_launch<4>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 5: core_sparse_launch<5>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 6: core_sparse_launch<6>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        case 7: core_sparse_launch<7>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
-        default: core_sparse_launch<8>(p, Xs, cell_start, C, nbr_start, nbr, core_s, st); break;
+        case 1: core_sparse_launch<1>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 2: core_sparse_launch<2>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 3: core_sparse_launch<3>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 4: core_sparse_launch<4>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 5: core_sparse_launch<5>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 6: core_sparse_launch<6>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        case 7: core_sparse_launch<7>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+        default: core_sparse_launch<8>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
     }
     return cudaGetLastError();
 }

@@ -151,23 +151,32 @@ cudaError_t launch_walk_fill(const Params& p, const int* cell_coord, int C, Leve
                              int* nbr, cudaStream_t st);
 
 // Core points (core.cu).
-cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell, int C,
-                        const int* nbr_start, const int* nbr, unsigned char* core_s, cudaStream_t st);
+cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
+                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, unsigned char* core_s,
+                        cudaStream_t st);
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Params& p, const unsigned char* core_s, const int* cell_start, int C,
-                              int* core_cnt, cudaStream_t st);
-cudaError_t launch_core_compact(const Params& p, const int* Xs, const unsigned char* core_s,
-                                const int* cell_start, const int* core_start, int C, int* Xc, int* bbox,
+                              int* core_cnt, int* bbox, cudaStream_t st);
+cudaError_t launch_core_pack(const Params& p, const int* Xs, const unsigned char* core_s, const int* pt_cell,
+                             const int* cell_start, const int* core_start, int* Xc, int* bbox, cudaStream_t st);
+cudaError_t launch_cell_max(const int* cell_start, int C, int* out, cudaStream_t st);
+cudaError_t launch_pair_count(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
+                              const int* cell_coord, int C, int* t_count, int* f_count, cudaStream_t st);
+cudaError_t launch_pair_fill(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
+                             const int* cell_coord, int C, const int* t_start, const int* f_start, int2* pairs,
+                             cudaStream_t st);
+cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, int* range, int* hard_cnt,
                                 cudaStream_t st);
-cudaError_t launch_pair_count(const int* nbr_start, const int* nbr, const int* core_start, int C,
-                              int* pair_count, cudaStream_t st);
-cudaError_t launch_pair_fill(const int* nbr_start, const int* nbr, const int* core_start, int C,
-                             const int* pair_start, int2* pairs, cudaStream_t st);
 cudaError_t launch_uf_init(int* parent, int C, cudaStream_t st);
-// npairs is read on the device (pair_start[C]); max_pairs bounds it and sizes the grid.
-cudaError_t launch_merge(const Params& p, const int2* pairs, const int* npairs, int max_pairs, const int* Xc,
-                         const int* core_start, const int* bbox, int* parent, unsigned* status, cudaStream_t st);
+// Blocks of the FastMerging kernel; each owns 2 * wpb words of `scratch`,
+// wpb = ceil(largest grid / 32).
+int merge_fm_blocks();
+// One merge wave (0: touching pairs, 1: the others): warp-level test of every
+// pair in range[2*wave .. 2*wave+1], then FastMerging of the pairs it hands on.
+cudaError_t launch_merge_wave(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
+                              const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
+                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, cudaStream_t st);
 
 // Labels (label.cu).
 cudaError_t launch_cluster_ids(const Params& p, int* parent, const int* core_start, const int* cell_start,
@@ -175,7 +184,7 @@ cudaError_t launch_cluster_ids(const Params& p, int* parent, const int* core_sta
                                int* cell_cid, cudaStream_t st, unsigned* status);
 cudaError_t launch_labels(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
                           const unsigned char* core_s, const int* nbr_start, const int* nbr,
-                          const int* core_start, const int* Xc, const int* cell_cid, const int* perm,
-                          int* labels, unsigned char* is_core, cudaStream_t st);
+                          const int* core_start, const int* Xc, const int* bbox, const int* cell_cid,
+                          const int* perm, int* labels, unsigned char* is_core, cudaStream_t st);
 
 }  // namespace gd

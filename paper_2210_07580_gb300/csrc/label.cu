@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) labels_kernel(Params p, const int* __rest
                                                      const unsigned char* __restrict__ core_s,
                                                      const int* __restrict__ nbr_start, const int* __restrict__ nbr,
                                                      const int* __restrict__ core_start, const int* __restrict__ Xc,
+                                                     const int* __restrict__ bbox,
                                                      const int* __restrict__ cell_cid, const int* __restrict__ perm,
                                                      int* __restrict__ labels, unsigned char* __restrict__ is_core) {
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -83,6 +84,17 @@ __global__ void __launch_bounds__(256) labels_kernel(Params p, const int* __rest
                 const int c2 = nbr[t];
                 const int id = cell_cid[c2];
                 if (id < 0 || id >= best) continue;
+                // skip a grid whose core points' box is farther than eps from x
+                const int* bb = bbox + (long long)c2 * 2 * D;
+                long long g2 = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    long long g = 0;
+                    if (bb[j] > x[j]) g = (long long)bb[j] - x[j];
+                    else if (x[j] > bb[D + j]) g = (long long)x[j] - bb[D + j];
+                    g2 += g * g;
+                }
+                if (g2 > p.eps2) continue;
                 for (int k = core_start[c2]; k < core_start[c2 + 1]; ++k) {
                     int y[D];
 #pragma unroll
@@ -104,29 +116,30 @@ __global__ void __launch_bounds__(256) labels_kernel(Params p, const int* __rest
 template <int D>
 static void labels_launch(const Params& p, const int* Xs, const int* pt_cell, const unsigned char* core_s,
                           const int* nbr_start, const int* nbr, const int* core_start, const int* Xc,
-                          const int* cell_cid, const int* perm, int* labels, unsigned char* is_core, cudaStream_t st) {
+                          const int* bbox, const int* cell_cid, const int* perm, int* labels, unsigned char* is_core,
+                          cudaStream_t st) {
     constexpr int DP = D == 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
     int blocks = (p.n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    labels_kernel<D, DP><<<blocks, 256, 0, st>>>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid,
-                                                 perm, labels, is_core);
+    labels_kernel<D, DP><<<blocks, 256, 0, st>>>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox,
+                                                 cell_cid, perm, labels, is_core);
     GD_COUNT_LAUNCH();
 }
 
 cudaError_t launch_labels(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
                           const unsigned char* core_s, const int* nbr_start, const int* nbr, const int* core_start,
-                          const int* Xc, const int* cell_cid, const int* perm, int* labels, unsigned char* is_core,
-                          cudaStream_t st) {
+                          const int* Xc, const int* bbox, const int* cell_cid, const int* perm, int* labels,
+                          unsigned char* is_core, cudaStream_t st) {
     (void)cell_start;
     switch (p.d) {
-        case 1: labels_launch<1>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 2: labels_launch<2>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 3: labels_launch<3>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 4: labels_launch<4>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 5: labels_launch<5>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 6: labels_launch<6>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        case 7: labels_launch<7>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
-        default: labels_launch<8>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels, is_core, st); break;
+        case 1: labels_launch<1>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 2: labels_launch<2>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 3: labels_launch<3>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 4: labels_launch<4>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 5: labels_launch<5>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 6: labels_launch<6>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        case 7: labels_launch<7>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
+        default: labels_launch<8>(p, Xs, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm, labels, is_core, st); break;
     }
     return cudaGetLastError();
 }

@@ -92,7 +92,10 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     int* mnmx = small;
     int* num_cells = small + 16;
     unsigned* status = (unsigned*)(small + 17);
+    int* max_cell = small + 18;
     int* level_count = small + 24;
+    int* mrange = small + 32;
+    int* hard_cnt = small + 36;
     int host[64];
 
     Params p;
@@ -135,7 +138,7 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     const size_t N = (size_t)n;
     void *keyA, *keyB;
     int *valA, *valB, *Xs, *pt_cell, *Xc, *cell_start, *cell_coord, *nbr_start, *core_start, *bbox, *pair_start,
-        *parent, *cid_root, *cell_cid, *tmp;
+        *pair_start_f, *parent, *cid_root, *cell_cid, *tmp;
     unsigned char* core_s;
     NA_TAKE(keyA, void*, N * 8 * p.key_words);
     NA_TAKE(keyB, void*, N * 8 * p.key_words);
@@ -159,6 +162,7 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_TAKE(core_start, int*, (N + 1) * 4);
     NA_TAKE(bbox, int*, N * 2 * d * 4);
     NA_TAKE(pair_start, int*, (N + 1) * 4);
+    NA_TAKE(pair_start_f, int*, (N + 1) * 4);
     NA_TAKE(parent, int*, N * 4);
     NA_TAKE(cid_root, int*, N * 4);
     NA_TAKE(cell_cid, int*, N * 4);
@@ -176,33 +180,43 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_CUDA(launch_compact(p, X, keys, perm, tmp, cell_start, cell_coord, pt_cell, Xs, num_cells, st));
     NA_TRY(fetch(host, num_cells, 1, st));
     const int C = host[0];
+    NA_CUDA(launch_cell_max(cell_start, C, max_cell, st));
 
     NA_CUDA(build_levels(p, cell_coord, C, lv, tmp, st));
     NA_CUDA(launch_walk_count(p, cell_coord, C, lv, nbr_start, st));
     NA_CUDA(scan_exclusive(nbr_start, nbr_start, C, tmp, st));
     NA_TRY(fetch(host, nbr_start + C, 1, st));
     const long long nnbr = (unsigned)host[0];
+    NA_TRY(fetch(host, max_cell, 1, st));
+    const int wpb = (host[0] + 31) / 32 + 1;
     int* nbr;
-    int2* pairs;
+    int2 *pairs, *hard;
+    unsigned* mscratch;
     NA_TAKE(nbr, int*, (size_t)nnbr * 4 + 16);
     NA_TAKE(pairs, int2*, (size_t)nnbr * 8 + 16);
+    NA_TAKE(hard, int2*, (size_t)nnbr * 8 + 16);
+    NA_TAKE(mscratch, unsigned*, (size_t)merge_fm_blocks() * 2 * wpb * 4);
     NA_CUDA(launch_walk_fill(p, cell_coord, C, lv, nbr_start, nbr, st));
 
-    NA_CUDA(launch_core(p, Xs, cell_start, pt_cell, C, nbr_start, nbr, core_s, st));
-    NA_CUDA(launch_core_count(p, core_s, cell_start, C, core_start, st));
+    NA_CUDA(launch_core(p, Xs, cell_start, pt_cell, cell_coord, C, nbr_start, nbr, core_s, st));
+    NA_CUDA(launch_core_count(p, core_s, cell_start, C, core_start, bbox, st));
     NA_CUDA(scan_exclusive(core_start, core_start, C, tmp, st));
-    NA_CUDA(launch_core_compact(p, Xs, core_s, cell_start, core_start, C, Xc, bbox, st));
-    NA_CUDA(launch_pair_count(nbr_start, nbr, core_start, C, pair_start, st));
+    NA_CUDA(launch_core_pack(p, Xs, core_s, pt_cell, cell_start, core_start, Xc, bbox, st));
+    NA_CUDA(launch_pair_count(p, nbr_start, nbr, core_start, cell_coord, C, pair_start, pair_start_f, st));
     NA_CUDA(scan_exclusive(pair_start, pair_start, C, tmp, st));
-    NA_CUDA(launch_pair_fill(nbr_start, nbr, core_start, C, pair_start, pairs, st));
+    NA_CUDA(scan_exclusive(pair_start_f, pair_start_f, C, tmp, st));
+    NA_CUDA(launch_pair_fill(p, nbr_start, nbr, core_start, cell_coord, C, pair_start, pair_start_f, pairs, st));
 
     // the status word starts at zero on every call (the array keeps old contents)
     NA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
     NA_CUDA(launch_uf_init(parent, C, st));
-    NA_CUDA(launch_merge(p, pairs, pair_start + C, (int)nnbr, Xc, core_start, bbox, parent, status, st));
+    NA_CUDA(launch_merge_ranges(pair_start, pair_start_f, C, mrange, hard_cnt, st));
+    for (int wave = 0; wave < 2; ++wave)
+        NA_CUDA(launch_merge_wave(p, wave, pairs, mrange, (int)nnbr, Xc, core_start, bbox, parent, status, hard,
+                                  hard_cnt, mscratch, wpb, st));
     NA_CUDA(launch_cluster_ids(p, parent, core_start, cell_start, core_s, perm, C, cid_root, cell_cid, st, status));
-    NA_CUDA(launch_labels(p, Xs, cell_start, pt_cell, core_s, nbr_start, nbr, core_start, Xc, cell_cid, perm, labels,
-                          is_core, st));
+    NA_CUDA(launch_labels(p, Xs, cell_start, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm,
+                          labels, is_core, st));
     NA_TRY(fetch(host, (const int*)status, 1, st));
     if ((unsigned)host[0] & kDevTimeout) return GD_ETIMEOUT;
     return GD_OK;
