@@ -298,7 +298,8 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
 
     // --- core points (G13 rule)
     mark(6);
-    GD_CUDA(launch_core(p, w.Xs, w.cell_start, w.pt_cell, w.cell_coord, C, w.nbr_start, nbr, w.core_s, st));
+    GD_CUDA(launch_core(p, w.Xs, w.cell_start, w.pt_cell, w.cell_coord, C, w.nbr_start, nbr, w.pair_start, w.tmp,
+                        w.core_s, st));
 
     // --- core point sets s_i and their boxes
     mark(7);

@@ -1,7 +1,7 @@
 // Core points (Def. 1) by the G13 rule of Section 3.2: a grid holding at least
 // MinPts points has only core points, since its diameter is <= eps.  In every
 // other grid each point counts the points within eps over Nei(g) and stops as
-// soon as it reaches MinPts.
+// soon as it reaches MinPts (as in the paper, counting can stop early).
 #include "gd_internal.cuh"
 
 namespace gd {
@@ -15,135 +15,145 @@ __global__ void core_full_kernel(int n, int minpts, const int* __restrict__ cell
     }
 }
 
-// One warp per grid with fewer than MinPts points.  Lane t holds own point t
-// (groups of 32).  Neighbour grids whose box lies farther than eps from the
-// box of the group's points cannot contribute and are dropped.  The remaining
-// grids' points are streamed as one flat sequence, 32 at a time (lane k takes
-// the k-th), so that small grids still fill the warp; each own point is
-// broadcast in turn and its count grows by the popcount of the ballot of
-// hits.  The warp stops once every own point has reached MinPts.
+// Points of grids with fewer than MinPts points, as a flat list: nf_start is
+// the exclusive scan of (grid size if the grid is not full, else 0).
+__global__ void nonfull_count_kernel(int minpts, const int* __restrict__ cell_start, int C, int* __restrict__ nf) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int m = cell_start[c + 1] - cell_start[c];
+    nf[c] = m < minpts ? m : 0;
+}
+
+// One warp per point p of a non-full grid g.  The lanes take the grids of
+// Nei(g) 32 at a time and compare each grid's box (its identifier range,
+// which holds every point of the grid) with p:
+//   - box entirely within eps of p: all its points count, no distances;
+//   - box entirely beyond eps: skipped;
+//   - otherwise its points are tested one by one (the straddling grids'
+//     points are streamed as one flat sequence, lane k taking the k-th).
+// g itself is always entirely within eps (its diameter is <= eps).  The warp
+// stops as soon as the count reaches MinPts.
 template <int D, int DP>
-__global__ void __launch_bounds__(256) core_sparse_kernel(Params p, const int* __restrict__ Xs,
-                                                          const int* __restrict__ cell_start,
-                                                          const int* __restrict__ coord, int C,
-                                                          const int* __restrict__ nbr_start,
-                                                          const int* __restrict__ nbr,
-                                                          unsigned char* __restrict__ core_s) {
+__global__ void __launch_bounds__(256) core_point_kernel(Params p, const int* __restrict__ Xs,
+                                                         const int* __restrict__ cell_start,
+                                                         const int* __restrict__ coord, int C,
+                                                         const int* __restrict__ nf_start,
+                                                         const int* __restrict__ nbr_start,
+                                                         const int* __restrict__ nbr,
+                                                         unsigned char* __restrict__ core_s) {
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long eps2 = p.eps2;
+    const long long eps2 = p.eps2, s = p.s;
     const int minpts = p.minpts;
-    for (long long c = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); c < C; c += warps) {
-        const int b = cell_start[c], e = cell_start[c + 1];
-        if (e - b >= minpts) continue;
+    const int total = nf_start[C];
+    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
+        // grid of flat position w: last c with nf_start[c] <= w
+        int lo = 0, hi = C - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (nf_start[mid] <= w)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int c = lo;
+        const long long i = (long long)cell_start[c] + (w - nf_start[c]);
+        long long x[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];
+        int cnt = 0;
         const int t_begin = nbr_start[c], t_end = nbr_start[c + 1];
-        for (int g0 = b; g0 < e; g0 += 32) {
-            const int mg = min(32, e - g0);
-            int own[D];
+        for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
+            const int nb = min(32, t_end - t0);
+            int st = 0, sz = 0, whole = 0;
+            if (lane < nb) {
+                const int cc = nbr[t0 + lane];
+                long long mind = 0, maxd = 0;
 #pragma unroll
-            for (int j = 0; j < D; ++j) own[j] = lane < mg ? Xs[(long long)(g0 + lane) * DP + j] : 0;
-            long long olo[D], ohi[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                int lo = lane < mg ? own[j] : 0x7fffffff, hi = lane < mg ? own[j] : (int)0x80000000;
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = min(lo, __shfl_xor_sync(kFull, lo, o));
-                    hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+                for (int j = 0; j < D; ++j) {
+                    const long long blo = (long long)p.mn[j] + (long long)coord[(long long)cc * D + j] * s;
+                    const long long bhi = blo + s - 1;
+                    long long g = 0;
+                    if (blo > x[j]) g = blo - x[j];
+                    else if (x[j] > bhi) g = x[j] - bhi;
+                    mind += g * g;
+                    const long long a = x[j] - blo, b = bhi - x[j];
+                    const long long f = a > b ? a : b;
+                    maxd += f * f;
                 }
-                olo[j] = lo;
-                ohi[j] = hi;
+                const int b0 = cell_start[cc], m = cell_start[cc + 1] - b0;
+                if (maxd <= eps2) {
+                    whole = m;
+                } else if (mind <= eps2) {
+                    st = b0;
+                    sz = m;
+                }
             }
-            int cnt = 0;
-            bool all_done = false;
-            for (int t0 = t_begin; t0 < t_end && !all_done; t0 += 32) {
-                const int nb = min(32, t_end - t0);
-                int st = 0, sz = 0;
-                if (lane < nb) {
-                    const int cc = nbr[t0 + lane];
-                    long long g2 = 0;
+            int add = whole;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(kFull, add, o);
+            cnt += add;
+            if (cnt >= minpts) break;
+            const int incl = warp_inclusive_scan(sz);
+            const int flat = __shfl_sync(kFull, incl, 31);
+            for (int k0 = 0; k0 < flat; k0 += 32) {
+                const int k = k0 + lane;
+                int lo2 = 0, hi2 = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (__shfl_sync(kFull, incl, mid) > k)
+                        hi2 = mid;
+                    else
+                        lo2 = mid + 1;
+                }
+                const int gst = __shfl_sync(kFull, st, lo2);
+                const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
+                bool hit = false;
+                if (k < flat) {
+                    const long long qi = (long long)gst + (k - gex);
+                    long long dd = 0;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        const long long clo = (long long)p.mn[j] + (long long)coord[(long long)cc * D + j] * p.s;
-                        const long long chi = clo + p.s - 1;
-                        long long g = 0;
-                        if (clo > ohi[j]) g = clo - ohi[j];
-                        else if (olo[j] > chi) g = olo[j] - chi;
-                        g2 += g * g;
+                        const long long t = (long long)Xs[qi * DP + j] - x[j];
+                        dd += t * t;
                     }
-                    if (g2 <= eps2) {
-                        st = cell_start[cc];
-                        sz = cell_start[cc + 1] - st;
-                    }
+                    hit = dd <= eps2;
                 }
-                const int incl = warp_inclusive_scan(sz);
-                const int total = __shfl_sync(kFull, incl, 31);
-                for (int k0 = 0; k0 < total; k0 += 32) {
-                    const int k = k0 + lane;
-                    // which of the 32 grids holds flat position k: first lane with incl > k
-                    int lo = 0, hi = 31;
-#pragma unroll
-                    for (int step = 0; step < 5; ++step) {
-                        const int mid = (lo + hi) >> 1;
-                        const int v = __shfl_sync(kFull, incl, mid);
-                        if (v > k)
-                            hi = mid;
-                        else
-                            lo = mid + 1;
-                    }
-                    const int gi = lo;
-                    const int gst = __shfl_sync(kFull, st, gi);
-                    const int gex = __shfl_sync(kFull, incl, gi) - __shfl_sync(kFull, sz, gi);
-                    const bool valid = k < total;
-                    int q[D];
-                    const long long qi = (long long)gst + (k - gex);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) q[j] = valid ? Xs[qi * DP + j] : 0;
-                    for (int t = 0; t < mg; ++t) {
-                        int pt[D];
-#pragma unroll
-                        for (int j = 0; j < D; ++j) pt[j] = __shfl_sync(kFull, own[j], t);
-                        const bool hit = valid && sqdist<D>(pt, q) <= eps2;
-                        const int add = __popc(__ballot_sync(kFull, hit));
-                        if (lane == t) cnt += add;
-                    }
-                    if (__all_sync(kFull, lane >= mg || cnt >= minpts)) {
-                        all_done = true;
-                        break;
-                    }
-                }
+                cnt += __popc(__ballot_sync(kFull, hit));
+                if (cnt >= minpts) break;
             }
-            if (lane < mg) core_s[g0 + lane] = cnt >= minpts ? 1 : 0;
         }
+        if (lane == 0) core_s[i] = cnt >= minpts ? 1 : 0;
     }
 }
 
 template <int D>
-static void core_sparse_launch(const Params& p, const int* Xs, const int* cell_start, const int* coord, int C,
-                               const int* nbr_start, const int* nbr, unsigned char* core_s, cudaStream_t st) {
+static void core_point_launch(const Params& p, const int* Xs, const int* cell_start, const int* coord, int C,
+                              const int* nf_start, const int* nbr_start, const int* nbr, unsigned char* core_s,
+                              cudaStream_t st) {
     constexpr int DP = D == 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
-    long long blocks = ((long long)C * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    core_sparse_kernel<D, DP><<<(int)blocks, 256, 0, st>>>(p, Xs, cell_start, coord, C, nbr_start, nbr, core_s);
+    core_point_kernel<D, DP><<<152 * 16, 256, 0, st>>>(p, Xs, cell_start, coord, C, nf_start, nbr_start, nbr, core_s);
     GD_COUNT_LAUNCH();
 }
 
 cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
-                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, unsigned char* core_s,
-                        cudaStream_t st) {
+                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, int* nf_start, int* tmp,
+                        unsigned char* core_s, cudaStream_t st) {
     int blocks = (p.n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     core_full_kernel<<<blocks, 256, 0, st>>>(p.n, p.minpts, cell_start, pt_cell, core_s);
     GD_COUNT_LAUNCH();
+    nonfull_count_kernel<<<(C + 255) / 256, 256, 0, st>>>(p.minpts, cell_start, C, nf_start);
+    GD_COUNT_LAUNCH();
+    cudaError_t e = scan_exclusive(nf_start, nf_start, C, tmp, st);
+    if (e != cudaSuccess) return e;
     switch (p.d) {
-        case 1: core_sparse_launch<1>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 2: core_sparse_launch<2>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 3: core_sparse_launch<3>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 4: core_sparse_launch<4>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 5: core_sparse_launch<5>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 6: core_sparse_launch<6>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        case 7: core_sparse_launch<7>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
-        default: core_sparse_launch<8>(p, Xs, cell_start, cell_coord, C, nbr_start, nbr, core_s, st); break;
+#define GD_CORE(DD) \
+    case DD: core_point_launch<DD>(p, Xs, cell_start, cell_coord, C, nf_start, nbr_start, nbr, core_s, st); break;
+        GD_CORE(1) GD_CORE(2) GD_CORE(3) GD_CORE(4) GD_CORE(5) GD_CORE(6) GD_CORE(7)
+        default: core_point_launch<8>(p, Xs, cell_start, cell_coord, C, nf_start, nbr_start, nbr, core_s, st); break;
+#undef GD_CORE
     }
     return cudaGetLastError();
 }

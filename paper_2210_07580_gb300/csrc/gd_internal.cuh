@@ -151,9 +151,10 @@ cudaError_t launch_walk_fill(const Params& p, const int* cell_coord, int C, Leve
                              int* nbr, cudaStream_t st);
 
 // Core points (core.cu).
+// nf_start: C+1 ints of workspace (points of non-full grids, scanned).
 cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
-                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, unsigned char* core_s,
-                        cudaStream_t st);
+                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, int* nf_start, int* tmp,
+                        unsigned char* core_s, cudaStream_t st);
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Params& p, const unsigned char* core_s, const int* cell_start, int C,

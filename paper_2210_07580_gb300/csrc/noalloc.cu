@@ -198,7 +198,7 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_TAKE(mscratch, unsigned*, (size_t)merge_fm_blocks() * 2 * wpb * 4);
     NA_CUDA(launch_walk_fill(p, cell_coord, C, lv, nbr_start, nbr, st));
 
-    NA_CUDA(launch_core(p, Xs, cell_start, pt_cell, cell_coord, C, nbr_start, nbr, core_s, st));
+    NA_CUDA(launch_core(p, Xs, cell_start, pt_cell, cell_coord, C, nbr_start, nbr, pair_start, tmp, core_s, st));
     NA_CUDA(launch_core_count(p, core_s, cell_start, C, core_start, bbox, st));
     NA_CUDA(scan_exclusive(core_start, core_start, C, tmp, st));
     NA_CUDA(launch_core_pack(p, Xs, core_s, pt_cell, cell_start, core_start, Xc, bbox, st));
