@@ -33,9 +33,6 @@ WORKLOADS = {
     "tiny": "blobs d=2 n=20,000 eps=800 MinPts=10 (10 blobs sigma=1500 + 5% noise)",
 }
 L2_FLUSH_BYTES = 256 << 20
-# Algorithmic bytes per point of one radix-sort pass: read key (8) + value (4),
-# write key (8) + value (4).
-SORT_PASS_BYTES_PER_PT = 24
 
 
 def dist_env():
@@ -243,12 +240,13 @@ def run_gpu(args):
         total_pts = n * ws
         value = total_pts / (ms_max / 1e3) / 1e6
         peak, peak_kind = peaks()
-        # dominant kernel family: the radix sort (hist + scatter per pass);
-        # algorithmic bytes of its scatter passes over the stage time
-        passes = -(-sizes["key_bits"] // 8)
-        sort_ms = stages.get("sort", 0.0)
-        sort_bytes = passes * SORT_PASS_BYTES_PER_PT * n
-        achieved = sort_bytes / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else None
+        # dominant kernel: the onesweep radix-sort pass.  Algorithmic bytes
+        # of one launch: every key and value read once and written once.
+        passes = max(1, sizes["sort_passes"])
+        key_bytes = 8 if sizes["key_bits"] <= 64 else 16
+        launch_bytes = 2 * (key_bytes + 4) * n
+        launch_ms = stages.get("sort", 0.0) / passes
+        achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
@@ -263,11 +261,12 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(n * 4 + n)},
             "gpu_launches": int(launches),
             "stages_ms": stages,
-            "roofline": {"bound": "hbm", "kernel": "radix sort (hist + scatter, all passes)",
+            "roofline": {"bound": "hbm", "kernel": "onesweep_kernel (one radix-sort pass)",
                          "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
-                         "algorithmic_bytes": int(sort_bytes)},
+                         "bytes_per_launch": int(launch_bytes), "launch_ms": round(launch_ms, 4),
+                         "launches_per_step": passes},
             "wall_s_timed": round(t_wall, 3),
         }
         if not args.no_cpu_baseline and ws == 1:

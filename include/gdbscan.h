@@ -111,8 +111,10 @@ typedef enum {
 
 /* Sizes of the last run: out[0]=n, out[1]=d, out[2]=C (non-empty grids),
  * out[3]=nnbr (neighbour list length), out[4]=cell side s, out[5]=key bits,
- * out[6]=kernel launches of the run, out[7]=candidate merge pairs.  Returns GD_EINVAL before any run. */
-gd_status gd_last_sizes(const gd_ctx *ctx, int64_t out[8]);
+ * out[6]=kernel launches of the run, out[7]=candidate merge pairs,
+ * out[8]=radix-sort passes, out[9]=bits per digit, out[10]=pairs decided by
+ * FastMerging, out[11]=0 (reserved).  Returns GD_EINVAL before any run. */
+gd_status gd_last_sizes(const gd_ctx *ctx, int64_t out[12]);
 
 /* Copy `bytes` bytes of an internal array of the last run into host memory
  * (synchronous).  GD_EINVAL if bytes exceeds the array's size. */

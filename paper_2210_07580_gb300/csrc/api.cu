@@ -61,7 +61,7 @@ int padded_dim(int d) { return d == 1 ? 1 : d == 2 ? 2 : d <= 4 ? 4 : 8; }
 
 // Lay the fixed workspace out from `base` (or only size it when base is
 // null).  Arrays indexed by grid are sized for n grids, the upper bound.
-size_t carve(Work* w, char* base, int64_t n, int d, int key_words) {
+size_t carve(Work* w, char* base, int64_t n, int d, int key_words, int key_bits) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> void* {
         off = (off + 255) & ~(size_t)255;
@@ -92,7 +92,7 @@ size_t carve(Work* w, char* base, int64_t n, int d, int key_words) {
     w->parent = (int*)take(N * 4);
     w->cid_root = (int*)take(N * 4);
     w->cell_cid = (int*)take(N * 4);
-    size_t t = radix_tmp_ints((int)n, key_words);
+    size_t t = radix_tmp_ints((int)n, key_words, key_bits);
     t = t > compact_tmp_ints((int)n) ? t : compact_tmp_ints((int)n);
     t = t > levels_tmp_ints((int)n, d) ? t : levels_tmp_ints((int)n, d);
     t = t > scan_tmp_ints(n + 1) ? t : scan_tmp_ints(n + 1);
@@ -140,7 +140,7 @@ struct gd_ctx {
     int nstages = 0;
     std::string err;
     bool have_run = false;
-    int64_t sizes[8] = {};
+    int64_t sizes[12] = {};
     const void* view_ptr[7] = {};
     size_t view_bytes[7] = {};
 };
@@ -256,16 +256,17 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
     p.key_words = total_bits <= 64 ? 1 : 2;
 
     Work w;
-    const size_t need = carve(&w, nullptr, n, d, p.key_words);
+    const size_t need = carve(&w, nullptr, n, d, p.key_words, p.key_bits);
     GD_TRY(ensure(ctx, ctx->arena, need, st));
-    carve(&w, ctx->arena.ptr, n, d, p.key_words);
+    carve(&w, ctx->arena.ptr, n, d, p.key_words, p.key_bits);
 
-    // --- identifiers and sort (Eq. 1, Alg. 1)
+    // --- identifiers (Eq. 1) with digit histograms, then the sort (Alg. 1)
     mark(1);
-    GD_CUDA(launch_quantise(X, p, w.keyA, w.valA, st));
+    GD_CUDA(cudaMemsetAsync(ctx->small + kStatus, 0, sizeof(int), st));
+    GD_CUDA(quantise_hist(X, p, w.keyA, w.valA, w.tmp, st));
     mark(2);
     int in_b = 0;
-    GD_CUDA(radix_sort(w.keyA, w.valA, w.keyB, w.valB, n, p.key_words, p.key_bits, w.tmp, st, &in_b));
+    GD_CUDA(sort_passes(p, w.keyA, w.valA, w.keyB, w.valB, w.tmp, (unsigned*)(ctx->small + kStatus), st, &in_b));
     void* keys = in_b ? w.keyB : w.keyA;
     int* perm = in_b ? w.valB : w.valA;
 
@@ -326,7 +327,6 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
     GD_TRY(readback(ctx, ctx->small + kMaxCell, 1, st));
     const int wpb = (ctx->host_small[0] + 31) / 32 + 1;
     GD_TRY(ensure(ctx, ctx->mscratch, (size_t)merge_fm_blocks() * 2 * wpb * 4, st));
-    GD_CUDA(cudaMemsetAsync(ctx->small + kStatus, 0, sizeof(int), st));
     GD_CUDA(launch_uf_init(w.parent, C, st));
     GD_CUDA(launch_merge_ranges(w.pair_start, w.pair_start_f, C, ctx->small + kRange, ctx->small + kHardCnt, st));
     for (int wave = 0; wave < 2; ++wave)
@@ -343,7 +343,7 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
     mark(11);
     GD_TRY(readback(ctx, ctx->small, kSmallInts, st));
     const unsigned status = (unsigned)ctx->host_small[kStatus];
-    if (status & kDevTimeout) return fail(ctx, GD_ETIMEOUT, "union-find retry limit reached");
+    if (status & kDevTimeout) return fail(ctx, GD_ETIMEOUT, "a bounded device wait or retry loop hit its limit");
 
     if (ctx->timing) {
         for (int s = 0; s < kStages; ++s) cudaEventElapsedTime(&ctx->stage_ms[s], ctx->ev[s], ctx->ev[s + 1]);
@@ -359,6 +359,13 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
     ctx->sizes[5] = p.key_bits;
     ctx->sizes[6] = t_launches - launches0;
     ctx->sizes[7] = npairs;
+    {
+        const SortPlan sp = sort_plan(n, p.key_words, p.key_bits);
+        ctx->sizes[8] = sp.passes;
+        ctx->sizes[9] = sp.bits;
+    }
+    ctx->sizes[10] = (int64_t)ctx->host_small[kHardCnt] + ctx->host_small[kHardCnt + 1];
+    ctx->sizes[11] = 0;
     ctx->view_ptr[GD_VIEW_PERM] = perm;
     ctx->view_bytes[GD_VIEW_PERM] = (size_t)n * 4;
     ctx->view_ptr[GD_VIEW_CELL_START] = w.cell_start;
@@ -416,7 +423,7 @@ void gd_destroy(gd_ctx* ctx) {
 size_t gd_workspace_bytes(int64_t n, int d) {
     if (n < 0 || d < 1 || d > kMaxD) return 0;
     Work w;
-    return carve(&w, nullptr, n, d, 2) + (size_t)n * 8;
+    return carve(&w, nullptr, n, d, 2, 128) + (size_t)n * 8;
 }
 
 gd_status gd_dbscan(gd_ctx* ctx, const int32_t* X, int64_t n, int d, int64_t eps2, int32_t minpts, int32_t* labels,
@@ -466,9 +473,9 @@ const char* gd_status_str(gd_status s) {
 
 const char* gd_last_error(const gd_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
-gd_status gd_last_sizes(const gd_ctx* ctx, int64_t out[8]) {
+gd_status gd_last_sizes(const gd_ctx* ctx, int64_t out[12]) {
     if (!ctx || !out || !ctx->have_run) return GD_EINVAL;
-    for (int i = 0; i < 8; ++i) out[i] = ctx->sizes[i];
+    for (int i = 0; i < 12; ++i) out[i] = ctx->sizes[i];
     return GD_OK;
 }
 

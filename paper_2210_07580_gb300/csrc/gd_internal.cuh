@@ -127,11 +127,24 @@ cudaError_t scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaS
 // Grid construction (grid.cu).
 cudaError_t launch_init_bounds(int* mnmx, cudaStream_t st);
 cudaError_t launch_bounds(const int* X, int n, int d, int* mnmx, cudaStream_t st);
-cudaError_t launch_quantise(const int* X, const Params& p, void* keys, int* vals, cudaStream_t st);
-size_t radix_tmp_ints(int n, int key_words);
-// Sorts (keys, vals) by the low key_bits bits; returns which buffer (0: a, 1: b) holds the result.
-cudaError_t radix_sort(void* keys_a, int* vals_a, void* keys_b, int* vals_b, int n, int key_words,
-                       int key_bits, int* tmp, cudaStream_t st, int* result_in_b);
+// Identifiers and the radix sort (sort.cu).
+struct SortPlan {
+    int passes;   // digit positions
+    int bits;     // bits per digit (<= 9)
+    int buckets;  // 1 << bits
+    int tile;     // keys per onesweep tile
+    int tiles;
+};
+SortPlan sort_plan(int n, int key_words, int key_bits);
+size_t radix_tmp_ints(int n, int key_words, int key_bits);
+// Computes the keys (Eq. 1, packed) and values (input index) into keys_a /
+// vals_a, with the histogram of every digit position (into tmp).
+cudaError_t quantise_hist(const int* X, const Params& p, void* keys_a, int* vals_a, int* tmp, cudaStream_t st);
+// The onesweep passes: sorts (keys_a, vals_a) stably by key; *result_in_b
+// tells which buffer pair holds the result.  err receives kDevTimeout if a
+// look-back gave up.  tmp must still hold what quantise_hist left there.
+cudaError_t sort_passes(const Params& p, void* keys_a, int* vals_a, void* keys_b, int* vals_b, int* tmp, unsigned* err,
+                        cudaStream_t st, int* result_in_b);
 size_t compact_tmp_ints(int n);
 cudaError_t launch_compact(const Params& p, const int* X, const void* keys, const int* vals, int* tmp,
                            int* cell_start, int* cell_coord, int* pt_cell, int* Xs, int* num_cells,

@@ -1,5 +1,6 @@
-// Grid construction: bounds, identifiers (Eq. 1), LSD radix sort and the
-// non-empty-grid compaction of Alg. 1, plus a device-wide exclusive scan.
+// Grid construction: bounds (mn_j of Eq. 1) and the non-empty-grid
+// compaction of Alg. 1, plus a device-wide exclusive scan.  The identifiers
+// and the sort are in sort.cu.
 #include <climits>
 
 #include "gd_internal.cuh"
@@ -142,269 +143,6 @@ cudaError_t launch_bounds(const int* X, int n, int d, int* mnmx, cudaStream_t st
     bounds_kernel<<<blocks, 256, 0, st>>>(X, n, d, mnmx);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------- quantise
-
-__device__ __forceinline__ unsigned identifier(int x, int mn, long long s) {
-    // (x - mn) fits in 32 unsigned bits; an identifier is at most 2^31 - 1
-    // because d * range^2 < 2^62 is checked before this runs.
-    unsigned long long diff = (unsigned)(x - mn);
-    return (unsigned)(diff / (unsigned long long)s);
-}
-
-__global__ void __launch_bounds__(256) quantise1_kernel(const int* __restrict__ X, Params p,
-                                                        unsigned long long* __restrict__ keys,
-                                                        int* __restrict__ vals) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        const int* row = X + i * p.d;
-        unsigned long long k = 0;
-#pragma unroll
-        for (int j = 0; j < kMaxD; ++j)
-            if (j < p.d) k |= (unsigned long long)identifier(__ldg(row + j), p.mn[j], p.s) << p.shift[j];
-        keys[i] = k;
-        vals[i] = (int)i;
-    }
-}
-
-__device__ __forceinline__ void or_shifted(Key2& k, unsigned long long v, int sh) {
-    if (sh >= 64) {
-        k.hi |= v << (sh - 64);
-    } else {
-        k.lo |= v << sh;
-        if (sh > 0) k.hi |= v >> (64 - sh);
-    }
-}
-
-__global__ void __launch_bounds__(256) quantise2_kernel(const int* __restrict__ X, Params p, Key2* __restrict__ keys,
-                                                        int* __restrict__ vals) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        const int* row = X + i * p.d;
-        Key2 k{0ull, 0ull};
-#pragma unroll
-        for (int j = 0; j < kMaxD; ++j)
-            if (j < p.d) or_shifted(k, identifier(__ldg(row + j), p.mn[j], p.s), p.shift[j]);
-        keys[i] = k;
-        vals[i] = (int)i;
-    }
-}
-
-cudaError_t launch_quantise(const int* X, const Params& p, void* keys, int* vals, cudaStream_t st) {
-    int blocks = (p.n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (p.key_words == 1)
-        quantise1_kernel<<<blocks, 256, 0, st>>>(X, p, (unsigned long long*)keys, vals);
-    else
-        quantise2_kernel<<<blocks, 256, 0, st>>>(X, p, (Key2*)keys, vals);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------ radix sort
-// Stable LSD sort over 8-bit digits.  Per pass: a per-tile digit histogram
-// (digit-major table), an exclusive scan of the table, and a scatter that
-// ranks each tile stably in shared memory (warp match + per-warp counters)
-// and then writes digit runs out contiguously.
-
-constexpr int kRadixBits = 8;
-constexpr int kBuckets = 1 << kRadixBits;
-constexpr int kSortBlock = 256;
-constexpr int kSortWarps = kSortBlock / 32;
-
-template <typename K> struct KeyTraits;
-template <> struct KeyTraits<unsigned long long> {
-    static constexpr int kItems = 16;
-    __device__ static __forceinline__ unsigned digit(unsigned long long k, int sh) {
-        return (unsigned)(k >> sh) & (kBuckets - 1);
-    }
-};
-template <> struct KeyTraits<Key2> {
-    static constexpr int kItems = 8;
-    __device__ static __forceinline__ unsigned digit(const Key2& k, int sh) {
-        unsigned long long v;
-        if (sh >= 64) {
-            v = k.hi >> (sh - 64);
-        } else {
-            v = k.lo >> sh;
-            if (sh > 64 - kRadixBits) v |= k.hi << (64 - sh);
-        }
-        return (unsigned)v & (kBuckets - 1);
-    }
-};
-
-template <typename K> constexpr int sort_tile() { return kSortBlock * KeyTraits<K>::kItems; }
-
-size_t radix_tmp_ints(int n, int key_words) {
-    const int tile = key_words == 1 ? sort_tile<unsigned long long>() : sort_tile<Key2>();
-    const long long tiles = (n + tile - 1) / tile;
-    const long long table = tiles * kBuckets;
-    return (size_t)(table + 1) + scan_tmp_ints(table);
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kSortBlock) radix_hist_kernel(const K* __restrict__ keys, int n, int shift,
-                                                                int* __restrict__ table, int tiles) {
-    constexpr int kItems = KeyTraits<K>::kItems;
-    __shared__ int h[kSortWarps][kBuckets];
-    const int warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kSortWarps * kBuckets; i += kSortBlock) (&h[0][0])[i] = 0;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * sort_tile<K>();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        long long k = base + i * kSortBlock + threadIdx.x;
-        if (k < n) atomicAdd(&h[warp][KeyTraits<K>::digit(keys[k], shift)], 1);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kBuckets; b += kSortBlock) {
-        int s = 0;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) s += h[w][b];
-        table[(long long)b * tiles + blockIdx.x] = s;
-    }
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kSortBlock) radix_scatter_kernel(const K* __restrict__ keys_in,
-                                                                   const int* __restrict__ vals_in,
-                                                                   K* __restrict__ keys_out, int* __restrict__ vals_out,
-                                                                   int n, int shift, const int* __restrict__ table,
-                                                                   int tiles) {
-    constexpr int kItems = KeyTraits<K>::kItems;
-    constexpr int kTile = sort_tile<K>();
-    constexpr int kExchBytes = kTile * (sizeof(K) > sizeof(int) ? sizeof(K) : sizeof(int));
-    __shared__ __align__(16) unsigned char exch[kExchBytes];
-    __shared__ int wcount[kSortWarps][kBuckets];
-    __shared__ int dstart[kBuckets];  // first tile-local position of each digit
-    __shared__ int goff[kBuckets];    // global offset of this tile's run of each digit
-    __shared__ int sm[33];
-
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
-    const long long base = (long long)blockIdx.x * kTile;
-    const int count = (int)min((long long)kTile, (long long)n - base);
-
-    for (int i = threadIdx.x; i < kSortWarps * kBuckets; i += kSortBlock) (&wcount[0][0])[i] = 0;
-    for (int b = threadIdx.x; b < kBuckets; b += kSortBlock) goff[b] = table[(long long)b * tiles + blockIdx.x];
-    __syncthreads();
-
-    // Warp w owns the consecutive items [w*32*kItems, (w+1)*32*kItems) of the
-    // tile; item i of lane l is at w*32*kItems + i*32 + l (index order).
-    K key[kItems];
-    int rank[kItems];
-    unsigned dig[kItems];
-    const int wbase = warp * 32 * kItems;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        const bool valid = t < count;
-        if (valid) key[i] = keys_in[base + t];
-        dig[i] = valid ? KeyTraits<K>::digit(key[i], shift) : (unsigned)(kBuckets + lane);
-        const unsigned peers = __match_any_sync(kFull, dig[i]);
-        int before = 0;
-        if (valid) before = wcount[warp][dig[i]];
-        __syncwarp();
-        if (valid && lane == (int)(__ffs(peers) - 1)) wcount[warp][dig[i]] = before + __popc(peers);
-        __syncwarp();
-        rank[i] = before + __popc(peers & lanemask_lt());
-    }
-    __syncthreads();
-
-    // Per digit: exclusive prefix over warps, then over digits.
-    int tot = 0;
-    if (threadIdx.x < kBuckets) {
-        const int b = threadIdx.x;
-#pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            int c = wcount[w][b];
-            wcount[w][b] = tot;
-            tot += c;
-        }
-    }
-    int all;
-    int ex = block_exclusive_scan(threadIdx.x < kBuckets ? tot : 0, sm, &all);
-    if (threadIdx.x < kBuckets) dstart[threadIdx.x] = ex;
-    __syncthreads();
-
-    // Keys through shared memory into tile-local digit order, then out.
-    K* skeys = reinterpret_cast<K*>(exch);
-    int pos[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        if (t < count) {
-            pos[i] = dstart[dig[i]] + wcount[warp][dig[i]] + rank[i];
-            skeys[pos[i]] = key[i];
-        }
-    }
-    __syncthreads();
-    int dst[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = i * kSortBlock + threadIdx.x;
-        if (t < count) {
-            K k = skeys[t];
-            unsigned b = KeyTraits<K>::digit(k, shift);
-            dst[i] = goff[b] + (t - dstart[b]);
-            keys_out[dst[i]] = k;
-        }
-    }
-    __syncthreads();
-    int* svals = reinterpret_cast<int*>(exch);
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        if (t < count) svals[pos[i]] = vals_in[base + t];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = i * kSortBlock + threadIdx.x;
-        if (t < count) vals_out[dst[i]] = svals[t];
-    }
-}
-
-template <typename K>
-static cudaError_t radix_sort_t(K* ka, int* va, K* kb, int* vb, int n, int key_bits, int* tmp, cudaStream_t st,
-                                int* result_in_b) {
-    constexpr int kTile = sort_tile<K>();
-    const int tiles = (n + kTile - 1) / kTile;
-    const long long table_n = (long long)tiles * kBuckets;
-    int* table = tmp;
-    int* scan_tmp = tmp + table_n + 1;
-    K* src_k = ka;
-    int* src_v = va;
-    K* dst_k = kb;
-    int* dst_v = vb;
-    int flips = 0;
-    for (int shift = 0; shift < key_bits; shift += kRadixBits) {
-        radix_hist_kernel<K><<<tiles, kSortBlock, 0, st>>>(src_k, n, shift, table, tiles);
-        GD_COUNT_LAUNCH();
-        cudaError_t e = scan_exclusive(table, table, table_n, scan_tmp, st);
-        if (e != cudaSuccess) return e;
-        radix_scatter_kernel<K><<<tiles, kSortBlock, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, table, tiles);
-        GD_COUNT_LAUNCH();
-        K* tk = src_k;
-        src_k = dst_k;
-        dst_k = tk;
-        int* tv = src_v;
-        src_v = dst_v;
-        dst_v = tv;
-        flips ^= 1;
-    }
-    *result_in_b = flips;
-    return cudaGetLastError();
-}
-
-cudaError_t radix_sort(void* keys_a, int* vals_a, void* keys_b, int* vals_b, int n, int key_words, int key_bits,
-                       int* tmp, cudaStream_t st, int* result_in_b) {
-    *result_in_b = 0;
-    if (n <= 1 || key_bits <= 0) return cudaSuccess;
-    if (key_words == 1)
-        return radix_sort_t((unsigned long long*)keys_a, vals_a, (unsigned long long*)keys_b, vals_b, n, key_bits,
-                            tmp, st, result_in_b);
-    return radix_sort_t((Key2*)keys_a, vals_a, (Key2*)keys_b, vals_b, n, key_bits, tmp, st, result_in_b);
 }
 
 // ------------------------------------------------------------ compaction

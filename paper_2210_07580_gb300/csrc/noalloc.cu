@@ -166,15 +166,17 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_TAKE(parent, int*, N * 4);
     NA_TAKE(cid_root, int*, N * 4);
     NA_TAKE(cell_cid, int*, N * 4);
-    size_t t = radix_tmp_ints(n, p.key_words);
+    size_t t = radix_tmp_ints(n, p.key_words, p.key_bits);
     if (compact_tmp_ints(n) > t) t = compact_tmp_ints(n);
     if (levels_tmp_ints(n, d) > t) t = levels_tmp_ints(n, d);
     if (scan_tmp_ints((long long)n + 1) > t) t = scan_tmp_ints((long long)n + 1);
     NA_TAKE(tmp, int*, t * 4);
 
-    NA_CUDA(launch_quantise(X, p, keyA, valA, st));
+    // the status word starts at zero on every call (the array keeps old contents)
+    NA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
     int in_b = 0;
-    NA_CUDA(radix_sort(keyA, valA, keyB, valB, n, p.key_words, p.key_bits, tmp, st, &in_b));
+    NA_CUDA(quantise_hist(X, p, keyA, valA, tmp, st));
+    NA_CUDA(sort_passes(p, keyA, valA, keyB, valB, tmp, status, st, &in_b));
     void* keys = in_b ? keyB : keyA;
     int* perm = in_b ? valB : valA;
     NA_CUDA(launch_compact(p, X, keys, perm, tmp, cell_start, cell_coord, pt_cell, Xs, num_cells, st));
@@ -207,8 +209,6 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_CUDA(scan_exclusive(pair_start_f, pair_start_f, C, tmp, st));
     NA_CUDA(launch_pair_fill(p, nbr_start, nbr, core_start, cell_coord, C, pair_start, pair_start_f, pairs, st));
 
-    // the status word starts at zero on every call (the array keeps old contents)
-    NA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
     NA_CUDA(launch_uf_init(parent, C, st));
     NA_CUDA(launch_merge_ranges(pair_start, pair_start_f, C, mrange, hard_cnt, st));
     for (int wave = 0; wave < 2; ++wave)
