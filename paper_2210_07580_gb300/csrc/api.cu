@@ -329,10 +329,12 @@ gd_status run(gd_ctx* ctx, const int32_t* X, int64_t n64, int d, int64_t eps2, i
     GD_TRY(ensure(ctx, ctx->mscratch, (size_t)merge_fm_blocks() * 2 * wpb * 4, st));
     GD_CUDA(launch_uf_init(w.parent, C, st));
     GD_CUDA(launch_merge_ranges(w.pair_start, w.pair_start_f, C, ctx->small + kRange, ctx->small + kHardCnt, st));
-    for (int wave = 0; wave < 2; ++wave)
+    for (int wave = 0; wave < 2; ++wave) {
         GD_CUDA(launch_merge_wave(p, wave, pairs, ctx->small + kRange, (int)nnbr, w.Xc, w.core_start, w.bbox, w.parent,
                                   (unsigned*)(ctx->small + kStatus), hard, ctx->small + kHardCnt,
-                                  (unsigned*)ctx->mscratch.ptr, wpb, st));
+                                  (unsigned*)ctx->mscratch.ptr, wpb, merge_fm_blocks(), st));
+        if (wave == 0) GD_CUDA(launch_uf_flatten(w.parent, C, (unsigned*)(ctx->small + kStatus), st));
+    }
 
     // --- cluster ids, border points, labels
     mark(10);

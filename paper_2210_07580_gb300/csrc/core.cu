@@ -31,8 +31,34 @@ __global__ void nonfull_count_kernel(int minpts, const int* __restrict__ cell_st
 //   - box entirely beyond eps: skipped;
 //   - otherwise its points are tested one by one (the straddling grids'
 //     points are streamed as one flat sequence, lane k taking the k-th).
-// g itself is always entirely within eps (its diameter is <= eps).  The warp
-// stops as soon as the count reaches MinPts.
+// g itself is always entirely within eps (its diameter is <= eps).  Whole
+// grids are counted first; straddling grids are then scanned -- for short
+// neighbour lists in three bands of increasing box distance (up to eps/4,
+// eps/2, eps), so that a core point usually reaches MinPts among the nearest
+// points.  The warp stops as soon as the count reaches MinPts.
+struct BoxDist {
+    long long mind, maxd;
+};
+
+template <int D>
+__device__ __forceinline__ BoxDist box_dist(const long long* x, const int* __restrict__ coord, int cc,
+                                            const Params& p) {
+    BoxDist r{0, 0};
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const long long blo = (long long)p.mn[j] + (long long)coord[(long long)cc * D + j] * p.s;
+        const long long bhi = blo + p.s - 1;
+        long long g = 0;
+        if (blo > x[j]) g = blo - x[j];
+        else if (x[j] > bhi) g = x[j] - bhi;
+        r.mind += g * g;
+        const long long a = x[j] - blo, b = bhi - x[j];
+        const long long f = a > b ? a : b;
+        r.maxd += f * f;
+    }
+    return r;
+}
+
 template <int D, int DP>
 __global__ void __launch_bounds__(256) core_point_kernel(Params p, const int* __restrict__ Xs,
                                                          const int* __restrict__ cell_start,
@@ -43,7 +69,7 @@ __global__ void __launch_bounds__(256) core_point_kernel(Params p, const int* __
                                                          unsigned char* __restrict__ core_s) {
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long eps2 = p.eps2, s = p.s;
+    const long long eps2 = p.eps2;
     const int minpts = p.minpts;
     const int total = nf_start[C];
     for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
@@ -63,65 +89,63 @@ __global__ void __launch_bounds__(256) core_point_kernel(Params p, const int* __
         for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];
         int cnt = 0;
         const int t_begin = nbr_start[c], t_end = nbr_start[c + 1];
+        // whole grids
         for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
-            const int nb = min(32, t_end - t0);
-            int st = 0, sz = 0, whole = 0;
-            if (lane < nb) {
+            int whole = 0;
+            if (t0 + lane < t_end) {
                 const int cc = nbr[t0 + lane];
-                long long mind = 0, maxd = 0;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    const long long blo = (long long)p.mn[j] + (long long)coord[(long long)cc * D + j] * s;
-                    const long long bhi = blo + s - 1;
-                    long long g = 0;
-                    if (blo > x[j]) g = blo - x[j];
-                    else if (x[j] > bhi) g = x[j] - bhi;
-                    mind += g * g;
-                    const long long a = x[j] - blo, b = bhi - x[j];
-                    const long long f = a > b ? a : b;
-                    maxd += f * f;
-                }
-                const int b0 = cell_start[cc], m = cell_start[cc + 1] - b0;
-                if (maxd <= eps2) {
-                    whole = m;
-                } else if (mind <= eps2) {
-                    st = b0;
-                    sz = m;
-                }
+                const BoxDist bd = box_dist<D>(x, coord, cc, p);
+                if (bd.maxd <= eps2) whole = cell_start[cc + 1] - cell_start[cc];
             }
-            int add = whole;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(kFull, add, o);
-            cnt += add;
-            if (cnt >= minpts) break;
-            const int incl = warp_inclusive_scan(sz);
-            const int flat = __shfl_sync(kFull, incl, 31);
-            for (int k0 = 0; k0 < flat; k0 += 32) {
-                const int k = k0 + lane;
-                int lo2 = 0, hi2 = 31;
-#pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if (__shfl_sync(kFull, incl, mid) > k)
-                        hi2 = mid;
-                    else
-                        lo2 = mid + 1;
-                }
-                const int gst = __shfl_sync(kFull, st, lo2);
-                const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
-                bool hit = false;
-                if (k < flat) {
-                    const long long qi = (long long)gst + (k - gex);
-                    long long dd = 0;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const long long t = (long long)Xs[qi * DP + j] - x[j];
-                        dd += t * t;
+            for (int o = 16; o > 0; o >>= 1) whole += __shfl_xor_sync(kFull, whole, o);
+            cnt += whole;
+        }
+        // straddling grids, nearest band first when the list is short (dense
+        // neighbourhoods: few grids, many points each); one pass otherwise
+        const int nbands = (t_end - t_begin) <= 128 ? 3 : 1;
+        for (int band = 0; band < nbands && cnt < minpts; ++band) {
+            const long long blo = band == 0 ? -1 : (band == 1 ? eps2 / 16 : eps2 / 4);
+            const long long bhi = nbands == 1 ? eps2 : (band == 0 ? eps2 / 16 : (band == 1 ? eps2 / 4 : eps2));
+            for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
+                int st = 0, sz = 0;
+                if (t0 + lane < t_end) {
+                    const int cc = nbr[t0 + lane];
+                    const BoxDist bd = box_dist<D>(x, coord, cc, p);
+                    if (bd.maxd > eps2 && bd.mind > blo && bd.mind <= bhi) {
+                        st = cell_start[cc];
+                        sz = cell_start[cc + 1] - st;
                     }
-                    hit = dd <= eps2;
                 }
-                cnt += __popc(__ballot_sync(kFull, hit));
-                if (cnt >= minpts) break;
+                const int incl = warp_inclusive_scan(sz);
+                const int flat = __shfl_sync(kFull, incl, 31);
+                for (int k0 = 0; k0 < flat; k0 += 32) {
+                    const int k = k0 + lane;
+                    int lo2 = 0, hi2 = 31;
+#pragma unroll
+                    for (int step = 0; step < 5; ++step) {
+                        const int mid = (lo2 + hi2) >> 1;
+                        if (__shfl_sync(kFull, incl, mid) > k)
+                            hi2 = mid;
+                        else
+                            lo2 = mid + 1;
+                    }
+                    const int gst = __shfl_sync(kFull, st, lo2);
+                    const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
+                    bool hit = false;
+                    if (k < flat) {
+                        const long long qi = (long long)gst + (k - gex);
+                        long long dd = 0;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const long long t = (long long)Xs[qi * DP + j] - x[j];
+                            dd += t * t;
+                        }
+                        hit = dd <= eps2;
+                    }
+                    cnt += __popc(__ballot_sync(kFull, hit));
+                    if (cnt >= minpts) break;
+                }
             }
         }
         if (lane == 0) core_s[i] = cnt >= minpts ? 1 : 0;

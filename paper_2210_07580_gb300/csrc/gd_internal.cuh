@@ -183,14 +183,17 @@ cudaError_t launch_pair_fill(const Params& p, const int* nbr_start, const int* n
 cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, int* range, int* hard_cnt,
                                 cudaStream_t st);
 cudaError_t launch_uf_init(int* parent, int C, cudaStream_t st);
-// Blocks of the FastMerging kernel; each owns 2 * wpb words of `scratch`,
-// wpb = ceil(largest grid / 32).
+// Points every grid at its union-find root (no unions may run concurrently).
+cudaError_t launch_uf_flatten(int* parent, int C, unsigned* status, cudaStream_t st);
+// Default number of FastMerging blocks; each block owns 2 * wpb words of
+// `scratch`, wpb = ceil(largest grid / 32) + 1.
 int merge_fm_blocks();
 // One merge wave (0: touching pairs, 1: the others): warp-level test of every
 // pair in range[2*wave .. 2*wave+1], then FastMerging of the pairs it hands on.
 cudaError_t launch_merge_wave(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
                               const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
-                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, cudaStream_t st);
+                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, int fm_blocks,
+                              cudaStream_t st);
 
 // Labels (label.cu).
 cudaError_t launch_cluster_ids(const Params& p, int* parent, const int* core_start, const int* cell_start,

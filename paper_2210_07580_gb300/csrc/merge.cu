@@ -270,11 +270,13 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 //   2. the two box tests;
 //   3. the exact test over core points in 32 x 32 tiles (lane l holds a point
 //      of s_j, points of s_i are broadcast), stopping at the first pair within
-//      eps.  Small pairs (m_i * m_j <= kExhaustive) are decided here in full;
-//      larger ones get `budget` diagonal tiles (distinct chunks of both sets),
-//      which finds a witness for nearly every pair that has many, and are
-//      otherwise handed to the block-level FastMerging kernel.
-constexpr long long kExhaustive = 8 * 1024;
+//      eps.  Pairs of two small sets (both at most kSmallSet points) are
+//      decided here in full (at most 16 tiles); any other pair gets `budget`
+//      diagonal tiles (distinct chunks of both sets), which finds a witness
+//      for nearly every pair that has many, and is otherwise handed to the
+//      block-level FastMerging kernel -- in particular a few points against
+//      thousands, where one scan of the large set usually decides.
+constexpr int kSmallSet = 128;
 
 template <int D, int DP>
 __global__ void __launch_bounds__(256) merge_warp_kernel(Params p, const int2* __restrict__ pairs,
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(Params p, const int2* _
             const int aj = core_start[pr.y], mj = core_start[pr.y + 1] - aj;
             const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
             const long long tiles = (long long)na * nb;
-            const bool exhaustive = (long long)mi * mj <= kExhaustive;
+            const bool exhaustive = mi <= kSmallSet && mj <= kSmallSet;
             const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
             for (long long t = 0; t < limit; ++t) {
                 const int ta = exhaustive ? (int)(t / nb) : (int)(t % na);
@@ -487,10 +489,17 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
         __syncthreads();
         if (same) continue;
 
-        const int* A = Xc + (long long)core_start[pr.x] * DP;
-        const int* B = Xc + (long long)core_start[pr.y] * DP;
-        const int ma = core_start[pr.x + 1] - core_start[pr.x];
-        const int mb = core_start[pr.y + 1] - core_start[pr.y];
+        // s_i is the smaller set: each round removes at least its pivot, and
+        // a small set is usually emptied by the first pruning
+        int gi = pr.x, gj = pr.y;
+        if (core_start[gi + 1] - core_start[gi] > core_start[gj + 1] - core_start[gj]) {
+            gi = pr.y;
+            gj = pr.x;
+        }
+        const int* A = Xc + (long long)core_start[gi] * DP;
+        const int* B = Xc + (long long)core_start[gj] * DP;
+        const int ma = core_start[gi + 1] - core_start[gi];
+        const int mb = core_start[gj + 1] - core_start[gj];
         const int wa = (ma + 31) >> 5, wb = (mb + 31) >> 5;
         for (int w = threadIdx.x; w < wa; w += kFmBlock)
             live_a[w] = (w < wa - 1 || (ma & 31) == 0) ? 0xffffffffu : ((1u << (ma & 31)) - 1u);
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
         __syncthreads();
 
         long long piv[D], tgt[D];
-        const int* bj = bbox + (long long)pr.y * 2 * D;
+        const int* bj = bbox + (long long)gj * 2 * D;
 #pragma unroll
         for (int j = 0; j < D; ++j) tgt[j] = ((long long)bj[j] + bj[D + j]) / 2;
         int cnt;
@@ -541,6 +550,24 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
     }
 }
 
+// Between the waves: point every grid at its root, so that the second wave's
+// precheck costs two loads per pair.
+__global__ void uf_flatten_kernel(int* parent, int C, unsigned* status) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int r = uf_find(parent, c);
+    if (r < 0)
+        atomicOr(status, kDevTimeout);
+    else if (r != c)
+        parent[c] = r;
+}
+
+cudaError_t launch_uf_flatten(int* parent, int C, unsigned* status, cudaStream_t st) {
+    uf_flatten_kernel<<<(C + 255) / 256, 256, 0, st>>>(parent, C, status);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 template <int D>
 static void merge_waves_launch(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
                                const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
@@ -552,20 +579,20 @@ static void merge_waves_launch(const Params& p, int wave, const int2* pairs, con
     if (blocks < 1) blocks = 1;
     const int* r = range + 2 * wave;
     merge_warp_kernel<D, DP><<<(int)blocks, 256, 0, st>>>(p, pairs, r, Xc, core_start, bbox, parent, status, hard,
-                                                          hard_cnt + wave, 4);
+                                                          hard_cnt + wave, 2);
     GD_COUNT_LAUNCH();
     merge_block_kernel<D, DP><<<fm_blocks, kFmBlock, 0, st>>>(p, hard, r, hard_cnt + wave, Xc, core_start, bbox,
                                                               parent, status, scratch, wpb);
     GD_COUNT_LAUNCH();
 }
 
-int merge_fm_blocks() { return 152 * 4; }
+int merge_fm_blocks() { return 152 * 8; }
 
 cudaError_t launch_merge_wave(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
                               const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
-                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, cudaStream_t st) {
+                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, int fm_blocks, cudaStream_t st) {
     if (max_pairs <= 0) return cudaSuccess;
-    const int fb = merge_fm_blocks();
+    const int fb = fm_blocks;
     switch (p.d) {
 #define GD_WAVE(DD) \
     case DD: merge_waves_launch<DD>(p, wave, pairs, range, max_pairs, Xc, core_start, bbox, parent, status, hard, hard_cnt, scratch, wpb, fb, st); break;

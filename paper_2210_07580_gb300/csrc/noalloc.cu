@@ -197,7 +197,8 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
     NA_TAKE(nbr, int*, (size_t)nnbr * 4 + 16);
     NA_TAKE(pairs, int2*, (size_t)nnbr * 8 + 16);
     NA_TAKE(hard, int2*, (size_t)nnbr * 8 + 16);
-    NA_TAKE(mscratch, unsigned*, (size_t)merge_fm_blocks() * 2 * wpb * 4);
+    const int fm_blocks = 152;  // fewer FastMerging blocks: their bitmaps come out of the static array
+    NA_TAKE(mscratch, unsigned*, (size_t)fm_blocks * 2 * wpb * 4);
     NA_CUDA(launch_walk_fill(p, cell_coord, C, lv, nbr_start, nbr, st));
 
     NA_CUDA(launch_core(p, Xs, cell_start, pt_cell, cell_coord, C, nbr_start, nbr, pair_start, tmp, core_s, st));
@@ -211,9 +212,11 @@ gd_status run_noalloc(char* base, const int32_t* X, int n, int d, long long eps2
 
     NA_CUDA(launch_uf_init(parent, C, st));
     NA_CUDA(launch_merge_ranges(pair_start, pair_start_f, C, mrange, hard_cnt, st));
-    for (int wave = 0; wave < 2; ++wave)
+    for (int wave = 0; wave < 2; ++wave) {
         NA_CUDA(launch_merge_wave(p, wave, pairs, mrange, (int)nnbr, Xc, core_start, bbox, parent, status, hard,
-                                  hard_cnt, mscratch, wpb, st));
+                                  hard_cnt, mscratch, wpb, fm_blocks, st));
+        if (wave == 0) NA_CUDA(launch_uf_flatten(parent, C, status, st));
+    }
     NA_CUDA(launch_cluster_ids(p, parent, core_start, cell_start, core_s, perm, C, cid_root, cell_cid, st, status));
     NA_CUDA(launch_labels(p, Xs, cell_start, pt_cell, core_s, nbr_start, nbr, core_start, Xc, bbox, cell_cid, perm,
                           labels, is_core, st));

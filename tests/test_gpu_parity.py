@@ -206,3 +206,35 @@ def test_full_size_workloads(ctx, name):
     got = run_gpu(ctx, X, eps2, minpts)
     want = oracle.grid(X, eps2, minpts)
     assert_same(got, want, name)
+
+
+@pytest.mark.parametrize("gap_extra,d", [(0, 2), (1, 2), (0, 3), (1, 3)])
+def test_dense_slabs_rare_or_no_witness(ctx, gap_extra, d):
+    """Two dense slabs whose facing grids are neighbours: with the gap equal to
+    eps exactly one planted pair of points is a witness (merge), with eps + 1
+    there is none.  Large core sets on both sides drive the pairs past the
+    warp's tile budget into FastMerging, which must prove 'no' exactly or find
+    the one witness."""
+    rng = np.random.default_rng(100 + 10 * d + gap_extra)
+    eps = 300
+    n_side = 60000
+    A = rng.integers(0, 3000, size=(n_side, d))
+    A[:, 0] = rng.integers(0, 2001, size=n_side)
+    B = rng.integers(0, 3000, size=(n_side, d))
+    B[:, 0] = rng.integers(0, 2001, size=n_side) + 2000 + eps + gap_extra + 1
+    # keep the facing faces sparse except for the planted pair
+    A = A[A[:, 0] < 1990]
+    B = B[B[:, 0] > 2000 + eps + gap_extra + 11]
+    pa = np.zeros((1, d), np.int64)
+    pa[0, 0] = 2000
+    pa[0, 1:] = 1500
+    pb = pa.copy()
+    pb[0, 0] = 2000 + eps + gap_extra
+    X = np.ascontiguousarray(np.vstack([A, B, pa, pb, A[:5] + 1]).astype(np.int32))
+    X = np.ascontiguousarray(X[rng.permutation(len(X))])
+    eps2 = eps * eps
+    want = oracle.grid(X, eps2, 5, merge="fastmerging")
+    got = run_gpu(ctx, X, eps2, 5)
+    assert_same(got, want, f"slabs d={d} gap_extra={gap_extra}")
+    # the planted points must be core for the test to mean anything
+    assert want[1].sum() > 0.9 * len(X)
