@@ -98,6 +98,18 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total
     return res;
 }
 
+// Linking priority of a union-find root: a bijective 32-bit mix of the index
+// (the murmur3 finaliser), so distinct roots never tie.
+__device__ __forceinline__ unsigned uf_priority(int x) {
+    unsigned h = (unsigned)x;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
 // Union-find root with path halving; -1 if the retry cap is reached.  Parents
 // are read through L2 (other SMs link roots concurrently) and every halving
 // store writes an ancestor, so concurrent finds and unions stay consistent.

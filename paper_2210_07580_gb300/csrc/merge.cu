@@ -208,9 +208,13 @@ cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, i
 }
 
 // ------------------------------------------------------------ union-find
-// Roots are always linked under the smaller index (atomicCAS on the root),
-// and finds halve paths with plain stores: every stored parent is an
-// ancestor, so concurrent halving never breaks a path.
+// Of two roots, the one with the lower priority is linked under the other
+// (atomicCAS on the root), and finds halve paths with plain stores: every
+// stored parent is an ancestor, so concurrent halving never breaks a path.
+// The priority is a fixed bijective hash of the index, not the index itself:
+// grids are in lexicographic order, so index-ordered linking builds long
+// chains along clusters, while a random-looking order keeps trees shallow.
+// (Cluster ids do not depend on which grid ends up the root.)
 
 __global__ void uf_init_kernel(int* parent, int C) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,12 +234,12 @@ __device__ __forceinline__ bool uf_union(int* parent, int a, int b) {
         b = uf_find(parent, b);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
-        if (a > b) {
+        if (uf_priority(a) < uf_priority(b)) {
             const int t = a;
             a = b;
             b = t;
         }
-        // link root b under root a
+        // link root b (lower priority) under root a
         if (atomicCAS(parent + b, b, a) == b) return true;
     }
     return false;
