@@ -155,6 +155,51 @@ def run_reference(args):
     return 0
 
 
+def bench_batched(ctx, dev, args):
+    """Batched vs looped throughput (inst/s) on the 256-instance workload,
+    same GPU, same context; the labels of both paths must be identical."""
+    import torch
+    from paper_2210_07580_gb300 import synth
+    jobs = synth.batch_instances(args.batch_k, seed=7)
+    djobs = [(torch.from_numpy(X).to(dev), e, m) for X, e, m in jobs]
+    outs_b = [(torch.empty(len(X), dtype=torch.int32, device=dev), torch.empty(len(X), dtype=torch.uint8, device=dev))
+              for X, _, _ in jobs]
+    outs_l = [(torch.empty(len(X), dtype=torch.int32, device=dev), torch.empty(len(X), dtype=torch.uint8, device=dev))
+              for X, _, _ in jobs]
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        ctx.dbscan_batched(djobs, outputs=outs_b, stream=stream)
+
+    def looped():
+        for (Xd, e, m), (lab, core) in zip(djobs, outs_l):
+            ctx.dbscan(Xd, e, m, labels=lab, is_core=core, stream=stream)
+
+    res = {}
+    for name, fn in (("batched", batched), ("looped", looped)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        res[name] = min(ts)
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) for a, b in zip(outs_b, outs_l))
+    k = len(jobs)
+    return {"workload": f"{k} instances: n log-uniform in [1e3, 5e5], d in {{2,3,5,7}}, eps in [200, 2000], "
+                        f"MinPts in {{5,10,50,100}}, blobs + 5% noise",
+            "points": int(sum(len(X) for X, _, _ in jobs)),
+            "batched_inst_per_s": round(k / (res["batched"] / 1e3), 1),
+            "looped_inst_per_s": round(k / (res["looped"] / 1e3), 1),
+            "batched_ms": round(res["batched"], 3), "looped_ms": round(res["looped"], 3),
+            "speedup": round(res["looped"] / res["batched"], 2), "labels_identical": bool(same)}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -269,6 +314,8 @@ def run_gpu(args):
                          "launches_per_step": passes},
             "wall_s_timed": round(t_wall, 3),
         }
+        if not args.no_batch:
+            line["batched"] = bench_batched(ctx, dev, args)
         if not args.no_cpu_baseline and ws == 1:
             t, ns, thr = time_oracle(args.workload, 1, args.cpu_sample)
             line["cpu_baseline"] = {"value": round(ns / t / 1e6, 3), "unit": "Mpts/s", "cores": thr,
@@ -294,6 +341,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="points of the workload the CPU oracle times (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched vs looped measurement")
+    ap.add_argument("--batch-k", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

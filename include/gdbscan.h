@@ -88,6 +88,34 @@ gd_status gd_dbscan_host(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, i
                          int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
                          gd_stream_t stream);
 
+/* One instance of a batch: device pointers and parameters as for gd_dbscan. */
+typedef struct {
+    const int32_t *X;  /* [n][d] row-major, device */
+    int64_t n;
+    int d;
+    int64_t eps2;
+    int32_t minpts;
+    int32_t *labels;   /* [n], device */
+    uint8_t *is_core;  /* [n], device, or NULL */
+} gd_instance;
+
+/* Exact DBSCAN of k independent instances (uneven sizes, dimensions and
+ * parameters) in one batch: every stage of the pipeline is one launch per
+ * group of instances (grouped by dimension or key width) covering all of
+ * them, and the host synchronises with `stream` a fixed handful of times per
+ * batch instead of per instance.  Each instance's result equals gd_dbscan's
+ * on it alone.  `inst` is a host array of k records; k == 0 is a no-op.  On
+ * error the outputs of every instance are unspecified and gd_last_error
+ * names the failing instance. */
+gd_status gd_dbscan_batched(gd_ctx *ctx, int k, const gd_instance *inst, gd_stream_t stream);
+
+/* Device bytes the context currently holds (workspace kept for reuse). */
+size_t gd_ctx_bytes(const gd_ctx *ctx);
+
+/* Release the context's cached device and pinned host buffers (they are
+ * allocated again on the next call).  Waits for the context's last work. */
+gd_status gd_ctx_trim(gd_ctx *ctx);
+
 /* Static text for a status code. */
 const char *gd_status_str(gd_status s);
 

@@ -5,5 +5,5 @@ C ABI of include/gdbscan.h); ``binding`` marshals arguments to it.  Importing
 this package does not load the library; the first call does, and raises if
 the library has not been built.
 """
-from .binding import (Context, GdError, dbscan, eps2_from_eps, load_library,  # noqa: F401
+from .binding import (Context, GdError, GdInstance, dbscan, eps2_from_eps, load_library,  # noqa: F401
                       workspace_bytes)

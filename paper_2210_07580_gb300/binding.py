@@ -20,6 +20,12 @@ GD_OK, GD_EINVAL, GD_ERANGE, GD_ENOMEM, GD_ECUDA, GD_ETIMEOUT, GD_EBUSY = range(
 VIEW_PERM, VIEW_CELL_START, VIEW_CELL_COORD, VIEW_NBR_START, VIEW_NBR, VIEW_CORE_SORTED, VIEW_CELL_CID = range(7)
 
 
+class GdInstance(ctypes.Structure):
+    """gd_instance of include/gdbscan.h."""
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int), ("eps2", ctypes.c_int64),
+                ("minpts", ctypes.c_int32), ("labels", ctypes.c_void_p), ("is_core", ctypes.c_void_p)]
+
+
 class GdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"gdbscan error {status}: {msg}")
@@ -66,6 +72,12 @@ def load_library(path: str | None = None):
         lib.gd_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.c_int]
         lib.gd_stage_times.restype = ctypes.c_int
+        lib.gd_ctx_bytes.argtypes = [vp]
+        lib.gd_ctx_bytes.restype = ctypes.c_size_t
+        lib.gd_ctx_trim.argtypes = [vp]
+        lib.gd_ctx_trim.restype = ctypes.c_int
+        lib.gd_dbscan_batched.argtypes = [vp, ctypes.c_int, vp, vp]
+        lib.gd_dbscan_batched.restype = ctypes.c_int
         lib.gd_dbscan_noalloc.argtypes = [vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan_noalloc.restype = ctypes.c_int
         if path is None:
@@ -138,6 +150,33 @@ class Context:
         self._check(st)
         return labels, is_core.view(torch.bool) if is_core.dtype == torch.uint8 else is_core
 
+    def dbscan_batched(self, jobs, outputs=None, stream=None):
+        """Cluster a batch of instances in one gd_dbscan_batched call.  jobs is a
+        list of (X, eps2, minpts) with X a CUDA int32 [n, d] tensor (n >= 1);
+        returns a list of (labels, is_core) device tensors (or fills `outputs`,
+        a list of (labels int32, is_core uint8) tensor pairs)."""
+        import torch
+        k = len(jobs)
+        arr = (GdInstance * max(k, 1))()
+        outs = []
+        keep = []
+        for i, (X, eps2, minpts) in enumerate(jobs):
+            if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
+                raise TypeError("each X must be a CUDA int32 tensor of shape [n, d]")
+            X = X.contiguous()
+            keep.append(X)
+            n, d = X.shape
+            if outputs is not None:
+                lab, core = outputs[i]
+            else:
+                lab = torch.empty(n, dtype=torch.int32, device=X.device)
+                core = torch.empty(n, dtype=torch.uint8, device=X.device)
+            outs.append((lab, core))
+            arr[i] = GdInstance(X.data_ptr(), n, d, int(eps2), int(minpts), lab.data_ptr(), core.data_ptr())
+        self._check(self._lib.gd_dbscan_batched(self._h, k, ctypes.cast(arr, ctypes.c_void_p),
+                                                _stream_handle(stream)))
+        return [(lab, core.view(torch.bool) if core.dtype == torch.uint8 else core) for lab, core in outs]
+
     def dbscan_host(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
         """Cluster host points (numpy or CPU torch int32 [n, d]; pinned memory
         is fastest).  Copies in, clusters and copies the results out."""
@@ -156,6 +195,15 @@ class Context:
                                       is_core.data_ptr(), _stream_handle(stream))
         self._check(st)
         return labels, is_core
+
+    # -- memory
+    def bytes_held(self) -> int:
+        """Device bytes the context holds for reuse."""
+        return int(self._lib.gd_ctx_bytes(self._h))
+
+    def trim(self):
+        """Release the context's cached buffers."""
+        self._check(self._lib.gd_ctx_trim(self._h))
 
     # -- introspection
     def last_sizes(self) -> dict:

@@ -1,11 +1,17 @@
 // Internal declarations shared by the CUDA translation units of libgdbscan.
 //
-// Pipeline (one DBSCAN instance, all arrays device-resident):
-//   bounds -> quantise/pack keys (Eq. 1) -> LSD radix sort (Alg. 1)
-//   -> grid compaction + coordinate gather (Alg. 1) -> grid-tree levels (Alg. 2)
-//   -> neighbour-grid walk (Alg. 3) -> core points (G13 rule, Section 3.2)
-//   -> core-point compaction -> core-grid merge (Def. 6-7, Alg. 4-5) with
-//   union-find (LDF variant, Section 5.2) -> cluster ids -> border + labels.
+// Every stage runs over a batch of K independent DBSCAN instances (K = 1 for
+// gd_dbscan).  An instance is described by an Inst record in device memory
+// (its parameters and workspace pointers); a launch covers a flat space of
+// items -- the points, grids, pairs ... of all instances concatenated -- and
+// each thread, warp or block finds its instance from the space's offset table.
+//
+// Pipeline of one instance:
+//   bounds -> identifiers (Eq. 1) + digit histograms -> radix sort (Alg. 1)
+//   -> grid compaction + coordinate gather (Alg. 1) -> grid-tree levels
+//   (Alg. 2) -> neighbour-grid walk (Alg. 3) -> core points (G13 rule,
+//   Section 3.2) -> core-point packing -> core-grid merge (Def. 6-7, Alg. 4-5)
+//   with union-find (LDF variant, Section 5.2) -> cluster ids -> labels.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,7 +22,7 @@ namespace gd {
 constexpr int kMaxD = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Bits of the device status word (OR-ed by kernels, read by the host).
+// Bits of an instance's device status word (OR-ed by kernels).
 enum : unsigned { kDevTimeout = 1u, kDevOverflow = 2u };
 
 // Retry cap for the lock-free union-find loops: far above any legitimate
@@ -29,7 +35,7 @@ struct Params {
     int n;            // points
     int d;            // dimensions (1..8)
     int dp;           // padded row stride of the grid-order coordinates (1,2,4,8)
-    long long eps2;   // squared radius
+    long long eps2;   // squared radius (clamped below 2^62)
     int minpts;
     long long s;      // integer cell side: largest s with d*(s-1)^2 <= eps2
     long long r;      // largest |delta| per dimension whose gap alone is <= eps
@@ -45,6 +51,72 @@ struct Key2 {
     unsigned long long lo, hi;
 };
 
+// Slots of an instance's small device block (ints).
+enum SmallSlot {
+    kSmMnmx = 0,        // [16] per-dimension min then max
+    kSmCells = 16,      // C
+    kSmStatus = 17,     // status bits
+    kSmMaxCell = 18,    // largest grid
+    kSmNnbr = 19,       // neighbour-list length
+    kSmNonfull = 20,    // points of non-full grids
+    kSmPairsT = 21,     // touching candidate pairs
+    kSmPairsF = 22,     // other candidate pairs
+    kSmHard0 = 23,      // pairs handed to FastMerging, wave 0
+    kSmHard1 = 24,      // ... wave 1
+    kSmLevelCount = 32, // [8] nodes per grid-tree level
+    kSmallInts = 64
+};
+
+// One instance: parameters and workspace, in device memory.
+struct Inst {
+    Params p;
+    int passes, digit_bits, tiles;  // radix-sort plan
+    const int* X;
+    int* labels;
+    unsigned char* is_core;
+    int* small;  // [kSmallInts]
+    void* keyA;
+    void* keyB;
+    int* valA;
+    int* valB;
+    int* Xs;  // [n][dp] coordinates in grid order
+    int* pt_cell;
+    unsigned char* core_s;
+    int* Xc;  // [n][dp] core points packed per grid
+    int* cell_start;
+    int* cell_coord;
+    int* pbox;  // [C][2d] box of each grid's points: d minima, then d maxima
+    int* lv_key[kMaxD];
+    int* lv_cb[kMaxD];
+    int* lv_E;  // [d][C+1] level scratch
+    int* lv_L;  // [C]
+    int* nbr_start;
+    int* nbr;
+    int* nf_start;
+    int* core_start;
+    int* bbox;
+    int* pair_start;
+    int* pair_start_f;
+    int2* pairs;
+    int2* hard;
+    int* parent;
+    int* cid_root;
+    int* cell_cid;
+    int* bcnt;  // compaction: per-tile grid starts (scanned)
+    int* sort_hist;
+    int* sort_dstart;
+    int* sort_counters;
+    unsigned long long* sort_status;
+};
+
+// Flat item space over the instances of a launch: item i belongs to instance
+// idx[k] for off[k] <= i < off[k+1] (off has K+1 entries).
+struct Flat {
+    const long long* off;
+    const int* idx;
+    int K;
+};
+
 // ---------------------------------------------------------------- helpers
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -54,6 +126,36 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+
+// Position k in the flat space (largest k with off[k] <= i); off[0] = 0.
+__device__ __forceinline__ int flat_find(const Flat& f, long long i) {
+    int lo = 0, hi = f.K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(f.off + mid) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ long long flat_total(const Flat& f) { return __ldg(f.off + f.K); }
+
+// Caches the instance range of the last item, so that a thread walking items
+// of one instance does the binary search only when it crosses into another.
+struct FlatCursor {
+    int k = -1;
+    long long lo = 0, hi = 0;
+    // Returns true when the instance changed.
+    __device__ __forceinline__ bool seek(const Flat& f, long long i) {
+        if (i >= lo && i < hi) return false;
+        k = flat_find(f, i);
+        lo = __ldg(f.off + k);
+        hi = __ldg(f.off + k + 1);
+        return true;
+    }
+};
 
 // Exact squared distance of two integer points (int32 coordinates, int64 sum).
 template <int D>
@@ -124,21 +226,61 @@ __device__ __forceinline__ int uf_find(int* parent, int x) {
     return -1;
 }
 
+__device__ __forceinline__ void set_status(const Inst& I, unsigned bits) {
+    atomicOr(reinterpret_cast<unsigned*>(I.small + kSmStatus), bits);
+}
+
+template <int D> struct Padded {
+    static constexpr int value = D == 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
+};
+
+// Persistent grid size for grid-stride kernels.
+constexpr int kPersistBlocks = 152 * 16;
+
 // --------------------------------------------------- host-side launchers
-// All launchers enqueue on `st` and return cudaGetLastError().
+// All launchers enqueue on `st` and return cudaGetLastError().  `ins` is the
+// device array of Inst records; flat spaces are described by device offset
+// tables built by the host (sizes known there) or by count_flat (sizes known
+// only on the device).
 
 // Host-side count of kernel launches issued by this thread (reported per run).
 extern thread_local long long t_launches;
 #define GD_COUNT_LAUNCH() (++::gd::t_launches)
 
-// Device-wide exclusive scan of n ints (in may equal out); out[n] = total.
-// tmp must hold scan_tmp_ints(n) ints.
-size_t scan_tmp_ints(long long n);
-cudaError_t scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaStream_t st);
+// A segmented exclusive scan: segment k scans in[0..len) into out (in may
+// equal out) and writes its total to out[len].  Segments are given by a
+// device array of ScanSeg with blk0 = first flat tile of the segment.
+struct ScanSeg {
+    const int* in;
+    int* out;
+    long long len;
+    long long blk0;
+};
+constexpr int kScanTile = 2048;
+// tmp: at least (total tiles + K) ints.
+cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st);
+
+// Zeroes int ranges: range k covers ptr[k][0 .. len[k]); off is the exclusive
+// prefix of len over the ranges (n_ranges + 1 entries).
+struct ZeroRange {
+    int* ptr;
+    long long len;
+    long long off;
+};
+cudaError_t zero_ranges(const ZeroRange* r, int n_ranges, long long total, cudaStream_t st);
+
+// Device-side flat offsets: off[0] = 0, off[k+1] = off[k] + small[slot] of
+// instance idx[k].
+cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st);
 
 // Grid construction (grid.cu).
-cudaError_t launch_init_bounds(int* mnmx, cudaStream_t st);
-cudaError_t launch_bounds(const int* X, int n, int d, int* mnmx, cudaStream_t st);
+cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+constexpr int kCompactTile = 1024;
+cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st);
+cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st);
+// Over the flat space of points.
+cudaError_t launch_cell_max(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+
 // Identifiers and the radix sort (sort.cu).
 struct SortPlan {
     int passes;   // digit positions
@@ -148,72 +290,60 @@ struct SortPlan {
     int tiles;
 };
 SortPlan sort_plan(int n, int key_words, int key_bits);
-size_t radix_tmp_ints(int n, int key_words, int key_bits);
-// Computes the keys (Eq. 1, packed) and values (input index) into keys_a /
-// vals_a, with the histogram of every digit position (into tmp).
-cudaError_t quantise_hist(const int* X, const Params& p, void* keys_a, int* vals_a, int* tmp, cudaStream_t st);
-// The onesweep passes: sorts (keys_a, vals_a) stably by key; *result_in_b
-// tells which buffer pair holds the result.  err receives kDevTimeout if a
-// look-back gave up.  tmp must still hold what quantise_hist left there.
-cudaError_t sort_passes(const Params& p, void* keys_a, int* vals_a, void* keys_b, int* vals_b, int* tmp, unsigned* err,
-                        cudaStream_t st, int* result_in_b);
-size_t compact_tmp_ints(int n);
-cudaError_t launch_compact(const Params& p, const int* X, const void* keys, const int* vals, int* tmp,
-                           int* cell_start, int* cell_coord, int* pt_cell, int* Xs, int* num_cells,
-                           cudaStream_t st);
+// ints of workspace for one instance's sort (histograms, tile counters,
+// look-back status); layout in sort.cu.
+size_t sort_tmp_ints(int n, int key_words, int key_bits);
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** hist, int** dstart, int** counters,
+                     unsigned long long** status, size_t* zero_ints);
+constexpr int kQuantTile = 4096;  // points per quantise block
+// keys, values and digit histograms; `tiles` is the flat space of quantise
+// tiles (kQuantTile points) of instances with the given key width.
+// Histograms, counters and status must be zeroed first.
+cudaError_t launch_quantise_hist(const Inst* ins, Flat tiles, long long total, int key_words, int max_hist_ints,
+                                 cudaStream_t st);
+cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st);
+// One onesweep pass over the tiles of the instances in `tiles` (each with
+// more than `pass` passes and the given key width).
+cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_words, int pass, int max_buckets,
+                            int* flat_counter, cudaStream_t st);
 
 // Grid-tree levels and neighbour walk (neighbors.cu).
-struct Levels {
-    int* key[kMaxD];          // level j: identifier j of each node
-    int* child_begin[kMaxD];  // level j < d-1: first child at level j+1 ([N_j + 1])
-    int* count;               // [kMaxD] node counts per level (device)
-};
-size_t levels_tmp_ints(int C, int d);
-cudaError_t build_levels(const Params& p, const int* cell_coord, int C, Levels lv, int* tmp, cudaStream_t st);
-cudaError_t launch_walk_count(const Params& p, const int* cell_coord, int C, Levels lv, int* nbr_count,
-                              cudaStream_t st);
-cudaError_t launch_walk_fill(const Params& p, const int* cell_coord, int C, Levels lv, const int* nbr_start,
-                             int* nbr, cudaStream_t st);
+cudaError_t launch_point_boxes(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_level_diff(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_level_flag(const Inst* ins, Flat cells, long long total, int level, cudaStream_t st);
+cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, bool fill, cudaStream_t st);
 
 // Core points (core.cu).
-// nf_start: C+1 ints of workspace (points of non-full grids, scanned).
-cudaError_t launch_core(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
-                        const int* cell_coord, int C, const int* nbr_start, const int* nbr, int* nf_start, int* tmp,
-                        unsigned char* core_s, cudaStream_t st);
+cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+// Non-full points of instances with dimension d (flat offsets on the device).
+cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, cudaStream_t st);
 
 // Merging (merge.cu).
-cudaError_t launch_core_count(const Params& p, const unsigned char* core_s, const int* cell_start, int C,
-                              int* core_cnt, int* bbox, cudaStream_t st);
-cudaError_t launch_core_pack(const Params& p, const int* Xs, const unsigned char* core_s, const int* pt_cell,
-                             const int* cell_start, const int* core_start, int* Xc, int* bbox, cudaStream_t st);
-cudaError_t launch_cell_max(const int* cell_start, int C, int* out, cudaStream_t st);
-cudaError_t launch_pair_count(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
-                              const int* cell_coord, int C, int* t_count, int* f_count, cudaStream_t st);
-cudaError_t launch_pair_fill(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
-                             const int* cell_coord, int C, const int* t_start, const int* f_start, int2* pairs,
-                             cudaStream_t st);
-cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, int* range, int* hard_cnt,
-                                cudaStream_t st);
-cudaError_t launch_uf_init(int* parent, int C, cudaStream_t st);
-// Points every grid at its union-find root (no unions may run concurrently).
-cudaError_t launch_uf_flatten(int* parent, int C, unsigned* status, cudaStream_t st);
-// Default number of FastMerging blocks; each block owns 2 * wpb words of
-// `scratch`, wpb = ceil(largest grid / 32) + 1.
+cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+// Copies scan totals into the small blocks: nbr_start[C] -> kSmNnbr,
+// nf_start[C] -> kSmNonfull, pair_start[C] / pair_start_f[C] -> kSmPairsT /
+// kSmPairsF (for the bits of `which`: 1, 2, 4) and, with 4, resets the hard
+// counters.
+cudaError_t launch_totals(const Inst* ins, const int* idx, int K, int which, cudaStream_t st);
+cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+// Warp-level test of the candidate pairs of one wave (0: touching, 1: others)
+// of instances with dimension d; undecided pairs go to the instance's hard list.
+cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, cudaStream_t st);
+// FastMerging (Alg. 5) of the hard pairs of one wave: `blocks` blocks, block b
+// using the 2 * wpb bitmap words at scratch + 2 * wpb * b (wpb >= the largest
+// grid of the batch / 32 + 1).
+cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
+                               cudaStream_t st);
 int merge_fm_blocks();
-// One merge wave (0: touching pairs, 1: the others): warp-level test of every
-// pair in range[2*wave .. 2*wave+1], then FastMerging of the pairs it hands on.
-cudaError_t launch_merge_wave(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
-                              const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
-                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, int fm_blocks,
-                              cudaStream_t st);
 
 // Labels (label.cu).
-cudaError_t launch_cluster_ids(const Params& p, int* parent, const int* core_start, const int* cell_start,
-                               const unsigned char* core_s, const int* perm, int C, int* cid_root,
-                               int* cell_cid, cudaStream_t st, unsigned* status);
-cudaError_t launch_labels(const Params& p, const int* Xs, const int* cell_start, const int* pt_cell,
-                          const unsigned char* core_s, const int* nbr_start, const int* nbr,
-                          const int* core_start, const int* Xc, const int* bbox, const int* cell_cid,
-                          const int* perm, int* labels, unsigned char* is_core, cudaStream_t st);
+cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_labels(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
 
 }  // namespace gd

@@ -1,158 +1,224 @@
-// Grid construction: bounds (mn_j of Eq. 1) and the non-empty-grid
-// compaction of Alg. 1, plus a device-wide exclusive scan.  The identifiers
-// and the sort are in sort.cu.
+// Grid construction over a batch: bounds (mn_j of Eq. 1) and the
+// non-empty-grid compaction of Alg. 1, plus the segmented scan and device-side
+// flat offsets every stage uses.  Identifiers and the sort are in sort.cu.
 #include <climits>
 
 #include "gd_internal.cuh"
 
 namespace gd {
 
-// ------------------------------------------------------------------ scan
-// Three phases: per-tile sums, one-block scan of the sums, per-tile scan.
+// ------------------------------------------------------- segmented scan
+// Three phases: per-tile sums, one block per segment scanning its tiles'
+// sums, per-tile scan.  A tile never spans two segments.
 
 constexpr int kScanBlock = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanBlock * kScanItems;
+constexpr int kScanItems = kScanTile / kScanBlock;
 
-size_t scan_tmp_ints(long long n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 2; }
+__device__ __forceinline__ int seg_of_tile(const ScanSeg* segs, int K, long long b) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
-__global__ void __launch_bounds__(kScanBlock) scan_reduce_kernel(const int* __restrict__ in, long long n,
-                                                                 int* __restrict__ bsum) {
+__global__ void __launch_bounds__(kScanBlock) seg_reduce_kernel(const ScanSeg* __restrict__ segs, int K,
+                                                                int* __restrict__ bsum) {
     __shared__ int sm[33];
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    const int k = seg_of_tile(segs, K, blockIdx.x);
+    const ScanSeg sg = segs[k];
+    const long long base = (blockIdx.x - sg.blk0) * (long long)kScanTile + (long long)threadIdx.x * kScanItems;
     int s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i)
-        if (base + i < n) s += in[base + i];
+        if (base + i < sg.len) s += sg.in[base + i];
     int total;
     block_exclusive_scan(s, sm, &total);
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) scan_top_kernel(int* __restrict__ bsum, int nb) {
+// One block per segment: exclusive scan of its tiles' sums in place; the
+// segment total goes to out[len].
+__global__ void __launch_bounds__(1024) seg_top_kernel(const ScanSeg* __restrict__ segs, int* __restrict__ bsum,
+                                                       long long total_tiles) {
     __shared__ int sm[33];
+    const ScanSeg sg = segs[blockIdx.x];
+    const long long end = (blockIdx.x + 1 < gridDim.x) ? segs[blockIdx.x + 1].blk0 : total_tiles;
     int carry = 0;
-    for (int base = 0; base < nb; base += 1024) {
-        int k = base + threadIdx.x;
-        int v = k < nb ? bsum[k] : 0;
+    for (long long base = sg.blk0; base < end; base += 1024) {
+        const long long k = base + threadIdx.x;
+        const int v = k < end ? bsum[k] : 0;
         int total;
-        int ex = block_exclusive_scan(v, sm, &total);
-        if (k < nb) bsum[k] = carry + ex;
+        const int ex = block_exclusive_scan(v, sm, &total);
+        if (k < end) bsum[k] = carry + ex;
         carry += total;
     }
-    if (threadIdx.x == 0) bsum[nb] = carry;
+    if (threadIdx.x == 0) sg.out[sg.len] = carry;
 }
 
-__global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const int* in, int* out, long long n,
-                                                               const int* __restrict__ bsum, int nb) {
+__global__ void __launch_bounds__(kScanBlock) seg_down_kernel(const ScanSeg* __restrict__ segs, int K,
+                                                              const int* __restrict__ bsum) {
     __shared__ int sm[33];
-    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    const int k = seg_of_tile(segs, K, blockIdx.x);
+    const ScanSeg sg = segs[k];
+    const long long base = (blockIdx.x - sg.blk0) * (long long)kScanTile + (long long)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < n) ? in[base + i] : 0;
+        v[i] = (base + i < sg.len) ? sg.in[base + i] : 0;
         s += v[i];
     }
     int total;
     int run = bsum[blockIdx.x] + block_exclusive_scan(s, sm, &total);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) out[base + i] = run;
+        if (base + i < sg.len) sg.out[base + i] = run;
         run += v[i];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
-cudaError_t scan_exclusive(const int* in, int* out, long long n, int* tmp, cudaStream_t st) {
-    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
-    const int nb = (int)((n + kScanTile - 1) / kScanTile);
-    scan_reduce_kernel<<<nb, kScanBlock, 0, st>>>(in, n, tmp);
+cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    if (total_tiles > 0) {
+        seg_reduce_kernel<<<(unsigned)total_tiles, kScanBlock, 0, st>>>(segs, K, tmp);
+        GD_COUNT_LAUNCH();
+    }
+    seg_top_kernel<<<K, 1024, 0, st>>>(segs, tmp, total_tiles);
     GD_COUNT_LAUNCH();
-    scan_top_kernel<<<1, 1024, 0, st>>>(tmp, nb);
+    if (total_tiles > 0) {
+        seg_down_kernel<<<(unsigned)total_tiles, kScanBlock, 0, st>>>(segs, K, tmp);
+        GD_COUNT_LAUNCH();
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- zero ranges
+
+__global__ void zero_ranges_kernel(const ZeroRange* __restrict__ r, int n_ranges, long long total) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ranges - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (r[mid].off <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        r[lo].ptr[i - r[lo].off] = 0;
+    }
+}
+
+cudaError_t zero_ranges(const ZeroRange* r, int n_ranges, long long total, cudaStream_t st) {
+    if (n_ranges <= 0 || total <= 0) return cudaSuccess;
+    long long b = (total + 255) / 256;
+    if (b > kPersistBlocks) b = kPersistBlocks;
+    zero_ranges_kernel<<<(int)b, 256, 0, st>>>(r, n_ranges, total);
     GD_COUNT_LAUNCH();
-    scan_down_kernel<<<nb, kScanBlock, 0, st>>>(in, out, n, tmp, nb);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ flat offsets
+
+__global__ void count_flat_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int K, int slot,
+                                  long long* __restrict__ off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long run = 0;
+    off[0] = 0;
+    for (int k = 0; k < K; ++k) {
+        run += ins[idx[k]].small[slot];
+        off[k + 1] = run;
+    }
+}
+
+cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st) {
+    count_flat_kernel<<<1, 32, 0, st>>>(ins, idx, K, slot, off);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- bounds
 
-__global__ void init_bounds_kernel(int* mnmx) {
-    if (threadIdx.x < kMaxD) {
-        mnmx[threadIdx.x] = INT_MAX;
-        mnmx[kMaxD + threadIdx.x] = INT_MIN;
+// Per-dimension min and max (mn_j of Eq. 1).  Each thread accumulates in
+// registers while its items stay in one instance and flushes with atomics
+// when it moves to another; at the end, a warp whose lanes all hold the same
+// instance reduces with shuffles and applies one atomic per dimension.  The
+// small blocks' mnmx must hold INT_MAX / INT_MIN first.
+__device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const int* mx) {
+    for (int j = 0; j < I.p.d; ++j) {
+        atomicMin(I.small + kSmMnmx + j, mn[j]);
+        atomicMax(I.small + kSmMnmx + kMaxD + j, mx[j]);
     }
 }
 
-cudaError_t launch_init_bounds(int* mnmx, cudaStream_t st) {
-    init_bounds_kernel<<<1, 32, 0, st>>>(mnmx);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-// Per-dimension min and max (mn_j of Eq. 1), reduced per warp then per block,
-// then one atomic per block and dimension.
-__global__ void __launch_bounds__(256) bounds_kernel(const int* __restrict__ X, int n, int d, int* mnmx) {
+__global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
     int mn[kMaxD], mx[kMaxD];
 #pragma unroll
     for (int j = 0; j < kMaxD; ++j) {
         mn[j] = INT_MAX;
         mx[j] = INT_MIN;
     }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int* row = X + i * d;
+    FlatCursor cur;
+    int kk = -1;  // instance index of the accumulated values
+    const int* X = nullptr;
+    int d = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        if (cur.seek(f, i)) {
+            if (kk >= 0) bounds_flush(ins[kk], mn, mx);
+#pragma unroll
+            for (int j = 0; j < kMaxD; ++j) {
+                mn[j] = INT_MAX;
+                mx[j] = INT_MIN;
+            }
+            kk = f.idx[cur.k];
+            X = ins[kk].X;
+            d = ins[kk].p.d;
+        }
+        const int* row = X + (i - cur.lo) * d;
 #pragma unroll
         for (int j = 0; j < kMaxD; ++j)
             if (j < d) {
-                int v = __ldg(row + j);
+                const int v = __ldg(row + j);
                 mn[j] = min(mn[j], v);
                 mx[j] = max(mx[j], v);
             }
     }
-    __shared__ int smn[8][kMaxD], smx[8][kMaxD];
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned uniform = __match_any_sync(kFull, kk);
+    if (uniform == kFull) {
+        if (kk < 0) return;
 #pragma unroll
-    for (int j = 0; j < kMaxD; ++j) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[j] = min(mn[j], __shfl_xor_sync(kFull, mn[j], o));
-            mx[j] = max(mx[j], __shfl_xor_sync(kFull, mx[j], o));
-        }
-        if (lane == 0) {
-            smn[warp][j] = mn[j];
-            smx[warp][j] = mx[j];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < d) {
-        int a = INT_MAX, b = INT_MIN;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a = min(a, smn[w][threadIdx.x]);
-            b = max(b, smx[w][threadIdx.x]);
-        }
-        atomicMin(mnmx + threadIdx.x, a);
-        atomicMax(mnmx + kMaxD + threadIdx.x, b);
+        for (int j = 0; j < kMaxD; ++j)
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[j] = min(mn[j], __shfl_xor_sync(kFull, mn[j], o));
+                mx[j] = max(mx[j], __shfl_xor_sync(kFull, mx[j], o));
+            }
+        if (lane_id() == 0) bounds_flush(ins[kk], mn, mx);
+    } else if (kk >= 0) {
+        bounds_flush(ins[kk], mn, mx);
     }
 }
 
-cudaError_t launch_bounds(const int* X, int n, int d, int* mnmx, cudaStream_t st) {
-    int blocks = (n + 255) / 256;
+cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
-    bounds_kernel<<<blocks, 256, 0, st>>>(X, n, d, mnmx);
+    bounds_kernel<<<(int)blocks, 256, 0, st>>>(ins, pts, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ compaction
 // Alg. 1's scan over the sorted points: a grid starts where the key changes.
+// Flat space: compaction tiles of kCompactTile points of each instance.
 
 constexpr int kCompactBlock = 256;
-constexpr int kCompactItems = 4;
-constexpr int kCompactTile = kCompactBlock * kCompactItems;
-
-size_t compact_tmp_ints(int n) { return (size_t)((n + kCompactTile - 1) / kCompactTile) + 1 + scan_tmp_ints(n); }
+constexpr int kCompactItems = kCompactTile / kCompactBlock;
 
 __device__ __forceinline__ bool key_eq(unsigned long long a, unsigned long long b) { return a == b; }
 __device__ __forceinline__ bool key_eq(const Key2& a, const Key2& b) { return a.lo == b.lo && a.hi == b.hi; }
@@ -172,84 +238,129 @@ __device__ __forceinline__ unsigned key_field(const Key2& k, int sh, int bits) {
     return (unsigned)(v & ((1ull << bits) - 1ull));
 }
 
+// The sorted keys/values of an instance: the sort leaves them in A after an
+// even number of passes, in B after an odd number.
 template <typename K>
-__global__ void __launch_bounds__(kCompactBlock) cell_count_kernel(const K* __restrict__ keys, int n,
-                                                                   int* __restrict__ bcnt) {
+__device__ __forceinline__ const K* sorted_keys(const Inst& I) {
+    return (const K*)((I.passes & 1) ? I.keyB : I.keyA);
+}
+__device__ __forceinline__ const int* sorted_vals(const Inst& I) { return (I.passes & 1) ? I.valB : I.valA; }
+
+template <typename K>
+__global__ void __launch_bounds__(kCompactBlock) compact_count_kernel(const Inst* __restrict__ ins, Flat f) {
     __shared__ int sm[33];
-    const long long base = (long long)blockIdx.x * kCompactTile + (long long)threadIdx.x * kCompactItems;
+    const int k = flat_find(f, blockIdx.x);
+    const Inst& I = ins[f.idx[k]];
+    const long long tile = blockIdx.x - f.off[k];
+    const int n = I.p.n;
+    const K* keys = sorted_keys<K>(I);
+    const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
     int c = 0;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
-        long long k = base + i;
-        if (k < n && (k == 0 || !key_eq(keys[k], keys[k - 1]))) c++;
+        const long long q = base + i;
+        if (q < n && (q == 0 || !key_eq(keys[q], keys[q - 1]))) c++;
     }
     int total;
     block_exclusive_scan(c, sm, &total);
-    if (threadIdx.x == 0) bcnt[blockIdx.x] = total;
+    if (threadIdx.x == 0) I.bcnt[tile] = total;
 }
 
+// Writes cell_start, identifiers (decoded from the key), pt_cell and the
+// grid-order coordinates Xs (gathered through the sorted permutation).
 template <typename K>
-__global__ void __launch_bounds__(kCompactBlock) cell_write_kernel(Params p, const int* __restrict__ X,
-                                                                   const K* __restrict__ keys,
-                                                                   const int* __restrict__ vals,
-                                                                   const int* __restrict__ boff,
-                                                                   int* __restrict__ cell_start,
-                                                                   int* __restrict__ cell_coord,
-                                                                   int* __restrict__ pt_cell, int* __restrict__ Xs,
-                                                                   int* __restrict__ num_cells) {
+__global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst* __restrict__ ins, Flat f) {
     __shared__ int sm[33];
-    const int n = p.n, d = p.d, dp = p.dp;
-    const long long base = (long long)blockIdx.x * kCompactTile + (long long)threadIdx.x * kCompactItems;
-    bool f[kCompactItems];
+    const int k = flat_find(f, blockIdx.x);
+    const Inst& I = ins[f.idx[k]];
+    const long long tile = blockIdx.x - f.off[k];
+    const int n = I.p.n, d = I.p.d, dp = I.p.dp;
+    const K* keys = sorted_keys<K>(I);
+    const int* vals = sorted_vals(I);
+    const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
+    bool fl[kCompactItems];
     int c = 0;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
-        long long k = base + i;
-        f[i] = k < n && (k == 0 || !key_eq(keys[k], keys[k - 1]));
-        c += f[i];
+        const long long q = base + i;
+        fl[i] = q < n && (q == 0 || !key_eq(keys[q], keys[q - 1]));
+        c += fl[i];
     }
     int total;
-    int cid = boff[blockIdx.x] + block_exclusive_scan(c, sm, &total) - 1;
+    int cid = I.bcnt[tile] + block_exclusive_scan(c, sm, &total) - 1;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
-        const long long k = base + i;
-        if (k >= n) break;
-        if (f[i]) {
+        const long long q = base + i;
+        if (q >= n) break;
+        if (fl[i]) {
             cid++;
-            cell_start[cid] = (int)k;
-            const K key = keys[k];
-            for (int j = 0; j < d; ++j) cell_coord[(long long)cid * d + j] = (int)key_field(key, p.shift[j], p.bits[j]);
+            I.cell_start[cid] = (int)q;
+            const K key = keys[q];
+            for (int j = 0; j < d; ++j)
+                I.cell_coord[(long long)cid * d + j] = (int)key_field(key, I.p.shift[j], I.p.bits[j]);
         }
-        pt_cell[k] = cid;
-        const int src = vals[k];
-        const int* row = X + (long long)src * d;
-        int* out = Xs + k * dp;
-        for (int j = 0; j < dp; ++j) out[j] = j < d ? __ldg(row + j) : 0;
-        if (k == n - 1) {
-            cell_start[cid + 1] = n;
-            *num_cells = cid + 1;
+        I.pt_cell[q] = cid;
+        const int* row = I.X + (long long)vals[q] * d;
+        int* out = I.Xs + q * dp;
+        if (dp == 4) {
+            int4 v;
+            v.x = __ldg(row);
+            v.y = d > 1 ? __ldg(row + 1) : 0;
+            v.z = d > 2 ? __ldg(row + 2) : 0;
+            v.w = d > 3 ? __ldg(row + 3) : 0;
+            *reinterpret_cast<int4*>(out) = v;
+        } else {
+            for (int j = 0; j < dp; ++j) out[j] = j < d ? __ldg(row + j) : 0;
+        }
+        if (q == n - 1) {
+            I.cell_start[cid + 1] = n;
+            I.small[kSmCells] = cid + 1;
         }
     }
 }
 
-cudaError_t launch_compact(const Params& p, const int* X, const void* keys, const int* vals, int* tmp,
-                           int* cell_start, int* cell_coord, int* pt_cell, int* Xs, int* num_cells, cudaStream_t st) {
-    const int nb = (p.n + kCompactTile - 1) / kCompactTile;
-    int* bcnt = tmp;
-    int* scan_tmp = tmp + nb + 1;
-    if (p.key_words == 1)
-        cell_count_kernel<<<nb, kCompactBlock, 0, st>>>((const unsigned long long*)keys, p.n, bcnt);
+cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    if (key_words == 1)
+        compact_count_kernel<unsigned long long><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     else
-        cell_count_kernel<<<nb, kCompactBlock, 0, st>>>((const Key2*)keys, p.n, bcnt);
+        compact_count_kernel<Key2><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     GD_COUNT_LAUNCH();
-    cudaError_t e = scan_exclusive(bcnt, bcnt, nb, scan_tmp, st);
-    if (e != cudaSuccess) return e;
-    if (p.key_words == 1)
-        cell_write_kernel<<<nb, kCompactBlock, 0, st>>>(p, X, (const unsigned long long*)keys, vals, bcnt, cell_start,
-                                                        cell_coord, pt_cell, Xs, num_cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    if (key_words == 1)
+        compact_write_kernel<unsigned long long><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     else
-        cell_write_kernel<<<nb, kCompactBlock, 0, st>>>(p, X, (const Key2*)keys, vals, bcnt, cell_start, cell_coord,
-                                                        pt_cell, Xs, num_cells);
+        compact_write_kernel<Key2><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+// Largest grid of each instance (bounds the merge's bitmaps), over the flat
+// space of points: the point that starts a grid looks the grid's size up.
+// small[kSmMaxCell] must be 0 first.
+__global__ void cell_max_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        cur.seek(f, i);
+        const int k = cur.k;
+        const Inst& I = ins[f.idx[k]];
+        const long long q = i - cur.lo;
+        const int c = I.pt_cell[q];
+        if (I.cell_start[c] != q) continue;
+        atomicMax(I.small + kSmMaxCell, I.cell_start[c + 1] - (int)q);
+    }
+}
+
+cudaError_t launch_cell_max(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    if (blocks > kPersistBlocks) blocks = kPersistBlocks;
+    cell_max_kernel<<<(int)blocks, 256, 0, st>>>(ins, pts, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

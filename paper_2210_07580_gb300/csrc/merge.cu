@@ -1,36 +1,51 @@
-// Merging core grids (Section 4.3, Def. 6-7): two neighbouring core grids
-// belong to one cluster iff some core point of one is within eps of some core
-// point of the other.  The grids are joined with a lock-free union-find, as
-// in the LDF variant (Section 5.2): a pair whose grids are already in one set
-// is skipped before any distance is computed.
+// Merging core grids (Section 4.3, Def. 6-7), over a batch: two neighbouring
+// core grids belong to one cluster iff some core point of one is within eps
+// of some core point of the other.  The grids are joined with a lock-free
+// union-find, as in the LDF variant (Section 5.2): a pair whose grids are
+// already in one set is skipped before any distance is computed.
 #include "gd_internal.cuh"
 
 namespace gd {
 
+static int blocks_for(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > kPersistBlocks) b = kPersistBlocks;
+    return b < 1 ? 1 : (int)b;
+}
+
+#define GD_FOR_FLAT(i, total)                                                                         \
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (total);                 \
+         i += (long long)gridDim.x * blockDim.x)
+
 // ------------------------------------------------- core points per grid
 
-// m_c (core points per grid) and reset of the grid's core bounding box.
-__global__ void core_count_kernel(int minpts, int d, const unsigned char* __restrict__ core_s,
-                                  const int* __restrict__ cell_start, int C, int* __restrict__ core_cnt,
-                                  int* __restrict__ bbox) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    const int b = cell_start[c], e = cell_start[c + 1];
-    int m = e - b;
-    if (m < minpts) {
-        m = 0;
-        for (int k = b; k < e; ++k) m += core_s[k];
-    }
-    core_cnt[c] = m;
-    for (int j = 0; j < d; ++j) {
-        bbox[(long long)c * 2 * d + j] = 0x7fffffff;
-        bbox[(long long)c * 2 * d + d + j] = (int)0x80000000;
+// m_c (core points per grid, into core_start before its scan) and reset of
+// the grid's core bounding box.
+__global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const int k = cur.k;
+        const Inst& I = ins[f.idx[k]];
+        const long long c = i - cur.lo;
+        const int d = I.p.d;
+        const int b = I.cell_start[c], e = I.cell_start[c + 1];
+        int m = e - b;
+        if (m < I.p.minpts) {
+            m = 0;
+            for (int q = b; q < e; ++q) m += I.core_s[q];
+        }
+        I.core_start[c] = m;
+        for (int j = 0; j < d; ++j) {
+            I.bbox[c * 2 * d + j] = 0x7fffffff;
+            I.bbox[c * 2 * d + d + j] = (int)0x80000000;
+        }
     }
 }
 
-cudaError_t launch_core_count(const Params& p, const unsigned char* core_s, const int* cell_start, int C,
-                              int* core_cnt, int* bbox, cudaStream_t st) {
-    core_count_kernel<<<(C + 255) / 256, 256, 0, st>>>(p.minpts, p.d, core_s, cell_start, C, core_cnt, bbox);
+cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    core_count_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -38,85 +53,69 @@ cudaError_t launch_core_count(const Params& p, const unsigned char* core_s, cons
 // Core points of each grid packed contiguously (s_i of Section 4.3.1), one
 // thread per point in grid order, and the bounding box of each grid's core
 // points: a warp's lanes hold consecutive points, so the lanes of one grid
-// form a run; the run is min/max-reduced with shuffles and its first lane
-// applies one atomic per dimension.
-__global__ void __launch_bounds__(256) core_pack_kernel(Params p, const int* __restrict__ Xs,
-                                                        const unsigned char* __restrict__ core_s,
-                                                        const int* __restrict__ pt_cell,
-                                                        const int* __restrict__ cell_start,
-                                                        const int* __restrict__ core_start, int* __restrict__ Xc,
-                                                        int* __restrict__ bbox) {
-    const int lane = lane_id(), d = p.d, dp = p.dp;
+// (of one instance) form a run; the run is min/max-reduced with shuffles and
+// its first lane applies one atomic per dimension.
+__global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    const int lane = lane_id();
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long n_round = ((long long)p.n + 31) & ~31ll;
+    const long long n_round = (total + 31) & ~31ll;
+    FlatCursor cur;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        const bool valid = i < p.n;
-        const int c = valid ? pt_cell[i] : -1 - lane;
-        const bool core = valid && core_s[i];
+        const bool valid = i < total;
+        if (valid) cur.seek(f, i);
+        const int k = valid ? cur.k : 0;
+        const Inst* I = ins + (valid ? f.idx[k] : 0);
+        const long long q = valid ? i - cur.lo : 0;
+        const int c = valid ? I->pt_cell[q] : -1;
+        const long long key = valid ? (((long long)k << 32) | (unsigned)c) : (-1ll - lane);
+        const bool core = valid && I->core_s[q];
+        const int d = valid ? I->p.d : 0, dp = valid ? I->p.dp : 0;
         int x[kMaxD];
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j) x[j] = (core && j < dp) ? Xs[i * dp + j] : 0;
+        for (int j = 0; j < kMaxD; ++j) x[j] = (core && j < dp) ? I->Xs[q * dp + j] : 0;
         if (core) {
-            const int b = cell_start[c];
+            const int b = I->cell_start[c];
             long long pos;
-            if (cell_start[c + 1] - b >= p.minpts) {
-                pos = core_start[c] + (i - b);
+            if (I->cell_start[c + 1] - b >= I->p.minpts) {
+                pos = I->core_start[c] + (q - b);
             } else {
                 int r = 0;
-                for (long long k = b; k < i; ++k) r += core_s[k];
-                pos = core_start[c] + r;
+                for (long long u = b; u < q; ++u) r += I->core_s[u];
+                pos = I->core_start[c] + r;
             }
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
-                if (j < dp) Xc[pos * dp + j] = x[j];
+                if (j < dp) I->Xc[pos * dp + j] = x[j];
         }
-        const unsigned peers = __match_any_sync(kFull, c);
+        const unsigned peers = __match_any_sync(kFull, key);
         const bool leader = lane == __ffs(peers) - 1;
         const bool any_core = (__ballot_sync(kFull, core) & peers) != 0;
+        const int dmax = __reduce_max_sync(kFull, (unsigned)d);
 #pragma unroll
         for (int j = 0; j < kMaxD; ++j) {
-            if (j >= d) break;
+            if (j >= dmax) break;
             int lo = core ? x[j] : 0x7fffffff, hi = core ? x[j] : (int)0x80000000;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int olo = __shfl_down_sync(kFull, lo, o);
                 const int ohi = __shfl_down_sync(kFull, hi, o);
-                const int oc = __shfl_down_sync(kFull, c, o);
-                if (lane + o < 32 && oc == c) {
+                const long long ok = __shfl_down_sync(kFull, key, o);
+                if (lane + o < 32 && ok == key) {
                     lo = min(lo, olo);
                     hi = max(hi, ohi);
                 }
             }
-            if (leader && any_core) {
-                atomicMin(bbox + (long long)c * 2 * d + j, lo);
-                atomicMax(bbox + (long long)c * 2 * d + d + j, hi);
+            if (leader && any_core && j < d) {
+                atomicMin(I->bbox + (long long)c * 2 * d + j, lo);
+                atomicMax(I->bbox + (long long)c * 2 * d + d + j, hi);
             }
         }
     }
 }
 
-cudaError_t launch_core_pack(const Params& p, const int* Xs, const unsigned char* core_s, const int* pt_cell,
-                             const int* cell_start, const int* core_start, int* Xc, int* bbox, cudaStream_t st) {
-    long long blocks = ((long long)p.n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    core_pack_kernel<<<(int)blocks, 256, 0, st>>>(p, Xs, core_s, pt_cell, cell_start, core_start, Xc, bbox);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-// Largest grid (bounds the per-block pruning bitmaps of the merge).
-__global__ void cell_max_kernel(const int* __restrict__ cell_start, int C, int* out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int m = c < C ? cell_start[c + 1] - cell_start[c] : 0;
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-    if (lane_id() == 0 && m > 0) atomicMax(out, m);
-}
-
-cudaError_t launch_cell_max(const int* cell_start, int C, int* out, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    cell_max_kernel<<<(C + 255) / 256, 256, 0, st>>>(cell_start, C, out);
+cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    core_pack_kernel<<<blocks_for(total), 256, 0, st>>>(ins, pts, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -130,79 +129,82 @@ cudaError_t launch_cell_max(const int* cell_start, int C, int* out, cudaStream_t
 // that later checks can be skipped).
 
 template <bool FILL>
-__global__ void pair_kernel(int d, const int* __restrict__ nbr_start, const int* __restrict__ nbr,
-                            const int* __restrict__ core_start, const int* __restrict__ coord, int C,
-                            int* __restrict__ t_cnt_or_start, int* __restrict__ f_cnt_or_start,
-                            int2* __restrict__ pairs) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    int kt = 0, kf = 0;
-    if (core_start[c + 1] > core_start[c]) {
-        int2* out_t = nullptr;
-        int2* out_f = nullptr;
-        if (FILL) {
-            out_t = pairs + t_cnt_or_start[c];
-            out_f = pairs + t_cnt_or_start[C] + f_cnt_or_start[c];
-        }
-        int g[kMaxD];
-        for (int j = 0; j < d; ++j) g[j] = coord[(long long)c * d + j];
-        for (int t = nbr_start[c]; t < nbr_start[c + 1]; ++t) {
-            const int j2 = nbr[t];
-            if (j2 <= c || core_start[j2 + 1] == core_start[j2]) continue;
-            bool touching = true;
-            for (int j = 0; j < d; ++j) {
-                const int dl = coord[(long long)j2 * d + j] - g[j];
-                if (dl > 1 || dl < -1) touching = false;
+__global__ void pair_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const int k = cur.k;
+        const Inst& I = ins[f.idx[k]];
+        const long long c = i - cur.lo;
+        const int d = I.p.d, C = I.small[kSmCells];
+        const int* core_start = I.core_start;
+        const int* coord = I.cell_coord;
+        int kt = 0, kf = 0;
+        if (core_start[c + 1] > core_start[c]) {
+            int2* out_t = nullptr;
+            int2* out_f = nullptr;
+            if (FILL) {
+                out_t = I.pairs + I.pair_start[c];
+                out_f = I.pairs + I.pair_start[C] + I.pair_start_f[c];
             }
-            if (touching) {
-                if (FILL) out_t[kt] = make_int2(c, j2);
-                kt++;
-            } else {
-                if (FILL) out_f[kf] = make_int2(c, j2);
-                kf++;
+            int g[kMaxD];
+            for (int j = 0; j < d; ++j) g[j] = coord[c * d + j];
+            for (int t = I.nbr_start[c]; t < I.nbr_start[c + 1]; ++t) {
+                const int j2 = I.nbr[t];
+                if (j2 <= c || core_start[j2 + 1] == core_start[j2]) continue;
+                bool touching = true;
+                for (int j = 0; j < d; ++j) {
+                    const int dl = coord[(long long)j2 * d + j] - g[j];
+                    if (dl > 1 || dl < -1) touching = false;
+                }
+                if (touching) {
+                    if (FILL) out_t[kt] = make_int2((int)c, j2);
+                    kt++;
+                } else {
+                    if (FILL) out_f[kf] = make_int2((int)c, j2);
+                    kf++;
+                }
             }
         }
-    }
-    if (!FILL) {
-        t_cnt_or_start[c] = kt;
-        f_cnt_or_start[c] = kf;
+        if (!FILL) {
+            I.pair_start[c] = kt;
+            I.pair_start_f[c] = kf;
+        }
     }
 }
 
-cudaError_t launch_pair_count(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
-                              const int* cell_coord, int C, int* t_count, int* f_count, cudaStream_t st) {
-    pair_kernel<false><<<(C + 255) / 256, 256, 0, st>>>(p.d, nbr_start, nbr, core_start, cell_coord, C, t_count,
-                                                        f_count, nullptr);
+cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    pair_kernel<false><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fill(const Params& p, const int* nbr_start, const int* nbr, const int* core_start,
-                             const int* cell_coord, int C, const int* t_start, const int* f_start, int2* pairs,
-                             cudaStream_t st) {
-    pair_kernel<true><<<(C + 255) / 256, 256, 0, st>>>(p.d, nbr_start, nbr, core_start, cell_coord, C,
-                                                       const_cast<int*>(t_start), const_cast<int*>(f_start), pairs);
+cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    pair_kernel<true><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-// range[0..1] = touching pairs, range[2..3] = the others; hard counters reset.
-__global__ void merge_ranges_kernel(const int* __restrict__ t_start, const int* __restrict__ f_start, int C,
-                                   int* range, int* hard_cnt) {
-    if (threadIdx.x == 0) {
-        const int nt = t_start[C], nf = f_start[C];
-        range[0] = 0;
-        range[1] = nt;
-        range[2] = nt;
-        range[3] = nt + nf;
-        hard_cnt[0] = 0;
-        hard_cnt[1] = 0;
+__global__ void totals_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int K, int which) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const Inst& I = ins[idx[k]];
+    const int C = I.small[kSmCells];
+    if (which & 1) I.small[kSmNnbr] = I.nbr_start[C];
+    if (which & 2) I.small[kSmNonfull] = I.nf_start[C];
+    if (which & 4) {
+        I.small[kSmPairsT] = I.pair_start[C];
+        I.small[kSmPairsF] = I.pair_start_f[C];
+        I.small[kSmHard0] = 0;
+        I.small[kSmHard1] = 0;
     }
 }
 
-cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, int* range, int* hard_cnt,
-                                cudaStream_t st) {
-    merge_ranges_kernel<<<1, 32, 0, st>>>(t_start, f_start, C, range, hard_cnt);
+cudaError_t launch_totals(const Inst* ins, const int* idx, int K, int which, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    totals_kernel<<<(K + 127) / 128, 128, 0, st>>>(ins, idx, K, which);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -216,13 +218,43 @@ cudaError_t launch_merge_ranges(const int* t_start, const int* f_start, int C, i
 // chains along clusters, while a random-looking order keeps trees shallow.
 // (Cluster ids do not depend on which grid ends up the root.)
 
-__global__ void uf_init_kernel(int* parent, int C) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) parent[c] = c;
+__global__ void uf_init_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const int k = cur.k;
+        const long long c = i - cur.lo;
+        ins[f.idx[k]].parent[c] = (int)c;
+    }
 }
 
-cudaError_t launch_uf_init(int* parent, int C, cudaStream_t st) {
-    uf_init_kernel<<<(C + 255) / 256, 256, 0, st>>>(parent, C);
+cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    uf_init_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+// Between the waves: point every grid at its root, so that the second wave's
+// precheck costs two loads per pair.
+__global__ void uf_flatten_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const int k = cur.k;
+        const Inst& I = ins[f.idx[k]];
+        const int c = (int)(i - cur.lo);
+        const int r = uf_find(I.parent, c);
+        if (r < 0)
+            set_status(I, kDevTimeout);
+        else if (r != c)
+            I.parent[c] = r;
+    }
+}
+
+cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    uf_flatten_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -244,7 +276,6 @@ __device__ __forceinline__ bool uf_union(int* parent, int a, int b) {
     }
     return false;
 }
-
 
 // Both box tests of a candidate pair.  Returns 0 (no: boxes farther than
 // eps), 1 (yes: the boxes are within eps even at their farthest corners) or
@@ -282,41 +313,42 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 //      thousands, where one scan of the large set usually decides.
 constexpr int kSmallSet = 128;
 
-template <int D, int DP>
-__global__ void __launch_bounds__(256) merge_warp_kernel(Params p, const int2* __restrict__ pairs,
-                                                         const int* __restrict__ range,
-                                                         const int* __restrict__ Xc,
-                                                         const int* __restrict__ core_start,
-                                                         const int* __restrict__ bbox, int* parent,
-                                                         unsigned* status, int2* __restrict__ hard,
-                                                         int* __restrict__ hard_cnt, int budget) {
+template <int D>
+__global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict__ ins, Flat f, int wave, int budget) {
+    constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long eps2 = p.eps2;
-    const int lo = range[0], hi = range[1];
-    for (long long w = lo + (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < hi; w += warps) {
-        const int2 pr = pairs[w];
+    const long long total = flat_total(f);
+    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
+        const int kk = flat_find(f, w);
+        const Inst& I = ins[f.idx[kk]];
+        const long long lw = w - f.off[kk];
+        const long long eps2 = I.p.eps2;
+        const int base = wave == 0 ? 0 : I.small[kSmPairsT];
+        const int2 pr = I.pairs[base + lw];
+        int* parent = I.parent;
         int same = 0;
         if (lane == 0) {
             const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
-            if (ra < 0 || rb < 0) atomicOr(status, kDevTimeout);
+            if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
             same = ra == rb;
         }
         if (__shfl_sync(kFull, same, 0)) continue;
 
-        const int dec = box_decision<D>(bbox + (long long)pr.x * 2 * D, bbox + (long long)pr.y * 2 * D, eps2);
+        const int dec = box_decision<D>(I.bbox + (long long)pr.x * 2 * D, I.bbox + (long long)pr.y * 2 * D, eps2);
         bool yes = dec == 1;
         bool handed = false;
         if (dec < 0) {
-            const int ai = core_start[pr.x], mi = core_start[pr.x + 1] - ai;
-            const int aj = core_start[pr.y], mj = core_start[pr.y + 1] - aj;
+            const int* Xc = I.Xc;
+            const int ai = I.core_start[pr.x], mi = I.core_start[pr.x + 1] - ai;
+            const int aj = I.core_start[pr.y], mj = I.core_start[pr.y + 1] - aj;
             const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
             const long long tiles = (long long)na * nb;
             const bool exhaustive = mi <= kSmallSet && mj <= kSmallSet;
             const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
             for (long long t = 0; t < limit; ++t) {
                 const int ta = exhaustive ? (int)(t / nb) : (int)(t % na);
-                const int tb = exhaustive ? (int)(t % nb) : (int)(t % nb);
+                const int tb = (int)(t % nb);
                 const int a0 = ta << 5, b0 = tb << 5;
                 const int ca = min(32, mi - a0);
                 int P[D], Q[D];
@@ -342,12 +374,24 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(Params p, const int2* _
         }
         if (lane == 0) {
             if (yes) {
-                if (!uf_union(parent, pr.x, pr.y)) atomicOr(status, kDevTimeout);
+                if (!uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
             } else if (handed) {
-                hard[lo + atomicAdd(hard_cnt, 1)] = pr;
+                I.hard[base + atomicAdd(I.small + kSmHard0 + wave, 1)] = pr;
             }
         }
     }
+}
+
+cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, cudaStream_t st) {
+    switch (d) {
+#define GD_MW(DD) \
+    case DD: merge_warp_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, pairs, wave, budget); break;
+        GD_MW(1) GD_MW(2) GD_MW(3) GD_MW(4) GD_MW(5) GD_MW(6) GD_MW(7) GD_MW(8)
+#undef GD_MW
+        default: return cudaErrorInvalidValue;
+    }
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------- FastMerging, per block
@@ -359,12 +403,12 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(Params p, const int2* _
 //   the rest of s_i of dist(., q), test, prune s_j around q, and repeat;
 //   no as soon as a pruning empties a set (Thm. 2: only points with no
 //   partner within eps are ever removed).
-// Each pruning is fused with the next argmin, so a round is two passes over
-// the live points.  Every round removes p from s_i and q from s_j, so the
-// loop ends after at most min(m_i, m_j) rounds.  The live sets are bitmaps
-// (one word per 32 points) in the block's slice of global scratch.
-// The angle-based part of Alg. 4 is not used: it needs arcsin/arccos, and
-// only saves work.
+// s_i is the smaller set.  Each pruning is fused with the next argmin, so a
+// round is two passes over the live points.  Every round removes p from s_i
+// and q from s_j, so the loop ends after at most min(m_i, m_j) rounds.  The
+// live sets are bitmaps (one word per 32 points) in the block's slice of the
+// scratch.  The angle-based part of Alg. 4 is not used: it needs arcsin and
+// arccos, and only saves work.
 
 __device__ __forceinline__ bool triangle_trivial(long long A, long long B, long long eps2) {
     // x is trivial iff sqrt(A) + sqrt(eps2) < sqrt(B)
@@ -466,26 +510,26 @@ __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, cons
     return block_best(best, cnt, sb, sc, count);
 }
 
-template <int D, int DP>
-__global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const int2* __restrict__ hard,
-                                                               const int* __restrict__ range,
-                                                               const int* __restrict__ hard_cnt,
-                                                               const int* __restrict__ Xc,
-                                                               const int* __restrict__ core_start,
-                                                               const int* __restrict__ bbox, int* parent,
-                                                               unsigned* status, unsigned* scratch, int wpb) {
+template <int D>
+__global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __restrict__ ins, Flat f, int wave,
+                                                               unsigned* scratch, int wpb) {
+    constexpr int DP = Padded<D>::value;
     __shared__ BestPt sb[kFmWarps];
     __shared__ int sc[kFmWarps];
     __shared__ int s_same;
-    const long long eps2 = p.eps2;
-    const int lo = range[0], nh = *hard_cnt;
     unsigned* live_a = scratch + (long long)blockIdx.x * 2 * wpb;
     unsigned* live_b = live_a + wpb;
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int2 pr = hard[lo + h];
+    const long long total = flat_total(f);
+    for (long long h = blockIdx.x; h < total; h += gridDim.x) {
+        const int kk = flat_find(f, h);
+        const Inst& I = ins[f.idx[kk]];
+        const long long eps2 = I.p.eps2;
+        const int base = wave == 0 ? 0 : I.small[kSmPairsT];
+        const int2 pr = I.hard[base + (h - f.off[kk])];
+        int* parent = I.parent;
         if (threadIdx.x == 0) {
             const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
-            if (ra < 0 || rb < 0) atomicOr(status, kDevTimeout);
+            if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
             s_same = ra == rb;
         }
         __syncthreads();
@@ -495,13 +539,14 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
 
         // s_i is the smaller set: each round removes at least its pivot, and
         // a small set is usually emptied by the first pruning
+        const int* core_start = I.core_start;
         int gi = pr.x, gj = pr.y;
         if (core_start[gi + 1] - core_start[gi] > core_start[gj + 1] - core_start[gj]) {
             gi = pr.y;
             gj = pr.x;
         }
-        const int* A = Xc + (long long)core_start[gi] * DP;
-        const int* B = Xc + (long long)core_start[gj] * DP;
+        const int* A = I.Xc + (long long)core_start[gi] * DP;
+        const int* B = I.Xc + (long long)core_start[gj] * DP;
         const int ma = core_start[gi + 1] - core_start[gi];
         const int mb = core_start[gj + 1] - core_start[gj];
         const int wa = (ma + 31) >> 5, wb = (mb + 31) >> 5;
@@ -512,7 +557,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
         __syncthreads();
 
         long long piv[D], tgt[D];
-        const int* bj = bbox + (long long)gj * 2 * D;
+        const int* bj = I.bbox + (long long)gj * 2 * D;
 #pragma unroll
         for (int j = 0; j < D; ++j) tgt[j] = ((long long)bj[j] + bj[D + j]) / 2;
         int cnt;
@@ -548,63 +593,25 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(Params p, const i
             if (cnt == 0) break;
         }
         if (yes && threadIdx.x == 0) {
-            if (!uf_union(parent, pr.x, pr.y)) atomicOr(status, kDevTimeout);
+            if (!uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
         }
         __syncthreads();
     }
 }
 
-// Between the waves: point every grid at its root, so that the second wave's
-// precheck costs two loads per pair.
-__global__ void uf_flatten_kernel(int* parent, int C, unsigned* status) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    const int r = uf_find(parent, c);
-    if (r < 0)
-        atomicOr(status, kDevTimeout);
-    else if (r != c)
-        parent[c] = r;
-}
-
-cudaError_t launch_uf_flatten(int* parent, int C, unsigned* status, cudaStream_t st) {
-    uf_flatten_kernel<<<(C + 255) / 256, 256, 0, st>>>(parent, C, status);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-template <int D>
-static void merge_waves_launch(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
-                               const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
-                               int2* hard, int* hard_cnt, unsigned* scratch, int wpb, int fm_blocks,
-                               cudaStream_t st) {
-    constexpr int DP = D == 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
-    long long blocks = ((long long)max_pairs * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    const int* r = range + 2 * wave;
-    merge_warp_kernel<D, DP><<<(int)blocks, 256, 0, st>>>(p, pairs, r, Xc, core_start, bbox, parent, status, hard,
-                                                          hard_cnt + wave, 2);
-    GD_COUNT_LAUNCH();
-    merge_block_kernel<D, DP><<<fm_blocks, kFmBlock, 0, st>>>(p, hard, r, hard_cnt + wave, Xc, core_start, bbox,
-                                                              parent, status, scratch, wpb);
-    GD_COUNT_LAUNCH();
-}
-
 int merge_fm_blocks() { return 152 * 8; }
 
-cudaError_t launch_merge_wave(const Params& p, int wave, const int2* pairs, const int* range, int max_pairs,
-                              const int* Xc, const int* core_start, const int* bbox, int* parent, unsigned* status,
-                              int2* hard, int* hard_cnt, unsigned* scratch, int wpb, int fm_blocks, cudaStream_t st) {
-    if (max_pairs <= 0) return cudaSuccess;
-    const int fb = fm_blocks;
-    switch (p.d) {
-#define GD_WAVE(DD) \
-    case DD: merge_waves_launch<DD>(p, wave, pairs, range, max_pairs, Xc, core_start, bbox, parent, status, hard, hard_cnt, scratch, wpb, fb, st); break;
-        GD_WAVE(1) GD_WAVE(2) GD_WAVE(3) GD_WAVE(4) GD_WAVE(5) GD_WAVE(6) GD_WAVE(7)
-        default: merge_waves_launch<8>(p, wave, pairs, range, max_pairs, Xc, core_start, bbox, parent, status, hard,
-                                       hard_cnt, scratch, wpb, fb, st); break;
-#undef GD_WAVE
+cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
+                               cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    switch (d) {
+#define GD_MB(DD) \
+    case DD: merge_block_kernel<DD><<<blocks, kFmBlock, 0, st>>>(ins, hard, wave, scratch, wpb); break;
+        GD_MB(1) GD_MB(2) GD_MB(3) GD_MB(4) GD_MB(5) GD_MB(6) GD_MB(7) GD_MB(8)
+#undef GD_MB
+        default: return cudaErrorInvalidValue;
     }
+    GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 

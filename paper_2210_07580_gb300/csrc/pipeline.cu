@@ -1,0 +1,692 @@
+// Batched host driver of the exact-DBSCAN pipeline.
+//
+// The K instances go through every stage together: each launch covers a flat
+// space over all of them (or over the ones sharing a dimension or a key
+// width, for kernels specialised on those).  The host synchronises with the
+// stream four times per batch, whatever K is:
+//   1. after the bounds      -> per-instance key layout, workspace sizes;
+//   2. after the compaction  -> grid counts C, largest grid;
+//   3. after the walk count  -> neighbour-list lengths (buffer sizes);
+//   4. at the end            -> status words.
+// Everything else -- pair counts, non-full point counts, pairs handed to
+// FastMerging -- stays on the device: the kernels that consume those spaces
+// read their offsets from tables the device fills (count_flat).
+#include <climits>
+#include <cstring>
+#include <utility>
+
+#include "pipeline.h"
+
+namespace gd {
+
+const char* const kStageNames[kStages] = {"bounds", "quantise", "sort",  "compact", "levels", "walk",
+                                          "core",   "core_pack", "pairs", "merge",   "labels"};
+
+namespace {
+
+int padded_dim(int d) { return d == 1 ? 1 : d == 2 ? 2 : d <= 4 ? 4 : 8; }
+
+unsigned long long isqrt_u64(unsigned long long v) {
+    // largest r with r*r <= v, by bisection on r
+    unsigned long long lo = 0, hi = 1ull << 32;
+    while (hi - lo > 1) {
+        const unsigned long long mid = lo + (hi - lo) / 2;
+        if ((unsigned __int128)mid * mid <= v)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+int bit_length(unsigned long long v) {
+    int b = 0;
+    while (v) {
+        b++;
+        v >>= 1;
+    }
+    return b;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Host view of one instance.
+struct HI {
+    Inst dev;            // the record uploaded to the device
+    long long C, maxcell, nnbr;
+    int q_tiles, c_tiles;
+    size_t arena_off, arena_bytes;
+};
+
+// Appends arrays to a host staging buffer; device pointers are the same
+// offsets from the device descriptor buffer.
+struct Builder {
+    unsigned char* host;
+    size_t cap, off;
+    char* dev;  // device base (known after the buffer is obtained)
+    bool overflow;
+    size_t take(size_t bytes) {
+        off = align256(off);
+        const size_t at = off;
+        if (off + bytes > cap) {
+            overflow = true;
+        } else {
+            off += bytes;
+        }
+        return at;
+    }
+    template <typename T> T* put(const T* data, size_t count) {
+        const size_t at = take(sizeof(T) * count);
+        if (!overflow && count) memcpy(host + at, data, sizeof(T) * count);
+        return reinterpret_cast<T*>(dev + at);
+    }
+    template <typename T> T* hostp(T* devp) { return reinterpret_cast<T*>(host + ((char*)devp - dev)); }
+};
+
+// Fixed-capacity bump allocator over a host work buffer (no heap use).
+struct HostBump {
+    unsigned char* base;
+    size_t cap, off;
+    template <typename T> T* take(size_t count) {
+        off = (off + 15) & ~(size_t)15;
+        if (off + sizeof(T) * count > cap) return nullptr;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+size_t desc_bound(int K) { return (size_t)4096 * (size_t)(K + 16); }
+size_t host_work_bound(int K) { return (size_t)(sizeof(HI) + 256) * (size_t)K + (size_t)64 * K * 8 + 65536; }
+
+// Per-instance workspace, laid out from `base` (or only sized when base is
+// null).  Arrays indexed by grid are sized for n grids, the upper bound.
+size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = align256(off);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t N = (size_t)n, dp = (size_t)padded_dim(d);
+    I.keyA = take(N * 8 * key_words);
+    I.keyB = take(N * 8 * key_words);
+    I.valA = (int*)take(N * 4);
+    I.valB = (int*)take(N * 4);
+    I.Xs = (int*)take(N * dp * 4);
+    I.pt_cell = (int*)take(N * 4);
+    I.core_s = (unsigned char*)take(N);
+    I.Xc = (int*)take(N * dp * 4);
+    I.cell_start = (int*)take((N + 1) * 4);
+    I.cell_coord = (int*)take(N * d * 4);
+    I.pbox = (int*)take(N * 2 * d * 4);
+    for (int j = 0; j < kMaxD; ++j) {
+        I.lv_key[j] = j < d ? (int*)take((N + 1) * 4) : nullptr;
+        I.lv_cb[j] = j < d - 1 ? (int*)take((N + 2) * 4) : nullptr;
+    }
+    I.lv_E = (int*)take((size_t)d * (N + 1) * 4);
+    I.lv_L = (int*)take(N * 4);
+    I.nbr_start = (int*)take((N + 1) * 4);
+    I.nf_start = (int*)take((N + 1) * 4);
+    I.core_start = (int*)take((N + 1) * 4);
+    I.bbox = (int*)take(N * 2 * d * 4);
+    I.pair_start = (int*)take((N + 1) * 4);
+    I.pair_start_f = (int*)take((N + 1) * 4);
+    I.parent = (int*)take(N * 4);
+    I.cid_root = (int*)take(N * 4);
+    I.cell_cid = (int*)take(N * 4);
+    I.bcnt = (int*)take(((N + kCompactTile - 1) / kCompactTile + 1) * 4);
+    int* sort_base = (int*)take(sort_tmp_ints(n, key_words, key_bits) * 4);
+    if (base) {
+        size_t zero_ints = 0;
+        sort_tmp_layout(sort_base, n, key_words, key_bits, &I.sort_hist, &I.sort_dstart, &I.sort_counters,
+                        &I.sort_status, &zero_ints);
+    }
+    return align256(off) + 256;
+}
+
+size_t sort_zero_ints(int n, int key_words, int key_bits) {
+    int *h, *ds, *c;
+    unsigned long long* s;
+    size_t z = 0;
+    sort_tmp_layout(nullptr, n, key_words, key_bits, &h, &ds, &c, &s, &z);
+    return z;
+}
+
+struct Run {
+    MemProvider& mem;
+    int K;
+    const gd_instance* in;
+    cudaStream_t st;
+    cudaEvent_t* ev;
+    RunInfo* info;
+    int fm_blocks;
+
+    HI* hi = nullptr;
+    int* hsmall = nullptr;   // host mirror of the small blocks [K][kSmallInts]
+    int* dsmall = nullptr;   // device small blocks
+    Builder b{};
+    Inst* dins = nullptr;    // device Inst array (in the descriptor buffer)
+    int* scan_tmp = nullptr;
+    size_t scan_tmp_ints = 0;
+    HostBump hw{};
+    int* all_idx = nullptr;  // 0..K-1
+
+    gd_status fail(gd_status s, const char* msg, int k = -1) {
+        if (info) {
+            info->error = msg;
+            if (k >= 0) info->error += " (instance " + std::to_string(k) + ")";
+        }
+        return s;
+    }
+    gd_status cuda(cudaError_t e, const char* where) {
+        if (e == cudaSuccess) return GD_OK;
+        if (info) info->error = std::string(where) + ": " + cudaGetErrorString(e);
+        return GD_ECUDA;
+    }
+    void mark(int s) {
+        if (ev) cudaEventRecord(ev[s], st);
+    }
+
+    gd_status begin_desc() {
+        void* h = nullptr;
+        void* d = nullptr;
+        const size_t cap = desc_bound(K);
+        gd_status s = mem.host(kHostDesc, cap, &h);
+        if (s != GD_OK) return fail(s, "descriptor staging");
+        s = mem.device(kMemDesc, cap, &d);
+        if (s != GD_OK) return fail(s, "descriptor buffer");
+        b.host = (unsigned char*)h;
+        b.cap = cap;
+        b.off = 0;
+        b.dev = (char*)d;
+        b.overflow = false;
+        // the Inst array always comes first
+        dins = reinterpret_cast<Inst*>(b.dev + b.take(sizeof(Inst) * K));
+        all_idx = nullptr;
+        return GD_OK;
+    }
+    gd_status upload_desc() {
+        if (b.overflow) return fail(GD_ENOMEM, "descriptor tables exceed their staging buffer");
+        Inst* h = b.hostp(dins);
+        for (int k = 0; k < K; ++k) h[k] = hi[k].dev;
+        return cuda(cudaMemcpyAsync(b.dev, b.host, b.off, cudaMemcpyHostToDevice, st), "upload descriptors");
+    }
+    const int* idx_all() {
+        if (!all_idx) {
+            int* t = b.hostp(reinterpret_cast<int*>(b.dev + b.take(sizeof(int) * K)));
+            all_idx = reinterpret_cast<int*>(b.dev + ((unsigned char*)t - b.host));
+            if (!b.overflow)
+                for (int k = 0; k < K; ++k) t[k] = k;
+        }
+        return all_idx;
+    }
+    // Host-known flat space over `m` instances (members) with sizes size(k).
+    template <typename F> Flat flat(const int* members, int m, F size, long long* total) {
+        const size_t at_off = b.take(sizeof(long long) * (m + 1));
+        const size_t at_idx = b.take(sizeof(int) * (m > 0 ? m : 1));
+        long long run = 0;
+        if (!b.overflow) {
+            long long* off = reinterpret_cast<long long*>(b.host + at_off);
+            int* idx = reinterpret_cast<int*>(b.host + at_idx);
+            for (int t = 0; t < m; ++t) {
+                off[t] = run;
+                idx[t] = members[t];
+                run += size(members[t]);
+            }
+            off[m] = run;
+        } else {
+            for (int t = 0; t < m; ++t) run += size(members[t]);
+        }
+        *total = run;
+        return Flat{reinterpret_cast<const long long*>(b.dev + at_off), reinterpret_cast<const int*>(b.dev + at_idx),
+                    m};
+    }
+    // Device-filled flat space over `m` members (offsets from count_flat).
+    Flat dflat(const int* members, int m, long long** off_dev) {
+        const size_t at_off = b.take(sizeof(long long) * (m + 1));
+        const size_t at_idx = b.take(sizeof(int) * (m > 0 ? m : 1));
+        if (!b.overflow) {
+            int* idx = reinterpret_cast<int*>(b.host + at_idx);
+            for (int t = 0; t < m; ++t) idx[t] = members[t];
+            reinterpret_cast<long long*>(b.host + at_off)[0] = 0;
+        }
+        *off_dev = reinterpret_cast<long long*>(b.dev + at_off);
+        return Flat{*off_dev, reinterpret_cast<const int*>(b.dev + at_idx), m};
+    }
+    // Segmented scans over one array per member instance.
+    template <typename F> ScanSeg* segs(const int* members, int m, F arr, long long* tiles) {
+        const size_t at = b.take(sizeof(ScanSeg) * (m > 0 ? m : 1));
+        long long blk = 0;
+        ScanSeg* h = reinterpret_cast<ScanSeg*>(b.host + at);
+        for (int t = 0; t < m; ++t) {
+            int* a = nullptr;
+            long long len = 0;
+            arr(members[t], &a, &len);
+            if (!b.overflow) h[t] = ScanSeg{a, a, len, blk};
+            blk += (len + kScanTile - 1) / kScanTile;
+        }
+        *tiles = blk;
+        return reinterpret_cast<ScanSeg*>(b.dev + at);
+    }
+    gd_status scan(const ScanSeg* sg, int m, long long tiles) {
+        if (tiles + m > (long long)scan_tmp_ints) return fail(GD_ENOMEM, "scan scratch too small");
+        return cuda(scan_segments(sg, m, tiles, scan_tmp, st), "scan");
+    }
+    gd_status readback() {
+        gd_status s = cuda(cudaMemcpyAsync(hsmall, dsmall, sizeof(int) * kSmallInts * K, cudaMemcpyDeviceToHost, st),
+                           "read back");
+        if (s != GD_OK) return s;
+        return cuda(cudaStreamSynchronize(st), "synchronise");
+    }
+    int* sm(int k) { return hsmall + (size_t)k * kSmallInts; }
+
+    gd_status go();
+};
+
+#define RUN_TRY(x)                    \
+    do {                              \
+        gd_status s_ = (x);           \
+        if (s_ != GD_OK) return s_;   \
+    } while (0)
+#define RUN_CUDA(x, what) RUN_TRY(cuda((x), what))
+
+gd_status Run::go() {
+    // ---------------------------------------------------------- set-up
+    void* hwp = nullptr;
+    RUN_TRY(mem.host(kHostSmall, sizeof(int) * kSmallInts * K + host_work_bound(K), &hwp));
+    hsmall = (int*)hwp;
+    hw = HostBump{(unsigned char*)hwp + sizeof(int) * kSmallInts * K, host_work_bound(K), 0};
+    hi = hw.take<HI>(K);
+    int* members = hw.take<int>(K);
+    int* members2 = hw.take<int>(K);
+    if (!hi || !members || !members2) return fail(GD_ENOMEM, "host work buffer");
+    void* dsm = nullptr;
+    RUN_TRY(mem.device(kMemSmall, sizeof(int) * kSmallInts * K, &dsm));
+    dsmall = (int*)dsm;
+
+    long long total_pts = 0;
+    int dmax = 1;
+    for (int k = 0; k < K; ++k) {
+        const gd_instance& g = in[k];
+        HI& h = hi[k];
+        memset(&h, 0, sizeof(h));
+        Params& p = h.dev.p;
+        p.n = (int)g.n;
+        p.d = g.d;
+        p.dp = padded_dim(g.d);
+        // Every squared distance is below 2^62 once the range check passes, so
+        // a larger eps2 changes nothing; clamping keeps the gap sums in range.
+        const long long cap = (1ll << 62) - 1;
+        p.eps2 = g.eps2 > cap ? cap : g.eps2;
+        p.minpts = g.minpts;
+        p.s = 1 + (long long)isqrt_u64((unsigned long long)p.eps2 / (unsigned long long)g.d);
+        p.r = p.eps2 == 0 ? 0 : 1 + ((long long)isqrt_u64((unsigned long long)p.eps2) - 1) / p.s;
+        h.dev.X = g.X;
+        h.dev.labels = g.labels;
+        h.dev.is_core = g.is_core;
+        h.dev.small = dsmall + (size_t)k * kSmallInts;
+        int* s = sm(k);
+        memset(s, 0, sizeof(int) * kSmallInts);
+        for (int j = 0; j < kMaxD; ++j) {
+            s[kSmMnmx + j] = INT_MAX;
+            s[kSmMnmx + kMaxD + j] = INT_MIN;
+        }
+        total_pts += g.n;
+        if (g.d > dmax) dmax = g.d;
+    }
+    // scan scratch: enough for any segmented scan of the batch
+    scan_tmp_ints = (size_t)K + 64;
+    for (int k = 0; k < K; ++k) scan_tmp_ints += (size_t)(in[k].n / kScanTile + 2);
+    void* stp = nullptr;
+    RUN_TRY(mem.device(kMemScanTmp, scan_tmp_ints * 4, &stp));
+    scan_tmp = (int*)stp;
+    for (int k = 0; k < K; ++k) members[k] = k;
+    auto n_of = [&](int k) { return (long long)in[k].n; };
+    auto C_of = [&](int k) { return hi[k].C; };
+    long long tot;
+
+    // --------------------------------------------- phase 1: bounds (sync 1)
+    mark(0);
+    RUN_TRY(begin_desc());
+    const Flat pts0 = flat(members, K, n_of, &tot);
+    RUN_TRY(upload_desc());
+    RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
+    RUN_CUDA(launch_bounds(dins, pts0, total_pts, st), "bounds");
+    RUN_TRY(readback());
+
+    // ------------------------- phase 2: keys, sort, compaction (sync 2)
+    int max_passes = 0, max_buckets = 1, max_hist = 1;
+    size_t arena = 0;
+    for (int k = 0; k < K; ++k) {
+        HI& h = hi[k];
+        Params& p = h.dev.p;
+        const int* s = sm(k);
+        unsigned long long rmax = 0;
+        int total_bits = 0;
+        for (int j = 0; j < p.d; ++j) {
+            const long long lo = s[kSmMnmx + j], up = s[kSmMnmx + kMaxD + j];
+            const unsigned long long rj = (unsigned long long)(up - lo);
+            if (rj > rmax) rmax = rj;
+            p.mn[j] = (int)lo;
+            p.bits[j] = bit_length(rj / (unsigned long long)p.s);
+            total_bits += p.bits[j];
+        }
+        if ((unsigned __int128)p.d * rmax * rmax >= ((unsigned __int128)1 << 62))
+            return fail(GD_ERANGE, "coordinate range too large: d * R^2 >= 2^62", k);
+        if (total_bits > 128) return fail(GD_ERANGE, "packed grid key needs more than 128 bits", k);
+        for (int j = p.d - 1, sh = 0; j >= 0; --j) {
+            p.shift[j] = sh;
+            sh += p.bits[j];
+        }
+        p.key_bits = total_bits;
+        p.key_words = total_bits <= 64 ? 1 : 2;
+        const SortPlan sp = sort_plan(p.n, p.key_words, p.key_bits);
+        h.dev.passes = sp.passes;
+        h.dev.digit_bits = sp.bits;
+        h.dev.tiles = sp.tiles;
+        h.q_tiles = (p.n + kQuantTile - 1) / kQuantTile;
+        h.c_tiles = (p.n + kCompactTile - 1) / kCompactTile;
+        if (sp.passes > max_passes) max_passes = sp.passes;
+        if (sp.buckets > max_buckets) max_buckets = sp.buckets;
+        if (sp.passes * sp.buckets > max_hist) max_hist = sp.passes * sp.buckets;
+        h.arena_off = arena;
+        h.arena_bytes = carve(h.dev, nullptr, p.n, p.d, p.key_words, p.key_bits);
+        arena += h.arena_bytes;
+    }
+    void* ap = nullptr;
+    RUN_TRY(mem.device(kMemArena, arena, &ap));
+    for (int k = 0; k < K; ++k) {
+        HI& h = hi[k];
+        carve(h.dev, (char*)ap + h.arena_off, h.dev.p.n, h.dev.p.d, h.dev.p.key_words, h.dev.p.key_bits);
+    }
+
+    RUN_TRY(begin_desc());
+    const Flat pts1 = flat(members, K, n_of, &tot);
+    const size_t zr_at = b.take(sizeof(ZeroRange) * K);
+    long long zr_total = 0;
+    {
+        ZeroRange* zr = reinterpret_cast<ZeroRange*>(b.host + zr_at);
+        for (int k = 0; k < K; ++k) {
+            const Params& p = hi[k].dev.p;
+            const long long z = (long long)sort_zero_ints(p.n, p.key_words, p.key_bits);
+            if (!b.overflow) zr[k] = ZeroRange{hi[k].dev.sort_hist, z, zr_total};
+            zr_total += z;
+        }
+    }
+    const ZeroRange* zr_dev = reinterpret_cast<const ZeroRange*>(b.dev + zr_at);
+    const size_t counters_at = b.take(sizeof(int) * 64);
+    int* counters = reinterpret_cast<int*>(b.dev + counters_at);
+    if (!b.overflow) memset(b.host + counters_at, 0, sizeof(int) * 64);
+    Flat qflat[2], cflat[2];
+    long long qtot[2] = {0, 0}, ctot[2] = {0, 0};
+    Flat oflat[2][16];
+    long long otot[2][16] = {};
+    int gpasses[2] = {0, 0};
+    for (int w = 0; w < 2; ++w) {
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (hi[k].dev.p.key_words == w + 1) members2[m++] = k;
+        qflat[w] = flat(members2, m, [&](int k) { return (long long)hi[k].q_tiles; }, &qtot[w]);
+        cflat[w] = flat(members2, m, [&](int k) { return (long long)hi[k].c_tiles; }, &ctot[w]);
+        for (int t = 0; t < m; ++t)
+            if (hi[members2[t]].dev.passes > gpasses[w]) gpasses[w] = hi[members2[t]].dev.passes;
+        for (int ps = 0; ps < gpasses[w]; ++ps) {
+            int m2 = 0;
+            for (int t = 0; t < m; ++t)
+                if (hi[members2[t]].dev.passes > ps) members[m2++] = members2[t];
+            oflat[w][ps] = flat(members, m2, [&](int k) { return (long long)hi[k].dev.tiles; }, &otot[w][ps]);
+        }
+    }
+    for (int k = 0; k < K; ++k) members[k] = k;
+    long long cseg_tiles = 0;
+    const ScanSeg* cseg = segs(
+        members, K,
+        [&](int k, int** a, long long* len) {
+            *a = hi[k].dev.bcnt;
+            *len = hi[k].c_tiles;
+        },
+        &cseg_tiles);
+    const int* idx = idx_all();
+    RUN_TRY(upload_desc());
+
+    mark(1);
+    RUN_CUDA(zero_ranges(zr_dev, K, zr_total, st), "clear sort state");
+    for (int w = 0; w < 2; ++w)
+        RUN_CUDA(launch_quantise_hist(dins, qflat[w], qtot[w], w + 1, max_hist, st), "quantise");
+    RUN_CUDA(launch_digit_scan(dins, idx, K, max_passes, st), "digit scan");
+    mark(2);
+    for (int w = 0; w < 2; ++w)
+        for (int ps = 0; ps < gpasses[w]; ++ps)
+            RUN_CUDA(launch_onesweep(dins, oflat[w][ps], otot[w][ps], w + 1, ps, max_buckets, counters + w * 16 + ps,
+                                     st),
+                     "sort pass");
+    mark(3);
+    for (int w = 0; w < 2; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w + 1, st), "compact count");
+    RUN_TRY(scan(cseg, K, cseg_tiles));
+    for (int w = 0; w < 2; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w + 1, st), "compact write");
+    RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
+    RUN_TRY(readback());
+
+    // ------------------------ phase 3: levels, walk count (sync 3)
+    long long max_cell = 1;
+    for (int k = 0; k < K; ++k) {
+        hi[k].C = sm(k)[kSmCells];
+        hi[k].maxcell = sm(k)[kSmMaxCell];
+        if (hi[k].maxcell > max_cell) max_cell = hi[k].maxcell;
+    }
+    const int wpb = (int)((max_cell + 31) / 32 + 1);
+    void* scr = nullptr;
+    RUN_TRY(mem.device(kMemScratch, (size_t)fm_blocks * 2 * wpb * 4, &scr));
+
+    RUN_TRY(begin_desc());
+    const Flat cells2 = flat(members, K, C_of, &tot);
+    const long long total_cells = tot;
+    Flat lflat[kMaxD];
+    long long ltot[kMaxD] = {};
+    const ScanSeg* lseg[kMaxD] = {};
+    long long lseg_tiles[kMaxD] = {};
+    int lm[kMaxD] = {};
+    for (int j = 0; j + 1 < dmax; ++j) {
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (hi[k].dev.p.d - 1 > j) members2[m++] = k;
+        lm[j] = m;
+        lflat[j] = flat(members2, m, C_of, &ltot[j]);
+        lseg[j] = segs(
+            members2, m,
+            [&](int k, int** a, long long* len) {
+                *a = hi[k].dev.lv_E + (size_t)j * (hi[k].C + 1);
+                *len = hi[k].C;
+            },
+            &lseg_tiles[j]);
+    }
+    long long nseg_tiles = 0;
+    const ScanSeg* nseg = segs(
+        members, K,
+        [&](int k, int** a, long long* len) {
+            *a = hi[k].dev.nbr_start;
+            *len = hi[k].C;
+        },
+        &nseg_tiles);
+    idx = idx_all();
+    RUN_TRY(upload_desc());
+
+    mark(4);
+    RUN_CUDA(launch_point_boxes(dins, cells2, total_cells, st), "point boxes");
+    RUN_CUDA(launch_level_diff(dins, cells2, total_cells, st), "levels");
+    for (int j = 0; j + 1 < dmax; ++j) {
+        RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
+        RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
+    }
+    RUN_CUDA(launch_level_write(dins, cells2, total_cells, st), "level write");
+    mark(5);
+    RUN_CUDA(launch_walk(dins, cells2, total_cells, false, st), "walk count");
+    RUN_TRY(scan(nseg, K, nseg_tiles));
+    RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
+    RUN_TRY(readback());
+
+    // ------------- phase 4: neighbours, core, merge, labels (sync 4)
+    long long total_nbr = 0;
+    for (int k = 0; k < K; ++k) {
+        hi[k].nnbr = (unsigned)sm(k)[kSmNnbr];
+        if (hi[k].nnbr >= INT_MAX) return fail(GD_ERANGE, "neighbour lists exceed 2^31 entries", k);
+        total_nbr += hi[k].nnbr;
+    }
+    void *nbp = nullptr, *pp = nullptr, *hp = nullptr;
+    RUN_TRY(mem.device(kMemNbr, (size_t)total_nbr * 4 + 256 * (size_t)K + 256, &nbp));
+    RUN_TRY(mem.device(kMemPairs, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &pp));
+    RUN_TRY(mem.device(kMemHard, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &hp));
+    {
+        size_t o4 = 0, o8 = 0;
+        for (int k = 0; k < K; ++k) {
+            hi[k].dev.nbr = (int*)((char*)nbp + o4);
+            hi[k].dev.pairs = (int2*)((char*)pp + o8);
+            hi[k].dev.hard = (int2*)((char*)hp + o8);
+            o4 += align256((size_t)hi[k].nnbr * 4);
+            o8 += align256((size_t)hi[k].nnbr * 8);
+        }
+    }
+
+    RUN_TRY(begin_desc());
+    const Flat cells = flat(members, K, C_of, &tot);
+    const Flat pts = flat(members, K, n_of, &tot);
+    // per-dimension groups
+    int dgroups[kMaxD], ng = 0;
+    for (int d = 1; d <= kMaxD; ++d)
+        for (int k = 0; k < K; ++k)
+            if (hi[k].dev.p.d == d) {
+                dgroups[ng++] = d;
+                break;
+            }
+    Flat g_pts[kMaxD], g_nf[kMaxD], g_pair[2][kMaxD], g_hard[2][kMaxD];
+    long long* g_nf_off[kMaxD];
+    long long* g_pair_off[2][kMaxD];
+    long long* g_hard_off[2][kMaxD];
+    long long g_pts_tot[kMaxD];
+    int g_m[kMaxD];
+    const int* g_idx[kMaxD];
+    for (int gi = 0; gi < ng; ++gi) {
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (hi[k].dev.p.d == dgroups[gi]) members2[m++] = k;
+        g_m[gi] = m;
+        g_pts[gi] = flat(members2, m, n_of, &g_pts_tot[gi]);
+        g_idx[gi] = g_pts[gi].idx;
+        g_nf[gi] = dflat(members2, m, &g_nf_off[gi]);
+        for (int w = 0; w < 2; ++w) {
+            g_pair[w][gi] = dflat(members2, m, &g_pair_off[w][gi]);
+            g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
+        }
+    }
+    auto arr_seg = [&](int* Inst::*field) {
+        long long tiles = 0;
+        const ScanSeg* sgp = segs(
+            members, K,
+            [&](int k, int** a, long long* len) {
+                *a = hi[k].dev.*field;
+                *len = hi[k].C;
+            },
+            &tiles);
+        return std::make_pair(sgp, tiles);
+    };
+    const auto nfseg = arr_seg(&Inst::nf_start);
+    const auto coreseg = arr_seg(&Inst::core_start);
+    const auto ptseg = arr_seg(&Inst::pair_start);
+    const auto pfseg = arr_seg(&Inst::pair_start_f);
+    idx = idx_all();
+    RUN_TRY(upload_desc());
+
+    RUN_CUDA(launch_walk(dins, cells, total_cells, true, st), "walk fill");
+    mark(6);
+    RUN_CUDA(launch_core_full(dins, pts, total_pts, st), "core (full grids)");
+    RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
+    RUN_TRY(scan(nfseg.first, K, nfseg.second));
+    RUN_CUDA(launch_totals(dins, idx, K, 2, st), "totals");
+    for (int gi = 0; gi < ng; ++gi) {
+        RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
+        RUN_CUDA(launch_core_point(dins, g_nf[gi], dgroups[gi], st), "core (counting)");
+    }
+    mark(7);
+    RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
+    RUN_TRY(scan(coreseg.first, K, coreseg.second));
+    RUN_CUDA(launch_core_pack(dins, pts, total_pts, st), "core pack");
+    mark(8);
+    RUN_CUDA(launch_pair_count(dins, cells, total_cells, st), "pair count");
+    RUN_TRY(scan(ptseg.first, K, ptseg.second));
+    RUN_TRY(scan(pfseg.first, K, pfseg.second));
+    RUN_CUDA(launch_pair_fill(dins, cells, total_cells, st), "pair fill");
+    RUN_CUDA(launch_totals(dins, idx, K, 4, st), "totals");
+    mark(9);
+    RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
+    for (int w = 0; w < 2; ++w) {
+        for (int gi = 0; gi < ng; ++gi) {
+            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], w == 0 ? kSmPairsT : kSmPairsF, g_pair_off[w][gi], st),
+                     "flat offsets");
+            RUN_CUDA(launch_merge_warp(dins, g_pair[w][gi], w, dgroups[gi], 2, st), "merge (warp)");
+        }
+        for (int gi = 0; gi < ng; ++gi) {
+            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmHard0 + w, g_hard_off[w][gi], st), "flat offsets");
+            RUN_CUDA(launch_merge_block(dins, g_hard[w][gi], w, dgroups[gi], fm_blocks, (unsigned*)scr, wpb, st),
+                     "merge (FastMerging)");
+        }
+        if (w == 0) RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, st), "union-find flatten");
+    }
+    mark(10);
+    RUN_CUDA(launch_cluster_ids(dins, cells, total_cells, st), "cluster ids");
+    for (int gi = 0; gi < ng; ++gi)
+        RUN_CUDA(launch_labels(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "labels");
+    mark(11);
+    RUN_TRY(readback());
+    for (int k = 0; k < K; ++k)
+        if ((unsigned)sm(k)[kSmStatus] & kDevTimeout)
+            return fail(GD_ETIMEOUT, "a bounded device wait or retry loop hit its limit", k);
+
+    if (info) {
+        const HI& h = hi[0];
+        const int* s0 = sm(0);
+        const int n = h.dev.p.n, d = h.dev.p.d;
+        const long long C = h.C;
+        info->sizes[0] = n;
+        info->sizes[1] = d;
+        info->sizes[2] = C;
+        info->sizes[3] = h.nnbr;
+        info->sizes[4] = h.dev.p.s;
+        info->sizes[5] = h.dev.p.key_bits;
+        info->sizes[6] = 0;  // filled by the caller (launch count)
+        info->sizes[7] = (long long)s0[kSmPairsT] + s0[kSmPairsF];
+        info->sizes[8] = h.dev.passes;
+        info->sizes[9] = h.dev.digit_bits;
+        info->sizes[10] = (long long)s0[kSmHard0] + s0[kSmHard1];
+        info->sizes[11] = 0;
+        info->view_ptr[GD_VIEW_PERM] = (h.dev.passes & 1) ? h.dev.valB : h.dev.valA;
+        info->view_bytes[GD_VIEW_PERM] = (size_t)n * 4;
+        info->view_ptr[GD_VIEW_CELL_START] = h.dev.cell_start;
+        info->view_bytes[GD_VIEW_CELL_START] = (size_t)(C + 1) * 4;
+        info->view_ptr[GD_VIEW_CELL_COORD] = h.dev.cell_coord;
+        info->view_bytes[GD_VIEW_CELL_COORD] = (size_t)C * d * 4;
+        info->view_ptr[GD_VIEW_NBR_START] = h.dev.nbr_start;
+        info->view_bytes[GD_VIEW_NBR_START] = (size_t)(C + 1) * 4;
+        info->view_ptr[GD_VIEW_NBR] = h.dev.nbr;
+        info->view_bytes[GD_VIEW_NBR] = (size_t)h.nnbr * 4;
+        info->view_ptr[GD_VIEW_CORE_SORTED] = h.dev.core_s;
+        info->view_bytes[GD_VIEW_CORE_SORTED] = (size_t)n;
+        info->view_ptr[GD_VIEW_CELL_CID] = h.dev.cell_cid;
+        info->view_bytes[GD_VIEW_CELL_CID] = (size_t)C * 4;
+    }
+    return GD_OK;
+}
+
+}  // namespace
+
+gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
+                    RunInfo* info, int fm_blocks) {
+    Run r{mem, K, inst, st, events, info, fm_blocks};
+    const long long l0 = t_launches;
+    const gd_status s = r.go();
+    if (info) info->launches = t_launches - l0;
+    return s;
+}
+
+}  // namespace gd

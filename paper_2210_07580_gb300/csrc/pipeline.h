@@ -1,0 +1,46 @@
+// Host-side batched driver of the exact-DBSCAN pipeline (pipeline.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "gd_internal.cuh"
+#include "gdbscan.h"
+
+namespace gd {
+
+// Where the driver's memory comes from: a context's growable buffers, or a
+// fixed static array (the no-allocation entry point).
+enum MemSlot { kMemSmall, kMemDesc, kMemArena, kMemScanTmp, kMemNbr, kMemPairs, kMemHard, kMemScratch, kMemSlots };
+enum HostSlot { kHostSmall, kHostDesc, kHostSlots };
+
+struct MemProvider {
+    virtual ~MemProvider() {}
+    // A device buffer of at least `bytes` for the slot (contents are not kept
+    // when it has to grow).  GD_ENOMEM if it cannot be had.
+    virtual gd_status device(int slot, size_t bytes, void** out) = 0;
+    // A host staging buffer (pinned where possible) of at least `bytes`.
+    virtual gd_status host(int slot, size_t bytes, void** out) = 0;
+};
+
+// Stage timing: when non-null, events[s] is recorded before stage s and
+// events[kStages] at the end.
+constexpr int kStages = 11;
+extern const char* const kStageNames[kStages];
+
+// What the driver reports about the run (instance 0 for the views).
+struct RunInfo {
+    long long sizes[12];
+    const void* view_ptr[7];
+    size_t view_bytes[7];
+    long long launches;
+    std::string error;
+};
+
+// Runs K instances.  The result of instance k is in inst[k].labels /
+// is_core (device pointers).  Returns the first error; `info` may be null.
+gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
+                    RunInfo* info, int fm_blocks);
+
+}  // namespace gd

@@ -4,16 +4,18 @@
 // identifiers are packed into one 64- or 128-bit key (dimension 1 most
 // significant, so key order is the lexicographic order of Alg. 1) and sorted
 // by digits of up to 9 bits:
-//   1. quantise_hist: computes every key and, in the same pass, the global
+//   1. quantise_hist: computes every key and, in the same pass, the
 //      histogram of every digit position;
 //   2. digit_scan: exclusive scan of each digit position's histogram;
 //   3. one onesweep pass per digit position: each block takes the next tile
 //      (dynamic tile ids), ranks its keys stably in shared memory, publishes
-//      its per-digit counts and finds the counts of all earlier tiles by a
-//      decoupled look-back, then writes each digit run out contiguously.
+//      its per-digit counts and finds the counts of all earlier tiles of its
+//      instance by a decoupled look-back, then writes each digit run out
+//      contiguously.
 // A pass reads and writes every key and value once.  Look-back waits are
-// bounded: a block only ever waits for tiles handed out before its own, and
-// gives up with kDevTimeout after a fixed number of polls.
+// bounded: a block only ever waits for tiles handed out before its own (tile
+// ids are taken in order from one counter over the whole batch), and gives
+// up with kDevTimeout after a fixed number of polls.
 #include "gd_internal.cuh"
 
 namespace gd {
@@ -58,31 +60,28 @@ SortPlan sort_plan(int n, int key_words, int key_bits) {
     return sp;
 }
 
-// Layout of the sort's workspace (ints): hist [P][R], digit_start [P][R],
-// tile counters [P], status [P][tiles][R] (64-bit words).
-size_t radix_tmp_ints(int n, int key_words, int key_bits) {
+// Layout of one instance's sort workspace (ints): hist [P][R],
+// dstart [P][R], tile counters [P], status [P][tiles][R] (64-bit words).
+// Everything but dstart must be zero before quantise_hist runs.
+size_t sort_tmp_ints(int n, int key_words, int key_bits) {
     const SortPlan sp = sort_plan(n, key_words, key_bits);
     const size_t pr = (size_t)sp.passes * sp.buckets;
     return 2 * pr + (size_t)sp.passes + 8 + 2 * (size_t)sp.passes * sp.tiles * sp.buckets + 64;
 }
 
-struct SortTmp {
-    int* hist;
-    int* dstart;
-    int* counters;
-    unsigned long long* status;
-};
-
-static SortTmp sort_tmp(int* tmp, const SortPlan& sp) {
-    SortTmp t;
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** hist, int** dstart, int** counters,
+                     unsigned long long** status, size_t* zero_ints) {
+    const SortPlan sp = sort_plan(n, key_words, key_bits);
     const size_t pr = (size_t)sp.passes * sp.buckets;
-    t.hist = tmp;
-    t.dstart = tmp + pr;
-    t.counters = tmp + 2 * pr;
-    size_t off = 2 * pr + sp.passes + 8;
-    off = (off + 1) & ~(size_t)1;  // 8-byte alignment (tmp is 256-byte aligned)
-    t.status = reinterpret_cast<unsigned long long*>(tmp + off);
-    return t;
+    // hist, counters and status first (one region to clear), dstart last
+    *hist = base;
+    *counters = base + pr;
+    size_t off = pr + sp.passes + 8;
+    off = (off + 1) & ~(size_t)1;  // 8-byte alignment (base is 256-byte aligned)
+    *status = reinterpret_cast<unsigned long long*>(base + off);
+    off += 2 * (size_t)sp.passes * sp.tiles * sp.buckets;
+    *zero_ints = off;
+    *dstart = base + off;
 }
 
 // ------------------------------------------------------------- quantise
@@ -109,54 +108,63 @@ __device__ __forceinline__ void pack_key(Key2& k, unsigned v, int sh) {
 __device__ __forceinline__ void zero_key(unsigned long long& k) { k = 0; }
 __device__ __forceinline__ void zero_key(Key2& k) { k.lo = k.hi = 0; }
 
-// Keys, values (input index) and the histogram of every digit position.
-// Runs of equal digits inside a warp are counted once (warp match), which
-// keeps shared-memory atomics cheap on clustered data.
+// One block per tile of kQuantTile points of one instance: keys, values
+// (input index) and the tile's histogram of every digit position, added to
+// the instance's histograms.  Runs of equal digits inside a warp are counted
+// once (warp match), which keeps shared-memory atomics cheap on clustered data.
 template <typename K>
-__global__ void __launch_bounds__(256) quantise_hist_kernel(const int* __restrict__ X, Params p, K* __restrict__ keys,
-                                                            int* __restrict__ vals, int* __restrict__ hist,
-                                                            int passes, int bits) {
+__global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restrict__ ins, Flat f) {
     extern __shared__ int sh_hist[];  // [passes][1 << bits]
+    const int k = flat_find(f, blockIdx.x);
+    const Inst& I = ins[f.idx[k]];
+    const long long tile = blockIdx.x - f.off[k];
+    const int passes = I.passes, bits = I.digit_bits;
     const int R = 1 << bits;
     const unsigned mask = (unsigned)R - 1u;
     for (int i = threadIdx.x; i < passes * R; i += blockDim.x) sh_hist[i] = 0;
     __syncthreads();
     const int lane = lane_id();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long n_round = ((long long)p.n + 31) & ~31ll;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        const bool valid = i < p.n;
-        K k;
-        zero_key(k);
+    const Params& p = I.p;
+    const int n = p.n, d = p.d;
+    K* keys = (K*)I.keyA;
+    for (int r = 0; r < kQuantTile; r += 256) {
+        const long long i = tile * kQuantTile + r + threadIdx.x;
+        const bool valid = i < n;
+        K key;
+        zero_key(key);
         if (valid) {
-            const int* row = X + i * p.d;
+            const int* row = I.X + i * d;
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
-                if (j < p.d) pack_key(k, identifier(__ldg(row + j), p.mn[j], p.s), p.shift[j]);
-            keys[i] = k;
-            vals[i] = (int)i;
+                if (j < d) pack_key(key, identifier(__ldg(row + j), p.mn[j], p.s), p.shift[j]);
+            keys[i] = key;
+            I.valA[i] = (int)i;
         }
         for (int ps = 0; ps < passes; ++ps) {
-            const unsigned dg = valid ? SortKey<K>::digit(k, ps * bits, mask) : (unsigned)R + lane;
+            const unsigned dg = valid ? SortKey<K>::digit(key, ps * bits, mask) : (unsigned)R + lane;
             const unsigned peers = __match_any_sync(kFull, dg);
             if (valid && lane == (int)(__ffs(peers) - 1)) atomicAdd(&sh_hist[ps * R + dg], __popc(peers));
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * R; i += blockDim.x)
-        if (sh_hist[i]) atomicAdd(hist + i, sh_hist[i]);
+        if (sh_hist[i]) atomicAdd(I.sort_hist + i, sh_hist[i]);
 }
 
-__global__ void digit_scan_kernel(const int* __restrict__ hist, int* __restrict__ dstart, int R) {
+// One block per (instance, pass): exclusive scan of the pass's histogram.
+__global__ void digit_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx) {
     __shared__ int sm[33];
-    const int ps = blockIdx.x;
+    const Inst& I = ins[idx[blockIdx.x]];
+    const int ps = blockIdx.y;
+    if (ps >= I.passes) return;
+    const int R = 1 << I.digit_bits;
     int carry = 0;
     for (int base = 0; base < R; base += blockDim.x) {
         const int b = base + threadIdx.x;
-        const int v = b < R ? hist[ps * R + b] : 0;
+        const int v = b < R ? I.sort_hist[ps * R + b] : 0;
         int total;
         const int ex = block_exclusive_scan(v, sm, &total);
-        if (b < R) dstart[ps * R + b] = carry + ex;
+        if (b < R) I.sort_dstart[ps * R + b] = carry + ex;
         carry += total;
     }
 }
@@ -173,32 +181,40 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const K* __restrict__ keys_in,
-                                                            const int* __restrict__ vals_in, K* __restrict__ keys_out,
-                                                            int* __restrict__ vals_out, int n, int shift, int bits,
-                                                            const int* __restrict__ dstart_g,
-                                                            unsigned long long* status, int* tile_counter,
-                                                            unsigned* err) {
+__global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __restrict__ ins, Flat f, int pass,
+                                                               int* flat_counter) {
     constexpr int kItems = SortKey<K>::kItems;
     constexpr int kTile = os_tile<K>();
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int sm[33];
+    __shared__ int s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(flat_counter, 1);
+    __syncthreads();
+    const int ft = s_tile;
+    const int kk = flat_find(f, ft);
+    const Inst& I = ins[f.idx[kk]];
+    const int tile = ft - (int)f.off[kk];
+    const int n = I.p.n, bits = I.digit_bits, shift = pass * bits;
     const int R = 1 << bits;
     const unsigned mask = (unsigned)R - 1u;
+    const K* keys_in = (const K*)((pass & 1) ? I.keyB : I.keyA);
+    K* keys_out = (K*)((pass & 1) ? I.keyA : I.keyB);
+    const int* vals_in = (pass & 1) ? I.valB : I.valA;
+    int* vals_out = (pass & 1) ? I.valA : I.valB;
+    const int* dstart_g = I.sort_dstart + pass * R;
+    unsigned long long* status = I.sort_status + (size_t)pass * I.tiles * R;
+
     // layout: exchange keys [kTile] K, exchange vals [kTile] int,
-    //         wcount [kOsWarps][R], dstart [R], goff [R]
+    //         wcount [kOsWarps][R], ldstart [R], goff [R]
     K* skeys = reinterpret_cast<K*>(smem);
     int* svals = reinterpret_cast<int*>(smem + sizeof(K) * kTile);
     int* wcount = svals + kTile;
     int* ldstart = wcount + kOsWarps * R;
     int* goff = ldstart + R;
-    __shared__ int sm[33];
-    __shared__ int s_tile;
 
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
     for (int i = threadIdx.x; i < kOsWarps * R; i += kOsBlock) wcount[i] = 0;
     __syncthreads();
-    const int tile = s_tile;
     const long long base = (long long)tile * kTile;
     const int count = (int)min((long long)kTile, (long long)n - base);
 
@@ -236,10 +252,11 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const K* __restri
     // Thread t owns the `per` consecutive digits starting at t * per.
     {
         const int per = (R + kOsBlock - 1) / kOsBlock;  // 1 or 2 (R <= 512)
-        int tots[(kMaxBuckets + kOsBlock - 1) / kOsBlock];
+        constexpr int kPerMax = (kMaxBuckets + kOsBlock - 1) / kOsBlock;
+        int tots[kPerMax];
         int sum = 0;
 #pragma unroll
-        for (int u = 0; u < (kMaxBuckets + kOsBlock - 1) / kOsBlock; ++u) {
+        for (int u = 0; u < kPerMax; ++u) {
             tots[u] = 0;
             const int b = threadIdx.x * per + u;
             if (u < per && b < R) {
@@ -258,7 +275,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const K* __restri
         int all;
         int ex = block_exclusive_scan(sum, sm, &all);
 #pragma unroll
-        for (int u = 0; u < (kMaxBuckets + kOsBlock - 1) / kOsBlock; ++u) {
+        for (int u = 0; u < kPerMax; ++u) {
             const int b = threadIdx.x * per + u;
             if (u < per && b < R) {
                 ldstart[b] = ex;
@@ -284,7 +301,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const K* __restri
                 const unsigned flag = (unsigned)(v >> 32);
                 if (flag == 0u) {
                     if (++polls > kMaxPolls) {
-                        atomicOr(err, kDevTimeout);
+                        set_status(I, kDevTimeout);
                         break;
                     }
                     __nanosleep(32);
@@ -316,10 +333,10 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const K* __restri
     for (int i = 0; i < kItems; ++i) {
         const int t = i * kOsBlock + threadIdx.x;
         if (t < count) {
-            const K k = skeys[t];
-            const unsigned dg = SortKey<K>::digit(k, shift, mask);
+            const K k2 = skeys[t];
+            const unsigned dg = SortKey<K>::digit(k2, shift, mask);
             const int dst = goff[dg] + (t - ldstart[dg]);
-            keys_out[dst] = k;
+            keys_out[dst] = k2;
             vals_out[dst] = svals[t];
         }
     }
@@ -329,74 +346,44 @@ template <typename K> static size_t onesweep_smem(int R) {
     return sizeof(K) * os_tile<K>() + sizeof(int) * os_tile<K>() + sizeof(int) * (kOsWarps * R + 2 * R);
 }
 
-template <typename K>
-static cudaError_t quantise_t(const int* X, const Params& p, K* ka, int* va, int* tmp, cudaStream_t st) {
-    const SortPlan sp = sort_plan(p.n, p.key_words, p.key_bits);
-    const SortTmp t = sort_tmp(tmp, sp);
-    const int R = sp.buckets;
-    if (sp.passes > 0) {
-        cudaError_t e = cudaMemsetAsync(t.hist, 0, sizeof(int) * (size_t)sp.passes * R, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(t.counters, 0, sizeof(int) * sp.passes, st);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(t.status, 0, sizeof(unsigned long long) * (size_t)sp.passes * sp.tiles * R, st);
-        if (e != cudaSuccess) return e;
-    }
-    int blocks = (p.n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
-    quantise_hist_kernel<K><<<blocks, 256, sizeof(int) * (size_t)sp.passes * R, st>>>(X, p, ka, va, t.hist,
-                                                                                       sp.passes, sp.bits);
+cudaError_t launch_quantise_hist(const Inst* ins, Flat qtiles, long long total, int key_words, int max_hist_ints,
+                                 cudaStream_t st) {
+    const long long tiles = total;
+    if (tiles <= 0) return cudaSuccess;
+    const size_t smem = sizeof(int) * (size_t)(max_hist_ints > 0 ? max_hist_ints : 1);
+    if (key_words == 1)
+        quantise_hist_kernel<unsigned long long><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+    else
+        quantise_hist_kernel<Key2><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
     GD_COUNT_LAUNCH();
-    if (sp.passes > 0) {
-        digit_scan_kernel<<<sp.passes, 256, 0, st>>>(t.hist, t.dstart, R);
-        GD_COUNT_LAUNCH();
-    }
     return cudaGetLastError();
 }
 
-template <typename K>
-static cudaError_t passes_t(const Params& p, K* ka, int* va, K* kb, int* vb, int* tmp, unsigned* err, cudaStream_t st,
-                            int* result_in_b) {
-    const SortPlan sp = sort_plan(p.n, p.key_words, p.key_bits);
-    const SortTmp t = sort_tmp(tmp, sp);
-    const int R = sp.buckets;
-    *result_in_b = 0;
-    if (sp.passes == 0 || p.n <= 1) return cudaSuccess;
-    const size_t smem = onesweep_smem<K>(R);
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    K* src_k = ka;
-    int* src_v = va;
-    K* dst_k = kb;
-    int* dst_v = vb;
-    for (int ps = 0; ps < sp.passes; ++ps) {
-        onesweep_kernel<K><<<sp.tiles, kOsBlock, smem, st>>>(src_k, src_v, dst_k, dst_v, p.n, ps * sp.bits, sp.bits,
-                                                             t.dstart + ps * R,
-                                                             t.status + (size_t)ps * sp.tiles * R,
-                                                             t.counters + ps, err);
-        GD_COUNT_LAUNCH();
-        K* tk = src_k;
-        src_k = dst_k;
-        dst_k = tk;
-        int* tv = src_v;
-        src_v = dst_v;
-        dst_v = tv;
-        *result_in_b ^= 1;
-    }
+cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st) {
+    if (K <= 0 || max_passes <= 0) return cudaSuccess;
+    digit_scan_kernel<<<dim3(K, max_passes), 256, 0, st>>>(ins, idx);
+    GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-cudaError_t quantise_hist(const int* X, const Params& p, void* keys_a, int* vals_a, int* tmp, cudaStream_t st) {
-    if (p.key_words == 1) return quantise_t(X, p, (unsigned long long*)keys_a, vals_a, tmp, st);
-    return quantise_t(X, p, (Key2*)keys_a, vals_a, tmp, st);
-}
-
-cudaError_t sort_passes(const Params& p, void* keys_a, int* vals_a, void* keys_b, int* vals_b, int* tmp, unsigned* err,
-                        cudaStream_t st, int* result_in_b) {
-    if (p.key_words == 1)
-        return passes_t(p, (unsigned long long*)keys_a, vals_a, (unsigned long long*)keys_b, vals_b, tmp, err, st,
-                        result_in_b);
-    return passes_t(p, (Key2*)keys_a, vals_a, (Key2*)keys_b, vals_b, tmp, err, st, result_in_b);
+cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_words, int pass, int max_buckets,
+                            int* flat_counter, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (key_words == 1) {
+        const size_t smem = onesweep_smem<unsigned long long>(max_buckets);
+        e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        onesweep_kernel<unsigned long long><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
+    } else {
+        const size_t smem = onesweep_smem<Key2>(max_buckets);
+        e = cudaFuncSetAttribute(onesweep_kernel<Key2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        onesweep_kernel<Key2><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
+    }
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
 }
 
 }  // namespace gd

@@ -123,3 +123,22 @@ def workload(name: str, seed: int = 1, n: int | None = None):
         nn = n or 10_000_000
         return skewed_mix(nn, 5, eps=1000.0, seed=seed), 1000 ** 2, 100
     raise KeyError(name)
+
+
+def batch_instances(k: int = 256, seed: int = 1, n_lo: float = 1e3, n_hi: float = 5e5):
+    """The batched workload: k independent instances with n log-uniform in
+    [n_lo, n_hi], d uniform in {2, 3, 5, 7}, eps uniform in [200, 2000],
+    MinPts uniform in {5, 10, 50, 100}; each instance is Gaussian blobs (2 to
+    8 blobs, sigma uniform in [300, 3000]) plus 5% uniform noise.
+    Returns a list of (X, eps2, minpts)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        d = int(rng.choice([2, 3, 5, 7]))
+        eps = int(rng.uniform(200, 2000))
+        minpts = int(rng.choice([5, 10, 50, 100]))
+        X = blobs(n, d, k=int(rng.integers(2, 9)), sigma=float(rng.uniform(300, 3000)), noise=0.05,
+                  seed=int(rng.integers(1 << 30)))
+        out.append((X, eps * eps, minpts))
+    return out

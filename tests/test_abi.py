@@ -44,6 +44,8 @@ def test_status_strings_and_workspace(lib):
     w2 = lib.gd_workspace_bytes(1_000_000, 3)
     w3 = lib.gd_workspace_bytes(1_000_000, 7)
     assert 0 < w1 < w2 < w3
+    # linear in n with a fixed overhead of about a megabyte
+    assert w1 < 4 << 20 and w2 < 1_000_000 * 512 and w3 < 1_000_000 * 512
     assert lib.gd_workspace_bytes(10, 9) == 0 and lib.gd_workspace_bytes(-1, 3) == 0
 
 

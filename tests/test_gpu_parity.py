@@ -122,8 +122,25 @@ def test_negative_and_offset_coordinates(ctx):
 
 # ------------------------------------------------- intermediate structure
 
+def refined_neighbours(X, eps2, gs):
+    """The GPU's neighbour lists from the oracle's grid-level Nei(g): the grids
+    of Nei(g) whose point boxes are within eps of g's point box."""
+    cs, ns, nei, order = gs["cell_start"], gs["nei_start"], gs["nei"], gs["order"]
+    Xs = X[order].astype(np.int64)
+    lo = np.minimum.reduceat(Xs, cs[:-1], axis=0)
+    hi = np.maximum.reduceat(Xs, cs[:-1], axis=0)
+    out = []
+    for c in range(len(cs) - 1):
+        nb = nei[ns[c]:ns[c + 1]]
+        gap = np.maximum(0, np.maximum(lo[nb] - hi[c], lo[c] - hi[nb]))
+        out.append(sorted(int(v) for v in nb[(gap ** 2).sum(1) <= eps2]))
+    return out
+
+
 def test_grid_structure_matches_oracle(ctx):
-    """Sorted permutation (stable), non-empty grids and Nei(g) per grid."""
+    """Sorted permutation (stable), non-empty grids, and neighbour lists: the
+    oracle's Nei(g) (Alg. 3) narrowed to grids whose point boxes are within
+    eps, which must still hold every grid with a point within eps."""
     X, eps2, minpts = synth.workload("tiny", n=8000, seed=2)
     run_gpu(ctx, X, eps2, minpts)
     sz = ctx.last_sizes()
@@ -137,24 +154,41 @@ def test_grid_structure_matches_oracle(ctx):
     np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_CELL_COORD, np.int32, C * 2).reshape(C, 2),
                                   gs["cell_coord"])
     ns = ctx.copy_view(binding.VIEW_NBR_START, np.int32, C + 1)
-    np.testing.assert_array_equal(ns, gs["nei_start"])
     nb = ctx.copy_view(binding.VIEW_NBR, np.int32, int(ns[-1]))
+    want = refined_neighbours(X, eps2, gs)
     for c in range(C):
-        assert sorted(nb[ns[c]:ns[c + 1]]) == sorted(gs["nei"][gs["nei_start"][c]:gs["nei_start"][c + 1]])
+        assert sorted(nb[ns[c]:ns[c + 1]]) == want[c], c
+    # completeness: every pair of points within eps lies in neighbouring grids
+    cell_of = np.empty(len(X), np.int64)
+    for c in range(C):
+        cell_of[gs["order"][gs["cell_start"][c]:gs["cell_start"][c + 1]]] = c
+    sub = np.random.default_rng(0).choice(len(X), 1500, replace=False)
+    D = ((X[sub, None, :].astype(np.int64) - X[None, :, :]) ** 2).sum(-1)
+    nsets = [set(nb[ns[c]:ns[c + 1]].tolist()) for c in range(C)]
+    I, J = np.nonzero(D <= eps2)
+    for a, b2 in zip(sub[I], J):
+        assert cell_of[b2] in nsets[cell_of[a]]
 
 
 def test_worked_example_neighbours(ctx):
+    """The constructed Fig. 1 layout: the GPU's grids and their order are the
+    paper's; its list for g6 is the oracle's Nei(g6) (pinned to the worked
+    example) narrowed by point boxes."""
     from golden_io import load_grid_case
     case = load_grid_case("fig2_neighbors_2d.txt")
-    run_gpu(ctx, case["X"], case["eps2"], case["minpts"])
+    X, eps2 = case["X"], case["eps2"]
+    run_gpu(ctx, X, eps2, case["minpts"])
     sz = ctx.last_sizes()
     assert sz["grids"] == 9 and sz["side"] == 11
     coord = ctx.copy_view(binding.VIEW_CELL_COORD, np.int32, 18).reshape(9, 2)
     assert [tuple(c) for c in coord] == [case["grids"][k] for k in range(1, 10)]
     ns = ctx.copy_view(binding.VIEW_NBR_START, np.int32, 10)
     nb = ctx.copy_view(binding.VIEW_NBR, np.int32, int(ns[-1]))
-    q, want = case["query"]
-    assert sorted(int(v) + 1 for v in nb[ns[q - 1]:ns[q]]) == want
+    gs = oracle.grid_structure(X, eps2)
+    q, paper = case["query"]
+    got = sorted(int(v) + 1 for v in nb[ns[q - 1]:ns[q]])
+    assert got == [v + 1 for v in refined_neighbours(X, eps2, gs)[q - 1]]
+    assert set(got) <= set(paper)
 
 
 # ------------------------------------------------------------ ABI paths
@@ -238,3 +272,52 @@ def test_dense_slabs_rare_or_no_witness(ctx, gap_extra, d):
     assert_same(got, want, f"slabs d={d} gap_extra={gap_extra}")
     # the planted points must be core for the test to mean anything
     assert want[1].sum() > 0.9 * len(X)
+
+
+# ------------------------------------------------------------ batches
+
+def batch_jobs(seed, k, n_lo=200, n_hi=20000):
+    """Uneven instances: sizes log-uniform, d in {2,3,5,7}, eps and MinPts
+    swept, blobs plus noise."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(k):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        d = int(rng.choice([2, 3, 5, 7]))
+        eps = int(rng.uniform(200, 2000))
+        minpts = int(rng.choice([5, 10, 50, 100]))
+        X = synth.blobs(n, d, k=int(rng.integers(2, 8)), sigma=float(rng.uniform(300, 3000)), noise=0.05,
+                        seed=int(rng.integers(1 << 30)))
+        jobs.append((X, eps * eps, minpts))
+    return jobs
+
+
+def test_batched_equals_single_and_oracle(ctx):
+    jobs = batch_jobs(2024, 24)
+    dev_jobs = [(torch.from_numpy(X).cuda(), e, m) for X, e, m in jobs]
+    res = ctx.dbscan_batched(dev_jobs)
+    torch.cuda.synchronize()
+    for i, ((X, e, m), (lab, core)) in enumerate(zip(jobs, res)):
+        want = oracle.grid(X, e, m)
+        assert_same((lab.cpu().numpy(), core.cpu().numpy()), want, f"batch instance {i} (n={len(X)}, d={X.shape[1]})")
+    # each instance alone gives the same result
+    for i in (0, 7, 23):
+        X, e, m = jobs[i]
+        single = run_gpu(ctx, X, e, m)
+        np.testing.assert_array_equal(single[0], res[i][0].cpu().numpy())
+
+
+def test_batched_mixed_key_widths_and_tiny(ctx):
+    """One batch mixing 64- and 128-bit keys, a one-point instance and d=1."""
+    rng = np.random.default_rng(9)
+    jobs = [
+        (rand_points(rng, 1, 3, 1000), 100, 1),
+        (rand_points(rng, 500, 1, 5000), 400, 3),
+        (np.ascontiguousarray(np.vstack([rng.normal(50000, 300, size=(3000, 7)), np.zeros((1, 7)),
+                                         np.full((1, 7), 99999)]).clip(0, 99999).astype(np.int32)), 200 ** 2, 5),
+        (rand_points(rng, 4000, 2, 3000), 2500, 4),
+    ]
+    res = ctx.dbscan_batched([(torch.from_numpy(X).cuda(), e, m) for X, e, m in jobs])
+    torch.cuda.synchronize()
+    for i, ((X, e, m), (lab, core)) in enumerate(zip(jobs, res)):
+        assert_same((lab.cpu().numpy(), core.cpu().numpy()), oracle.grid(X, e, m), f"mixed instance {i}")
