@@ -1,0 +1,240 @@
+"""Continuous-batching server for exact DBSCAN jobs on one GPU.
+
+Clients submit clustering jobs (points, eps2, MinPts) at any time and get a
+future.  A fixed set of slots serves them; each slot owns a gd_ctx (its
+device workspace stays resident and is reused from job to job) and its own
+CUDA stream, and runs on its own host thread, so the work of several slots
+overlaps on the device.  Scheduling:
+
+- admission by HBM footprint: a job is started only when a slot is free and
+  its estimated device footprint fits in what the budget has left; jobs that
+  do not fit wait (small jobs behind them may go first -- backfill);
+- continuous batching: a slot that takes a small job also takes the other
+  small jobs queued at that moment (up to a point and job budget) and runs
+  them as one gd_dbscan_batched call; large jobs run alone;
+- requests that arrive while others are on the GPU join the queue and are
+  admitted as slots and memory free up.
+
+The scheduler is plain Python over a backend object; GpuBackend calls the C
+ABI through the binding (every step of the clustering runs in the CUDA
+library).  Results equal those of the same job run alone (gd_dbscan and
+gd_dbscan_batched give bit-identical labels).
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass(eq=False)  # jobs compare by identity (queue removal)
+class Job:
+    X: np.ndarray
+    eps2: int
+    minpts: int
+    footprint: int
+    t_submit: float
+    future: Future = field(default_factory=Future)
+    t_start: float = 0.0
+    t_done: float = 0.0
+    batch_size: int = 1
+
+    @property
+    def n(self) -> int:
+        return int(self.X.shape[0])
+
+
+def estimate_footprint(n: int, d: int, workspace_bytes) -> int:
+    """Device bytes a job may need: the library's workspace bound, the input
+    and output copies, and room for neighbour lists and pairs (64 entries of
+    4 + 8 + 8 bytes per grid, grids <= points)."""
+    return int(workspace_bytes(n, d)) + n * (4 * d + 5) + n * 64 * 20 // 4
+
+
+class GpuBackend:
+    """Runs jobs through the C ABI: one Context and one CUDA stream per slot.
+    Inputs are staged through pinned host memory, results come back to host
+    numpy arrays."""
+
+    def __init__(self, device: int = 0, slots: int = 4):
+        import torch
+
+        from .binding import Context, workspace_bytes
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.ctxs = [Context(device) for _ in range(slots)]
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.workspace_bytes = workspace_bytes
+
+    def footprint(self, n: int, d: int) -> int:
+        return estimate_footprint(n, d, self.workspace_bytes)
+
+    def run(self, slot: int, jobs):
+        torch = self.torch
+        ctx, stream = self.ctxs[slot], self.streams[slot]
+        with torch.cuda.device(self.device), torch.cuda.stream(stream):
+            dev = []
+            for j in jobs:
+                h = torch.from_numpy(j.X).pin_memory()
+                dev.append((h.to(self.device, non_blocking=True), j.eps2, j.minpts))
+            if len(dev) == 1:
+                Xd, e, m = dev[0]
+                outs = [ctx.dbscan(Xd, e, m, stream=stream)]
+            else:
+                outs = ctx.dbscan_batched(dev, stream=stream)
+            res = [(lab.to("cpu", non_blocking=True), core.to("cpu", non_blocking=True)) for lab, core in outs]
+            stream.synchronize()
+        return [(lab.numpy(), core.numpy().astype(bool)) for lab, core in res]
+
+    def close(self):
+        for c in self.ctxs:
+            c.close()
+
+
+class Server:
+    """See the module docstring.  `backend` defaults to GpuBackend(device,
+    slots); tests pass a fake one."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int | None = None,
+                 small_job_points: int = 200_000, batch_max_jobs: int = 64, batch_max_points: int = 4_000_000,
+                 backend=None):
+        self.backend = backend if backend is not None else GpuBackend(device, slots)
+        if hbm_budget is None:
+            import torch
+            free, _ = torch.cuda.mem_get_info(device)
+            hbm_budget = int(free * 0.6)
+        self.budget = int(hbm_budget)
+        self.in_use = 0
+        self.small = small_job_points
+        self.batch_max_jobs = batch_max_jobs
+        self.batch_max_points = batch_max_points
+        self.queue: collections.deque[Job] = collections.deque()
+        self.cv = threading.Condition()
+        self.closed = False
+        self.done: list[Job] = []
+        self.workers = [threading.Thread(target=self._worker, args=(s,), daemon=True) for s in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    # ------------------------------------------------------------ client
+    def submit(self, X, eps2: int, minpts: int) -> Future:
+        X = np.ascontiguousarray(X, dtype=np.int32)
+        if X.ndim != 2 or X.shape[0] < 1:
+            raise ValueError("X must be a non-empty int32 array of shape [n, d]")
+        fp = self.backend.footprint(X.shape[0], X.shape[1])
+        if fp > self.budget:
+            raise ValueError(f"job needs about {fp} device bytes, more than the server budget {self.budget}")
+        job = Job(X, int(eps2), int(minpts), fp, time.perf_counter())
+        with self.cv:
+            if self.closed:
+                raise RuntimeError("server is closed")
+            self.queue.append(job)
+            self.cv.notify_all()
+        return job.future
+
+    def close(self, wait: bool = True):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+        if wait:
+            for w in self.workers:
+                w.join()
+        close = getattr(self.backend, "close", None)
+        if close:
+            close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------- scheduling
+    def _take(self):
+        """Called with the lock held: the next unit of work that fits the
+        budget, or None.  A large job at the head runs alone; small jobs are
+        coalesced (FIFO) into one batch; when the head does not fit, the first
+        queued job that does is taken (backfill)."""
+        if not self.queue:
+            return None
+        room = self.budget - self.in_use
+        head = self.queue[0]
+        if head.footprint <= room:
+            if head.n > self.small:
+                self.queue.popleft()
+                return [head]
+            batch, pts, fp = [], 0, 0
+            for j in list(self.queue):
+                if j.n > self.small:
+                    continue
+                if len(batch) >= self.batch_max_jobs or pts + j.n > self.batch_max_points or fp + j.footprint > room:
+                    break
+                batch.append(j)
+                pts += j.n
+                fp += j.footprint
+            for j in batch:
+                self.queue.remove(j)
+            return batch
+        for j in self.queue:
+            if j.footprint <= room:
+                self.queue.remove(j)
+                return [j]
+        return None
+
+    def _worker(self, slot: int):
+        while True:
+            with self.cv:
+                work = None
+                while not self.closed or self.queue:
+                    work = self._take()
+                    if work is not None:
+                        break
+                    if self.closed and not self.queue:
+                        break
+                    self.cv.wait(timeout=0.05)
+                if work is None:
+                    return
+                fp = sum(j.footprint for j in work)
+                self.in_use += fp
+            t0 = time.perf_counter()
+            for j in work:
+                j.t_start = t0
+                j.batch_size = len(work)
+            try:
+                results = self.backend.run(slot, work)
+                err = None
+            except Exception as e:  # the jobs fail, the server goes on
+                results, err = None, e
+            t1 = time.perf_counter()
+            with self.cv:
+                self.in_use -= fp
+                for k, j in enumerate(work):
+                    j.t_done = t1
+                    self.done.append(j)
+                self.cv.notify_all()
+            for k, j in enumerate(work):
+                if err is not None:
+                    j.future.set_exception(err)
+                else:
+                    j.future.set_result(results[k])
+
+    # --------------------------------------------------------------- stats
+    def latencies(self):
+        with self.cv:
+            return np.array([j.t_done - j.t_submit for j in self.done])
+
+    def stats(self) -> dict:
+        lat = self.latencies()
+        with self.cv:
+            jobs = list(self.done)
+        if not jobs:
+            return {"jobs": 0}
+        t0 = min(j.t_submit for j in jobs)
+        t1 = max(j.t_done for j in jobs)
+        return {"jobs": len(jobs), "wall_s": t1 - t0, "jobs_per_s": len(jobs) / max(t1 - t0, 1e-9),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_batch": float(np.mean([j.batch_size for j in jobs]))}

@@ -1,0 +1,98 @@
+"""Host-side logic of the continuous-batching server, with a fake backend
+(no GPU): admission by footprint, batching, backfill, routing of results,
+failure propagation and draining on close."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2210_07580_gb300.serve import Server
+
+
+class FakeBackend:
+    """Footprint n * 10 bytes; a run sleeps briefly and returns labels equal
+    to the first coordinate, so each result identifies its job."""
+
+    def __init__(self, fail_on=None):
+        self.lock = threading.Lock()
+        self.calls = []
+        self.in_use = 0
+        self.max_in_use = 0
+        self.fail_on = fail_on
+
+    def footprint(self, n, d):
+        return n * 10
+
+    def run(self, slot, jobs):
+        fp = sum(j.footprint for j in jobs)
+        with self.lock:
+            self.in_use += fp
+            self.max_in_use = max(self.max_in_use, self.in_use)
+            self.calls.append([j.n for j in jobs])
+        time.sleep(0.002 + 1e-7 * sum(j.n for j in jobs))
+        with self.lock:
+            self.in_use -= fp
+        if self.fail_on is not None and any(j.n == self.fail_on for j in jobs):
+            raise RuntimeError("planted failure")
+        return [(j.X[:, 0].copy(), j.X[:, 0] % 2 == 0) for j in jobs]
+
+
+def job(n, tag, d=2):
+    X = np.zeros((n, d), np.int32)
+    X[:, 0] = tag
+    return X
+
+
+def test_results_route_to_their_jobs_and_budget_holds():
+    fb = FakeBackend()
+    with Server(slots=3, hbm_budget=200_000, small_job_points=1000, backend=fb) as srv:
+        futs = [(t, srv.submit(job(50 + (t * 37) % 900, t), 100, 3)) for t in range(120)]
+        for t, f in futs:
+            lab, core = f.result(timeout=30)
+            assert (lab == t).all()
+    assert fb.max_in_use <= 200_000
+    assert any(len(c) > 1 for c in fb.calls), "small jobs were never batched"
+
+
+def test_large_jobs_run_alone_and_small_ones_backfill():
+    fb = FakeBackend()
+    srv = Server(slots=2, hbm_budget=60_000, small_job_points=1000, backend=fb)
+    big = [srv.submit(job(5000, 1000 + t), 1, 1) for t in range(3)]
+    small = [srv.submit(job(100, t), 1, 1) for t in range(20)]
+    for f in big + small:
+        f.result(timeout=30)
+    srv.close()
+    for c in fb.calls:
+        if any(n > 1000 for n in c):
+            assert c == [5000], "a large job shared a batch"
+    assert fb.max_in_use <= 60_000
+
+
+def test_oversized_job_is_refused():
+    srv = Server(slots=1, hbm_budget=1000, backend=FakeBackend())
+    with pytest.raises(ValueError):
+        srv.submit(job(500, 1), 1, 1)
+    srv.close()
+
+
+def test_failures_reach_the_jobs_and_the_server_goes_on():
+    fb = FakeBackend(fail_on=777)
+    with Server(slots=2, hbm_budget=10**9, small_job_points=10, backend=fb) as srv:
+        bad = srv.submit(job(777, 1), 1, 1)
+        good = srv.submit(job(500, 2), 1, 1)
+        with pytest.raises(RuntimeError, match="planted"):
+            bad.result(timeout=30)
+        assert (good.result(timeout=30)[0] == 2).all()
+
+
+def test_close_drains_the_queue_and_stats():
+    fb = FakeBackend()
+    srv = Server(slots=2, hbm_budget=10**9, small_job_points=100, backend=fb)
+    futs = [srv.submit(job(10 + t, t), 1, 1) for t in range(40)]
+    srv.close(wait=True)
+    assert all(f.done() for f in futs)
+    st = srv.stats()
+    assert st["jobs"] == 40 and st["p99_ms"] >= st["p50_ms"] >= 0
+    with pytest.raises(RuntimeError):
+        srv.submit(job(10, 1), 1, 1)
