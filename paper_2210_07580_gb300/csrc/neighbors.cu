@@ -189,6 +189,27 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
     return cudaGetLastError();
 }
 
+// Walk of the levels for one grid (Alg. 3), one warp per query grid.
+//
+// The warp keeps a stack of key ranges in shared memory: (level j, nodes
+// [lo, hi) of level j, partial offset of the path above them).  Each step
+// takes the entries of the top level -- up to 32 nodes across several
+// ranges, the last range possibly split -- and the lanes test one node each:
+// key within +-r, offset within eps (and, at a leaf, the point-box test);
+// surviving inner nodes push their child range (narrowed to keys within +-r
+// by bisection when it is long), surviving leaves are counted (FILL == false,
+// into nbr_start[c]) or written at nbr + nbr_start[c] (FILL == true; both
+// passes visit the nodes in the same order).
+//
+// Stack bound: levels never decrease from the bottom of the stack to its top
+// (a step pops the top level j and pushes level j + 1), so a level receives
+// pushes only when nothing deeper is left, and one step pushes at most 32
+// entries.  Hence at most 32 entries per level below the root: 1 + 32 (d - 1).
+constexpr int kWalkWarps = 4;
+constexpr int kWalkStack = 1 + 32 * (kMaxD - 1);
+// child ranges longer than this are narrowed by bisection before the push
+constexpr int kNarrowAbove = 16;
+
 // First index u in [lo, hi) with key[u] >= v (hi if none).
 __device__ __forceinline__ int lower_key(const int* __restrict__ key, int lo, int hi, long long v) {
     while (lo < hi) {
@@ -201,101 +222,161 @@ __device__ __forceinline__ int lower_key(const int* __restrict__ key, int lo, in
     return lo;
 }
 
-// Depth-first walk of the levels for one grid (Alg. 3).  FILL == false
-// counts the neighbours into nbr_start[c]; FILL == true writes them at
-// nbr + nbr_start[c] in lexicographic order (the query grid itself included).
+struct WalkShared {
+    int lo[kWalkWarps][kWalkStack];
+    int hi[kWalkWarps][kWalkStack];
+    long long part[kWalkWarps][kWalkStack];
+    signed char lvl[kWalkWarps][kWalkStack];
+    long long qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];    // query point box
+    long long klo[kWalkWarps][kMaxD], khi[kWalkWarps][kMaxD];    // key window g_j -+ r
+    long long base[kWalkWarps][kMaxD];                           // mn_j
+};
+
 template <bool FILL>
-__global__ void __launch_bounds__(128) walk_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+__global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    __shared__ WalkShared sh;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    int* const slo = sh.lo[w];
+    int* const shi = sh.hi[w];
+    long long* const spart = sh.part[w];
+    signed char* const slvl = sh.lvl[w];
+    const long long warps = (long long)gridDim.x * kWalkWarps;
+    const unsigned lt = lanemask_lt();
     FlatCursor cur;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        cur.seek(f, i);
-        const int k = cur.k;
-        const Inst& I = ins[f.idx[k]];
-        const long long c = i - cur.lo;
+    for (long long q = (long long)blockIdx.x * kWalkWarps + w; q < total; q += warps) {
+        cur.seek(f, q);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = q - cur.lo;
         const int d = I.p.d;
         const long long r = I.p.r, s = I.p.s, eps2 = I.p.eps2;
-        int g[kMaxD];
-        long long olo[kMaxD], ohi[kMaxD], base[kMaxD];
-        for (int j = 0; j < d; ++j) {
-            g[j] = I.cell_coord[c * d + j];
-            olo[j] = I.pbox[c * 2 * d + j];
-            ohi[j] = I.pbox[c * 2 * d + d + j];
-            base[j] = I.p.mn[j];
+        if (lane < d) {
+            const long long g = I.cell_coord[c * d + lane];
+            sh.qlo[w][lane] = I.pbox[c * 2 * d + lane];
+            sh.qhi[w][lane] = I.pbox[c * 2 * d + d + lane];
+            sh.klo[w][lane] = g - r;
+            sh.khi[w][lane] = g + r;
+            sh.base[w][lane] = I.p.mn[lane];
         }
-        const int* pbox = I.pbox;
-        // refine leaves by point boxes only around small grids
+        __syncwarp();
         const bool refine = I.cell_start[c + 1] - I.cell_start[c] <= kBoxPoints;
-        const int* const* lkey = I.lv_key;
-        const int* const* lcb = I.lv_cb;
-
-        int cur[kMaxD], end[kMaxD];
-        long long part[kMaxD];
+        const int* pbox = I.pbox;
         int* out = FILL ? I.nbr + I.nbr_start[c] : nullptr;
         int found = 0;
+        int top = 0;
+        {
+            const int n0 = I.small[kSmLevelCount];
+            const int a0 = lower_key(I.lv_key[0], 0, n0, sh.klo[w][0]);
+            const int b0 = lower_key(I.lv_key[0], a0, n0, sh.khi[w][0] + 1);
+            if (b0 > a0) {
+                if (lane == 0) {
+                    slo[0] = a0;
+                    shi[0] = b0;
+                    spart[0] = 0;
+                    slvl[0] = 0;
+                }
+                top = 1;
+            }
+        }
+        __syncwarp();
+        while (top > 0) {
+            // the group: the entries of the top level, lane i holding entry top-1-i
+            const int J = slvl[top - 1];
+            const int e = top - 1 - lane;
+            const bool in_group = e >= 0 && slvl[e] == J;
+            int elo = 0, sz = 0;
+            long long epart = 0;
+            if (in_group) {
+                elo = slo[e];
+                sz = min(shi[e] - elo, 64);
+                epart = spart[e];
+            }
+            const int P = warp_inclusive_scan(sz);
+            const int start = P - sz;
+            const int taken = min(32, __shfl_sync(kFull, P, 31));
+            const unsigned starts = __reduce_or_sync(kFull, (in_group && start < 32) ? (1u << start) : 0u);
+            const int consumed = __popc(__ballot_sync(kFull, in_group && P <= 32));
+            // the entry split at 32 nodes keeps its remainder on the stack
+            if (in_group && P > 32 && start < 32) slo[e] = elo + (32 - start);
+            // each lane's node: entry index = number of segment starts at or
+            // below the lane, minus one
+            const int ei = __popc(starts & ((2u << lane) - 1u)) - 1;
+            const int my_lo = __shfl_sync(kFull, elo, ei < 0 ? 0 : ei);
+            const int my_start = __shfl_sync(kFull, start, ei < 0 ? 0 : ei);
+            const long long my_part = __shfl_sync(kFull, epart, ei < 0 ? 0 : ei);
+            top -= consumed;
+            __syncwarp();
 
-        int j = 0;
-        part[0] = 0;
-        end[0] = I.small[kSmLevelCount];
-        cur[0] = lower_key(lkey[0], 0, end[0], (long long)g[0] - r);
-        while (j >= 0) {
-            if (cur[j] >= end[j]) {
-                if (--j >= 0) cur[j]++;
-                continue;
+            const bool act = lane < taken;
+            const int u = my_lo + (lane - my_start);
+            bool ok = false;
+            long long off = 0;
+            if (act) {
+                const long long key = __ldg(I.lv_key[J] + u);
+                if (key >= sh.klo[w][J] && key <= sh.khi[w][J]) {
+                    const long long clo = sh.base[w][J] + key * s, chi = clo + s - 1;
+                    const long long ql = sh.qlo[w][J], qh = sh.qhi[w][J];
+                    long long gap = 0;
+                    if (clo > qh) gap = clo - qh;
+                    else if (ql > chi) gap = ql - chi;
+                    off = my_part + gap * gap;
+                    ok = off <= eps2;
+                }
             }
-            const int u = cur[j];
-            const long long key = __ldg(lkey[j] + u);
-            if (key > (long long)g[j] + r) {
-                if (--j >= 0) cur[j]++;
-                continue;
-            }
-            // gap between the query's point box and the child's key range
-            const long long klo = base[j] + key * s, khi = klo + s - 1;
-            long long gap = 0;
-            if (klo > ohi[j]) gap = klo - ohi[j];
-            else if (olo[j] > khi) gap = olo[j] - khi;
-            const long long off = part[j] + gap * gap;
-            if (off > eps2) {
-                cur[j]++;
-                continue;
-            }
-            if (j == d - 1) {
-                // leaf: the two grids' boxes
-                long long g2 = 0;
-                if (refine) {
+            if (J == d - 1) {
+                // leaf: the two grids' point boxes
+                if (ok && refine) {
                     const int* ub = pbox + (long long)u * 2 * d;
+                    long long g2 = 0;
                     for (int t = 0; t < d; ++t) {
+                        const long long bl = __ldg(ub + t), bh = __ldg(ub + d + t);
+                        const long long ql = sh.qlo[w][t], qh = sh.qhi[w][t];
                         long long gg = 0;
-                        if (ub[t] > ohi[t]) gg = ub[t] - ohi[t];
-                        else if (olo[t] > ub[d + t]) gg = olo[t] - ub[d + t];
+                        if (bl > qh) gg = bl - qh;
+                        else if (ql > bh) gg = ql - bh;
                         g2 += gg * gg;
                     }
+                    ok = g2 <= eps2;
                 }
-                if (g2 <= eps2) {
-                    if (FILL) out[found] = u;
-                    found++;
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (FILL && ok) out[found + __popc(m & lt)] = u;
+                found += __popc(m);
+            } else {
+                int clo = 0, chi = 0;
+                if (ok) {
+                    clo = __ldg(I.lv_cb[J] + u);
+                    chi = __ldg(I.lv_cb[J] + u + 1);
+                    if (chi - clo > kNarrowAbove) {
+                        const int* nk = I.lv_key[J + 1];
+                        clo = lower_key(nk, clo, chi, sh.klo[w][J + 1]);
+                        chi = lower_key(nk, clo, chi, sh.khi[w][J + 1] + 1);
+                    }
+                    ok = chi > clo;
                 }
-                cur[j]++;
-                continue;
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (ok) {
+                    const int at = top + __popc(m & lt);
+                    slo[at] = clo;
+                    shi[at] = chi;
+                    spart[at] = off;
+                    slvl[at] = (signed char)(J + 1);
+                }
+                top += __popc(m);
             }
-            const int lo = __ldg(lcb[j] + u), hi = __ldg(lcb[j] + u + 1);
-            j++;
-            part[j] = off;
-            end[j] = hi;
-            cur[j] = lower_key(lkey[j], lo, hi, (long long)g[j] - r);
+            __syncwarp();
         }
-        if (!FILL) I.nbr_start[c] = found;
+        if (!FILL && lane == 0) I.nbr_start[c] = found;
+        __syncwarp();
     }
 }
 
 cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, bool fill, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    long long b = (total + 127) / 128;
+    long long b = (total + kWalkWarps - 1) / kWalkWarps;
     if (b > kPersistBlocks * 2) b = kPersistBlocks * 2;
     if (fill)
-        walk_kernel<true><<<(int)b, 128, 0, st>>>(ins, cells, total);
+        walk_kernel<true><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total);
     else
-        walk_kernel<false><<<(int)b, 128, 0, st>>>(ins, cells, total);
+        walk_kernel<false><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
