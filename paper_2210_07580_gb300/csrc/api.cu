@@ -32,6 +32,13 @@ struct CtxMem : MemProvider {
     HostBuf host_[kHostSlots];
     cudaStream_t st = nullptr;
     std::string* err = nullptr;
+    double nbr_ratio = 0.0;  // most neighbour entries per grid seen
+
+    bool pool_enabled() override { return true; }
+    double nbr_per_grid() override { return nbr_ratio; }
+    void note_nbr_per_grid(double r) override {
+        if (r > nbr_ratio) nbr_ratio = r;
+    }
 
     gd_status device(int slot, size_t bytes, void** out) override {
         DevBuf& b = dev[slot];
@@ -82,6 +89,7 @@ struct CtxMem : MemProvider {
             if (b.ptr) cudaFreeHost(b.ptr);
         for (DevBuf& b : dev) b = DevBuf();
         for (HostBuf& b : host_) b = HostBuf();
+        nbr_ratio = 0.0;
     }
 };
 

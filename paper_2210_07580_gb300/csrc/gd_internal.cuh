@@ -20,6 +20,9 @@
 namespace gd {
 
 constexpr int kMaxD = 8;
+// Largest stencil radius r = 1 + (isqrt(eps2) - 1) / s with s = 1 + isqrt(eps2 / d):
+// s > sqrt(eps2 / d) gives (isqrt(eps2) - 1) / s < sqrt(d), so r <= 1 + floor(sqrt(8)) = 3.
+constexpr int kMaxR = 3;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Bits of an instance's device status word (OR-ed by kernels).
@@ -63,6 +66,7 @@ enum SmallSlot {
     kSmPairsF = 22,     // other candidate pairs
     kSmHard0 = 23,      // pairs handed to FastMerging, wave 0
     kSmHard1 = 24,      // ... wave 1
+    kSmPool = 26,       // [2] instance 0 only: 64-bit neighbour-pool counter
     kSmLevelCount = 32, // [8] nodes per grid-tree level
     kSmallInts = 64
 };
@@ -312,7 +316,29 @@ cudaError_t launch_point_boxes(const Inst* ins, Flat cells, long long total, cud
 cudaError_t launch_level_diff(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_level_flag(const Inst* ins, Flat cells, long long total, int level, cudaStream_t st);
 cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, bool fill, cudaStream_t st);
+// Single-pass neighbour walk: the walk counts and, in the same pass, appends
+// each query's neighbours to a pool in runs of at most 32 (segments); after
+// the counts are scanned, the segments are scattered into the lists.  One
+// 64-bit counter hands out both: pool entries in its low kPoolBits bits,
+// segments above them.  A pool that overflows is discarded (the lists are then
+// filled by a second walk).
+constexpr int kPoolBits = 37;
+struct PoolSeg {
+    long long pos;  // first pool entry
+    int inst;       // instance (index into the Inst array)
+    int c;          // query grid
+    int off;        // offset of the run in the grid's list
+    int len;        // 1..32
+};
+struct WalkPool {
+    int* data;
+    PoolSeg* seg;
+    unsigned long long* ctr;
+    long long cap, seg_cap;
+};
+enum WalkMode { kWalkCount = 0, kWalkFill = 1, kWalkPool = 2 };
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, cudaStream_t st);
+cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st);
 
 // Core points (core.cu).
 cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st);

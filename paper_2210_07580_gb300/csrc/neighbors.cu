@@ -196,10 +196,11 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
 // takes the entries of the top level -- up to 32 nodes across several
 // ranges, the last range possibly split -- and the lanes test one node each:
 // key within +-r, offset within eps (and, at a leaf, the point-box test);
-// surviving inner nodes push their child range (narrowed to keys within +-r
-// by bisection when it is long), surviving leaves are counted (FILL == false,
-// into nbr_start[c]) or written at nbr + nbr_start[c] (FILL == true; both
-// passes visit the nodes in the same order).
+// surviving inner nodes push their child range narrowed to keys within +-r
+// (so no pushed node fails its key test), surviving leaves are counted into
+// nbr_start[c] and written: at nbr + nbr_start[c] once the counts are
+// scanned (kWalkFill), or to the pool in runs of up to 32 (kWalkPool, see
+// WalkPool).  Every mode visits the nodes in the same order.
 //
 // Stack bound: levels never decrease from the bottom of the stack to its top
 // (a step pops the top level j and pushes level j + 1), so a level receives
@@ -207,19 +208,28 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
 // entries.  Hence at most 32 entries per level below the root: 1 + 32 (d - 1).
 constexpr int kWalkWarps = 4;
 constexpr int kWalkStack = 1 + 32 * (kMaxD - 1);
-// child ranges longer than this are narrowed by bisection before the push
-constexpr int kNarrowAbove = 16;
 
-// First index u in [lo, hi) with key[u] >= v (hi if none).
-__device__ __forceinline__ int lower_key(const int* __restrict__ key, int lo, int hi, long long v) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((long long)__ldg(key + mid) < v)
-            lo = mid + 1;
-        else
-            hi = mid;
+// Narrow the key-sorted range [*lo, *hi) to keys in [vlo, vhi]: the two
+// bisections run side by side, so their loads overlap.
+__device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* lo, int* hi, long long vlo,
+                                             long long vhi) {
+    const int a = *lo, b = *hi;
+    int l1 = a, h1 = b, l2 = a, h2 = b;  // first key >= vlo; first key > vhi
+    while (l1 < h1 || l2 < h2) {
+        const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1;
+        const long long k1 = l1 < h1 ? (long long)__ldg(key + m1) : 0;
+        const long long k2 = l2 < h2 ? (long long)__ldg(key + m2) : 0;
+        if (l1 < h1) {
+            if (k1 < vlo) l1 = m1 + 1;
+            else h1 = m1;
+        }
+        if (l2 < h2) {
+            if (k2 <= vhi) l2 = m2 + 1;
+            else h2 = m2;
+        }
     }
-    return lo;
+    *lo = l1;
+    *hi = l2;
 }
 
 struct WalkShared {
@@ -229,11 +239,32 @@ struct WalkShared {
     signed char lvl[kWalkWarps][kWalkStack];
     long long qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];    // query point box
     long long klo[kWalkWarps][kMaxD], khi[kWalkWarps][kMaxD];    // key window g_j -+ r
-    long long base[kWalkWarps][kMaxD];                           // mn_j
+    int g[kWalkWarps][kMaxD];                                    // query identifier
+    // squared gap in dimension j between the query's point box and the cell
+    // at key offset delta = key - g_j, index delta + kMaxR (saturated at 2^62,
+    // which exceeds every eps2)
+    long long gap2[kWalkWarps][kMaxD][2 * kMaxR + 1];
+    int buf[kWalkWarps][64];  // kWalkPool: neighbours not yet flushed
 };
 
-template <bool FILL>
-__global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+// kWalkPool: hand `len` buffered neighbours of query c (instance k), the run
+// at offset `off` of its list, to the pool.
+__device__ __forceinline__ void pool_flush(const WalkPool& pool, const int* buf, int len, int k, int c, int off,
+                                           int lane) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(pool.ctr, (1ull << kPoolBits) | (unsigned long long)len);
+    t = __shfl_sync(kFull, t, 0);
+    const long long pos = (long long)(t & ((1ull << kPoolBits) - 1)), si = (long long)(t >> kPoolBits);
+    if (pos + len <= pool.cap && si < pool.seg_cap) {
+        if (lane < len) pool.data[pos + lane] = buf[lane];
+        if (lane == 0) pool.seg[si] = PoolSeg{pos, k, c, off, len};
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kWalkWarps)
+    walk_kernel(const Inst* __restrict__ ins, Flat f, long long total, WalkPool pool) {
+    constexpr bool FILL = MODE == kWalkFill, POOL = MODE == kWalkPool;
     __shared__ WalkShared sh;
     const int lane = lane_id(), w = threadIdx.x >> 5;
     int* const slo = sh.lo[w];
@@ -245,28 +276,42 @@ __global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __res
     FlatCursor cur;
     for (long long q = (long long)blockIdx.x * kWalkWarps + w; q < total; q += warps) {
         cur.seek(f, q);
-        const Inst& I = ins[f.idx[cur.k]];
+        const int kin = f.idx[cur.k];
+        const Inst& I = ins[kin];
         const long long c = q - cur.lo;
         const int d = I.p.d;
         const long long r = I.p.r, s = I.p.s, eps2 = I.p.eps2;
         if (lane < d) {
-            const long long g = I.cell_coord[c * d + lane];
-            sh.qlo[w][lane] = I.pbox[c * 2 * d + lane];
-            sh.qhi[w][lane] = I.pbox[c * 2 * d + d + lane];
+            const int gi = I.cell_coord[c * d + lane];
+            const long long g = gi, ql = I.pbox[c * 2 * d + lane], qh = I.pbox[c * 2 * d + d + lane];
+            sh.qlo[w][lane] = ql;
+            sh.qhi[w][lane] = qh;
             sh.klo[w][lane] = g - r;
             sh.khi[w][lane] = g + r;
-            sh.base[w][lane] = I.p.mn[lane];
+            sh.g[w][lane] = gi;
+            // the cell at offset delta spans [cl + delta s, cl + delta s + s - 1]
+            const long long cl = (long long)I.p.mn[lane] + g * s;
+#pragma unroll
+            for (int t = 0; t <= 2 * kMaxR; ++t) {
+                const long long dl = t - kMaxR;
+                long long gap = 0;
+                if (dl > 0) gap = cl + dl * s - qh;
+                else if (dl < 0) gap = ql - (cl + dl * s + s - 1);
+                sh.gap2[w][lane][t] = gap >= (1ll << 31) ? (1ll << 62) : gap * gap;
+            }
         }
         __syncwarp();
         const bool refine = I.cell_start[c + 1] - I.cell_start[c] <= kBoxPoints;
         const int* pbox = I.pbox;
         int* out = FILL ? I.nbr + I.nbr_start[c] : nullptr;
         int found = 0;
+        int nbuf = 0;     // kWalkPool: buffered neighbours
+        int flushed = 0;  // kWalkPool: neighbours already in the pool
+        int* const buf = sh.buf[w];
         int top = 0;
         {
-            const int n0 = I.small[kSmLevelCount];
-            const int a0 = lower_key(I.lv_key[0], 0, n0, sh.klo[w][0]);
-            const int b0 = lower_key(I.lv_key[0], a0, n0, sh.khi[w][0] + 1);
+            int a0 = 0, b0 = I.small[kSmLevelCount];
+            narrow_range(I.lv_key[0], &a0, &b0, sh.klo[w][0], sh.khi[w][0]);
             if (b0 > a0) {
                 if (lane == 0) {
                     slo[0] = a0;
@@ -310,15 +355,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __res
             const int u = my_lo + (lane - my_start);
             bool ok = false;
             long long off = 0;
+            // the node's child range is loaded with its key (one round trip)
+            int clo = 0, chi = 0;
             if (act) {
-                const long long key = __ldg(I.lv_key[J] + u);
-                if (key >= sh.klo[w][J] && key <= sh.khi[w][J]) {
-                    const long long clo = sh.base[w][J] + key * s, chi = clo + s - 1;
-                    const long long ql = sh.qlo[w][J], qh = sh.qhi[w][J];
-                    long long gap = 0;
-                    if (clo > qh) gap = clo - qh;
-                    else if (ql > chi) gap = ql - chi;
-                    off = my_part + gap * gap;
+                const int key = __ldg(I.lv_key[J] + u);
+                if (J < d - 1) {
+                    clo = __ldg(I.lv_cb[J] + u);
+                    chi = __ldg(I.lv_cb[J] + u + 1);
+                }
+                const int dl = key - sh.g[w][J];
+                if (dl >= -r && dl <= r) {
+                    off = my_part + sh.gap2[w][J][dl + kMaxR];
                     ok = off <= eps2;
                 }
             }
@@ -340,16 +387,22 @@ __global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __res
                 const unsigned m = __ballot_sync(kFull, ok);
                 if (FILL && ok) out[found + __popc(m & lt)] = u;
                 found += __popc(m);
-            } else {
-                int clo = 0, chi = 0;
-                if (ok) {
-                    clo = __ldg(I.lv_cb[J] + u);
-                    chi = __ldg(I.lv_cb[J] + u + 1);
-                    if (chi - clo > kNarrowAbove) {
-                        const int* nk = I.lv_key[J + 1];
-                        clo = lower_key(nk, clo, chi, sh.klo[w][J + 1]);
-                        chi = lower_key(nk, clo, chi, sh.khi[w][J + 1] + 1);
+                if (POOL) {
+                    if (ok) buf[nbuf + __popc(m & lt)] = u;
+                    nbuf += __popc(m);
+                    __syncwarp();
+                    if (nbuf >= 32) {
+                        pool_flush(pool, buf, 32, kin, (int)c, flushed, lane);
+                        flushed += 32;
+                        nbuf -= 32;
+                        const int rest = lane < nbuf ? buf[32 + lane] : 0;
+                        __syncwarp();
+                        if (lane < nbuf) buf[lane] = rest;
                     }
+                }
+            } else {
+                if (ok) {
+                    narrow_range(I.lv_key[J + 1], &clo, &chi, sh.klo[w][J + 1], sh.khi[w][J + 1]);
                     ok = chi > clo;
                 }
                 const unsigned m = __ballot_sync(kFull, ok);
@@ -364,19 +417,44 @@ __global__ void __launch_bounds__(32 * kWalkWarps) walk_kernel(const Inst* __res
             }
             __syncwarp();
         }
+        if (POOL && nbuf > 0) pool_flush(pool, buf, nbuf, kin, (int)c, flushed, lane);
         if (!FILL && lane == 0) I.nbr_start[c] = found;
         __syncwarp();
     }
 }
 
-cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, bool fill, cudaStream_t st) {
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     long long b = (total + kWalkWarps - 1) / kWalkWarps;
     if (b > kPersistBlocks * 2) b = kPersistBlocks * 2;
-    if (fill)
-        walk_kernel<true><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total);
+    if (mode == kWalkFill)
+        walk_kernel<kWalkFill><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
+    else if (mode == kWalkPool)
+        walk_kernel<kWalkPool><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
     else
-        walk_kernel<false><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total);
+        walk_kernel<kWalkCount><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+// The pool's segments into the scanned lists: one warp per segment.
+__global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restrict__ ins, WalkPool pool,
+                                                           long long nseg) {
+    const int lane = lane_id();
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long sgi = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); sgi < nseg;
+         sgi += warps) {
+        const PoolSeg sg = pool.seg[sgi];
+        const Inst& I = ins[sg.inst];
+        if (lane < sg.len) I.nbr[(long long)I.nbr_start[sg.c] + sg.off + lane] = pool.data[sg.pos + lane];
+    }
+}
+
+cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st) {
+    if (nseg <= 0) return cudaSuccess;
+    long long b = (nseg * 32 + 255) / 256;
+    if (b > kPersistBlocks) b = kPersistBlocks;
+    pool_scatter_kernel<<<(int)b, 256, 0, st>>>(ins, pool, nseg);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -323,6 +323,7 @@ gd_status Run::go() {
         p.minpts = g.minpts;
         p.s = 1 + (long long)isqrt_u64((unsigned long long)p.eps2 / (unsigned long long)g.d);
         p.r = p.eps2 == 0 ? 0 : 1 + ((long long)isqrt_u64((unsigned long long)p.eps2) - 1) / p.s;
+        if (p.r > kMaxR) return fail(GD_ERANGE, "stencil radius above its bound", k);
         h.dev.X = g.X;
         h.dev.labels = g.labels;
         h.dev.is_core = g.is_core;
@@ -522,10 +523,32 @@ gd_status Run::go() {
     }
     RUN_CUDA(launch_level_write(dins, cells2, total_cells, st), "level write");
     mark(5);
-    RUN_CUDA(launch_walk(dins, cells2, total_cells, false, st), "walk count");
+    // Single pass when a pool can be had: sized from the most neighbour
+    // entries per grid this memory has seen (a first run guesses).
+    WalkPool pool{};
+    if (mem.pool_enabled()) {
+        const double ratio = mem.nbr_per_grid() > 0 ? mem.nbr_per_grid() * 1.25 : 48.0;
+        const long long cap = (long long)(ratio * (double)total_cells) + 4096;
+        const long long seg_cap = total_cells + cap / 32 + 64;
+        void *pd = nullptr, *ps = nullptr;
+        if (cap < (1ll << kPoolBits) && seg_cap < (1ll << (64 - kPoolBits)) &&
+            mem.device(kMemPool, (size_t)cap * 4, &pd) == GD_OK &&
+            mem.device(kMemPoolSeg, (size_t)seg_cap * sizeof(PoolSeg), &ps) == GD_OK) {
+            pool = WalkPool{(int*)pd, (PoolSeg*)ps, (unsigned long long*)(dsmall + kSmPool), cap, seg_cap};
+        }
+    }
+    const bool pooled = pool.data != nullptr;
+    RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, st), "walk");
     RUN_TRY(scan(nseg, K, nseg_tiles));
     RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
     RUN_TRY(readback());
+    long long pool_segs = -1;  // -1: fill by a second walk
+    if (pooled) {
+        unsigned long long ctr;
+        memcpy(&ctr, sm(0) + kSmPool, sizeof(ctr));
+        const long long used = (long long)(ctr & ((1ull << kPoolBits) - 1)), segs = (long long)(ctr >> kPoolBits);
+        if (used <= pool.cap && segs <= pool.seg_cap) pool_segs = segs;
+    }
 
     // ------------- phase 4: neighbours, core, merge, labels (sync 4)
     long long total_nbr = 0;
@@ -534,6 +557,7 @@ gd_status Run::go() {
         if (hi[k].nnbr >= INT_MAX) return fail(GD_ERANGE, "neighbour lists exceed 2^31 entries", k);
         total_nbr += hi[k].nnbr;
     }
+    if (total_cells > 0) mem.note_nbr_per_grid((double)total_nbr / (double)total_cells);
     void *nbp = nullptr, *pp = nullptr, *hp = nullptr;
     RUN_TRY(mem.device(kMemNbr, (size_t)total_nbr * 4 + 256 * (size_t)K + 256, &nbp));
     RUN_TRY(mem.device(kMemPairs, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &pp));
@@ -598,7 +622,10 @@ gd_status Run::go() {
     idx = idx_all();
     RUN_TRY(upload_desc());
 
-    RUN_CUDA(launch_walk(dins, cells, total_cells, true, st), "walk fill");
+    if (pool_segs >= 0)
+        RUN_CUDA(launch_pool_scatter(dins, pool, pool_segs, st), "neighbour scatter");
+    else
+        RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, st), "walk fill");
     mark(6);
     RUN_CUDA(launch_core_full(dins, pts, total_pts, st), "core (full grids)");
     RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");

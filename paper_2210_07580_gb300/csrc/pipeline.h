@@ -12,7 +12,10 @@ namespace gd {
 
 // Where the driver's memory comes from: a context's growable buffers, or a
 // fixed static array (the no-allocation entry point).
-enum MemSlot { kMemSmall, kMemDesc, kMemArena, kMemScanTmp, kMemNbr, kMemPairs, kMemHard, kMemScratch, kMemSlots };
+enum MemSlot {
+    kMemSmall, kMemDesc, kMemArena, kMemScanTmp, kMemNbr, kMemPairs, kMemHard, kMemScratch, kMemPool, kMemPoolSeg,
+    kMemSlots
+};
 enum HostSlot { kHostSmall, kHostDesc, kHostSlots };
 
 struct MemProvider {
@@ -22,6 +25,11 @@ struct MemProvider {
     virtual gd_status device(int slot, size_t bytes, void** out) = 0;
     // A host staging buffer (pinned where possible) of at least `bytes`.
     virtual gd_status host(int slot, size_t bytes, void** out) = 0;
+    // Single-pass neighbour walk: whether to try it, and the largest number of
+    // neighbour entries per grid seen so far (sizes the pool; 0 = none yet).
+    virtual bool pool_enabled() { return false; }
+    virtual double nbr_per_grid() { return 0.0; }
+    virtual void note_nbr_per_grid(double) {}
 };
 
 // Stage timing: when non-null, events[s] is recorded before stage s and
