@@ -200,6 +200,61 @@ def bench_batched(ctx, dev, args):
             "speedup": round(res["looped"] / res["batched"], 2), "labels_identical": bool(same)}
 
 
+def _replay(srv, jobs, arrivals):
+    """Submit jobs at their arrival times (seconds from now; None = all at
+    once); wait for every result.  Returns (results, stats)."""
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    futs = []
+    for i, (X, e, m) in enumerate(jobs):
+        if arrivals is not None:
+            wait = t0 + arrivals[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        futs.append(srv.submit(X, e, m))
+    res = [f.result(timeout=900) for f in futs]
+    return res, srv.stats()
+
+
+def bench_serve(dev, args):
+    """Serving: the same job list through (a) the sequential plain path -- one
+    slot, one job per gd_dbscan call, host arrays in and out -- and (b) the
+    continuous-batching server (several slots, small jobs coalesced into
+    gd_dbscan_batched).  Throughput with every job queued at once, then
+    p50/p99 latency under one Poisson arrival stream at `load` times the
+    sequential path's throughput.  Each server first runs the list once
+    untimed (resident workspaces)."""
+    from paper_2210_07580_gb300 import synth
+    from paper_2210_07580_gb300.serve import Server
+    jobs = synth.serve_jobs(args.serve_jobs, seed=11)
+    npts = int(sum(len(X) for X, _, _ in jobs))
+    out = {"workload": f"{len(jobs)} jobs: n log-uniform in [1e3, 1e7], d in 2..7, eps in [200, 2000], "
+                       f"MinPts in {{5,10,50,100}}, blobs + 5% noise; host int32 arrays in, labels + core flags out",
+           "jobs": len(jobs), "points": npts, "load": args.serve_load}
+    configs = (("sequential", dict(slots=1, small_job_points=0)),
+               ("served", dict(slots=args.serve_slots, small_job_points=200_000)))
+    results = {}
+    for name, kw in configs:
+        with Server(device=dev.index or 0, **kw) as srv:
+            _replay(srv, jobs, None)  # warm-up
+            res, st = _replay(srv, jobs, None)
+            results[name] = res
+            out[name] = {"slots": kw["slots"], "jobs_per_s": round(st["jobs_per_s"], 2),
+                         "saturated_p50_ms": round(st["p50_ms"], 2), "saturated_p99_ms": round(st["p99_ms"], 2),
+                         "mean_batch": round(st["mean_batch"], 2)}
+            if name == "sequential":
+                rate = args.serve_load * st["jobs_per_s"]
+                arrivals = synth.poisson_arrivals(len(jobs), rate, seed=12)
+                out["rate_per_s"] = round(rate, 2)
+            _, st = _replay(srv, jobs, arrivals)
+            out[name].update({"poisson_p50_ms": round(st["p50_ms"], 2), "poisson_p99_ms": round(st["p99_ms"], 2),
+                              "poisson_mean_batch": round(st["mean_batch"], 2)})
+    out["speedup_jobs_per_s"] = round(out["served"]["jobs_per_s"] / out["sequential"]["jobs_per_s"], 2)
+    out["labels_identical"] = bool(all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+                                       for a, b in zip(results["sequential"], results["served"])))
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -288,8 +343,10 @@ def run_gpu(args):
         # dominant kernel: the onesweep radix-sort pass.  Algorithmic bytes
         # of one launch: every key and value read once and written once.
         passes = max(1, sizes["sort_passes"])
-        key_bytes = 8 if sizes["key_bits"] <= 64 else 16
-        launch_bytes = 2 * (key_bytes + 4) * n
+        # bytes one pass reads and writes per point: the packed key word, or
+        # the key plus the 32-bit index
+        unit_bytes = {0: 8, 1: 12, 2: 20}[sizes["key_class"]]
+        launch_bytes = 2 * unit_bytes * n
         launch_ms = stages.get("sort", 0.0) / passes
         achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
         line = {
@@ -316,6 +373,8 @@ def run_gpu(args):
         }
         if not args.no_batch:
             line["batched"] = bench_batched(ctx, dev, args)
+        if not args.no_serve:
+            line["serve"] = bench_serve(dev, args)
         if not args.no_cpu_baseline and ws == 1:
             t, ns, thr = time_oracle(args.workload, 1, args.cpu_sample)
             line["cpu_baseline"] = {"value": round(ns / t / 1e6, 3), "unit": "Mpts/s", "cores": thr,
@@ -343,6 +402,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched vs looped measurement")
     ap.add_argument("--batch-k", type=int, default=256)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-jobs", type=int, default=48)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="Poisson arrival rate as a fraction of the sequential path's jobs/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -141,7 +141,9 @@ typedef enum {
  * out[3]=nnbr (neighbour list length), out[4]=cell side s, out[5]=key bits,
  * out[6]=kernel launches of the run, out[7]=candidate merge pairs,
  * out[8]=radix-sort passes, out[9]=bits per digit, out[10]=pairs decided by
- * FastMerging, out[11]=0 (reserved).  Returns GD_EINVAL before any run. */
+ * FastMerging, out[11]=sort key class (0: key and point index packed in one
+ * 64-bit word, 1: 64-bit key + 32-bit index, 2: 128-bit key + 32-bit index).
+ * Returns GD_EINVAL before any run. */
 gd_status gd_last_sizes(const gd_ctx *ctx, int64_t out[12]);
 
 /* Copy `bytes` bytes of an internal array of the last run into host memory

@@ -210,7 +210,7 @@ class Context:
         out = (ctypes.c_int64 * 12)()
         self._check(self._lib.gd_last_sizes(self._h, out))
         keys = ["n", "d", "grids", "nnbr", "side", "key_bits", "launches", "pairs", "sort_passes", "digit_bits",
-                "fastmerging_pairs", "reserved"]
+                "fastmerging_pairs", "key_class"]
         return {k: int(v) for k, v in zip(keys, out)}
 
     def copy_view(self, which: int, dtype, count: int) -> np.ndarray:

@@ -44,6 +44,11 @@ struct Params {
     long long r;      // largest |delta| per dimension whose gap alone is <= eps
     int key_bits;     // total bits of the packed grid key
     int key_words;    // 1 or 2 64-bit words
+    // Sort key class: 0 = one 64-bit word holding the key above the point
+    // index (pack_bits low bits; no separate values), 1 = 64-bit key plus
+    // index values, 2 = 128-bit key plus index values.
+    int key_class;
+    int pack_bits;
     int mn[kMaxD];    // per-dimension minimum coordinate
     int bits[kMaxD];  // bits of each identifier in the key
     int shift[kMaxD]; // bit offset of identifier j (dimension 0 most significant)
@@ -280,8 +285,8 @@ cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long lo
 // Grid construction (grid.cu).
 cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, cudaStream_t st);
 constexpr int kCompactTile = 1024;
-cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st);
-cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st);
+cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);
+cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);
 // Over the flat space of points.
 cudaError_t launch_cell_max(const Inst* ins, Flat pts, long long total, cudaStream_t st);
 
@@ -303,12 +308,12 @@ constexpr int kQuantTile = 4096;  // points per quantise block
 // keys, values and digit histograms; `tiles` is the flat space of quantise
 // tiles (kQuantTile points) of instances with the given key width.
 // Histograms, counters and status must be zeroed first.
-cudaError_t launch_quantise_hist(const Inst* ins, Flat tiles, long long total, int key_words, int max_hist_ints,
+cudaError_t launch_quantise_hist(const Inst* ins, Flat tiles, long long total, int key_class, int max_hist_ints,
                                  cudaStream_t st);
 cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st);
 // One onesweep pass over the tiles of the instances in `tiles` (each with
 // more than `pass` passes and the given key width).
-cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_words, int pass, int max_buckets,
+cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
                             int* flat_counter, cudaStream_t st);
 
 // Grid-tree levels and neighbour walk (neighbors.cu).

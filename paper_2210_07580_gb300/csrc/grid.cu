@@ -244,9 +244,18 @@ template <typename K>
 __device__ __forceinline__ const K* sorted_keys(const Inst& I) {
     return (const K*)((I.passes & 1) ? I.keyB : I.keyA);
 }
-__device__ __forceinline__ const int* sorted_vals(const Inst& I) { return (I.passes & 1) ? I.valB : I.valA; }
+__device__ __forceinline__ int* sorted_vals(const Inst& I) { return (I.passes & 1) ? I.valB : I.valA; }
 
-template <typename K>
+// The grid key of sorted position q (packed keys carry the point index in
+// their low pack_bits bits).
+template <typename K, bool PACKED> __device__ __forceinline__ K grid_key(const K* keys, long long q, int pb) {
+    if constexpr (PACKED)
+        return keys[q] >> pb;
+    else
+        return keys[q];
+}
+
+template <typename K, bool PACKED>
 __global__ void __launch_bounds__(kCompactBlock) compact_count_kernel(const Inst* __restrict__ ins, Flat f) {
     __shared__ int sm[33];
     const int k = flat_find(f, blockIdx.x);
@@ -254,12 +263,14 @@ __global__ void __launch_bounds__(kCompactBlock) compact_count_kernel(const Inst
     const long long tile = blockIdx.x - f.off[k];
     const int n = I.p.n;
     const K* keys = sorted_keys<K>(I);
+    const int pb = I.p.pack_bits;
     const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
     int c = 0;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
         const long long q = base + i;
-        if (q < n && (q == 0 || !key_eq(keys[q], keys[q - 1]))) c++;
+        if (q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb))))
+            c++;
     }
     int total;
     block_exclusive_scan(c, sm, &total);
@@ -267,8 +278,9 @@ __global__ void __launch_bounds__(kCompactBlock) compact_count_kernel(const Inst
 }
 
 // Writes cell_start, identifiers (decoded from the key), pt_cell and the
-// grid-order coordinates Xs (gathered through the sorted permutation).
-template <typename K>
+// grid-order coordinates Xs (gathered through the sorted permutation; packed
+// keys also write the permutation out).
+template <typename K, bool PACKED>
 __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst* __restrict__ ins, Flat f) {
     __shared__ int sm[33];
     const int k = flat_find(f, blockIdx.x);
@@ -276,14 +288,15 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
     const long long tile = blockIdx.x - f.off[k];
     const int n = I.p.n, d = I.p.d, dp = I.p.dp;
     const K* keys = sorted_keys<K>(I);
-    const int* vals = sorted_vals(I);
+    int* vals = sorted_vals(I);
+    const int pb = I.p.pack_bits;
     const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
     bool fl[kCompactItems];
     int c = 0;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
         const long long q = base + i;
-        fl[i] = q < n && (q == 0 || !key_eq(keys[q], keys[q - 1]));
+        fl[i] = q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb)));
         c += fl[i];
     }
     int total;
@@ -295,12 +308,19 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
         if (fl[i]) {
             cid++;
             I.cell_start[cid] = (int)q;
-            const K key = keys[q];
+            const K key = grid_key<K, PACKED>(keys, q, pb);
             for (int j = 0; j < d; ++j)
                 I.cell_coord[(long long)cid * d + j] = (int)key_field(key, I.p.shift[j], I.p.bits[j]);
         }
         I.pt_cell[q] = cid;
-        const int* row = I.X + (long long)vals[q] * d;
+        int src;
+        if constexpr (PACKED) {
+            src = (int)(keys[q] & ((1ull << pb) - 1ull));
+            vals[q] = src;
+        } else {
+            src = vals[q];
+        }
+        const int* row = I.X + (long long)src * d;
         int* out = I.Xs + q * dp;
         if (dp == 4) {
             int4 v;
@@ -319,22 +339,26 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
     }
 }
 
-cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st) {
+cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    if (key_words == 1)
-        compact_count_kernel<unsigned long long><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+    if (key_class == 0)
+        compact_count_kernel<unsigned long long, true><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+    else if (key_class == 1)
+        compact_count_kernel<unsigned long long, false><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     else
-        compact_count_kernel<Key2><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+        compact_count_kernel<Key2, false><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_words, cudaStream_t st) {
+cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    if (key_words == 1)
-        compact_write_kernel<unsigned long long><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+    if (key_class == 0)
+        compact_write_kernel<unsigned long long, true><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+    else if (key_class == 1)
+        compact_write_kernel<unsigned long long, false><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     else
-        compact_write_kernel<Key2><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
+        compact_write_kernel<Key2, false><<<(unsigned)total, kCompactBlock, 0, st>>>(ins, tiles);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -383,6 +383,11 @@ gd_status Run::go() {
         }
         p.key_bits = total_bits;
         p.key_words = total_bits <= 64 ? 1 : 2;
+        {
+            const int ib = p.n > 1 ? bit_length((unsigned long long)(p.n - 1)) : 1;
+            p.key_class = p.key_words == 2 ? 2 : (total_bits + ib <= 64 ? 0 : 1);
+            p.pack_bits = p.key_class == 0 ? ib : 0;
+        }
         const SortPlan sp = sort_plan(p.n, p.key_words, p.key_bits);
         h.dev.passes = sp.passes;
         h.dev.digit_bits = sp.bits;
@@ -420,15 +425,16 @@ gd_status Run::go() {
     const size_t counters_at = b.take(sizeof(int) * 64);
     int* counters = reinterpret_cast<int*>(b.dev + counters_at);
     if (!b.overflow) memset(b.host + counters_at, 0, sizeof(int) * 64);
-    Flat qflat[2], cflat[2];
-    long long qtot[2] = {0, 0}, ctot[2] = {0, 0};
-    Flat oflat[2][16];
-    long long otot[2][16] = {};
-    int gpasses[2] = {0, 0};
-    for (int w = 0; w < 2; ++w) {
+    // one group per key class (packed 64-bit, 64-bit + values, 128-bit + values)
+    Flat qflat[3], cflat[3];
+    long long qtot[3] = {0, 0, 0}, ctot[3] = {0, 0, 0};
+    Flat oflat[3][16];
+    long long otot[3][16] = {};
+    int gpasses[3] = {0, 0, 0};
+    for (int w = 0; w < 3; ++w) {
         int m = 0;
         for (int k = 0; k < K; ++k)
-            if (hi[k].dev.p.key_words == w + 1) members2[m++] = k;
+            if (hi[k].dev.p.key_class == w) members2[m++] = k;
         qflat[w] = flat(members2, m, [&](int k) { return (long long)hi[k].q_tiles; }, &qtot[w]);
         cflat[w] = flat(members2, m, [&](int k) { return (long long)hi[k].c_tiles; }, &ctot[w]);
         for (int t = 0; t < m; ++t)
@@ -454,19 +460,18 @@ gd_status Run::go() {
 
     mark(1);
     RUN_CUDA(zero_ranges(zr_dev, K, zr_total, st), "clear sort state");
-    for (int w = 0; w < 2; ++w)
-        RUN_CUDA(launch_quantise_hist(dins, qflat[w], qtot[w], w + 1, max_hist, st), "quantise");
+    for (int w = 0; w < 3; ++w)
+        RUN_CUDA(launch_quantise_hist(dins, qflat[w], qtot[w], w, max_hist, st), "quantise");
     RUN_CUDA(launch_digit_scan(dins, idx, K, max_passes, st), "digit scan");
     mark(2);
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < 3; ++w)
         for (int ps = 0; ps < gpasses[w]; ++ps)
-            RUN_CUDA(launch_onesweep(dins, oflat[w][ps], otot[w][ps], w + 1, ps, max_buckets, counters + w * 16 + ps,
-                                     st),
+            RUN_CUDA(launch_onesweep(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, counters + w * 16 + ps, st),
                      "sort pass");
     mark(3);
-    for (int w = 0; w < 2; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w + 1, st), "compact count");
+    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w, st), "compact count");
     RUN_TRY(scan(cseg, K, cseg_tiles));
-    for (int w = 0; w < 2; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w + 1, st), "compact write");
+    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w, st), "compact write");
     RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
     RUN_TRY(readback());
 
@@ -686,7 +691,7 @@ gd_status Run::go() {
         info->sizes[8] = h.dev.passes;
         info->sizes[9] = h.dev.digit_bits;
         info->sizes[10] = (long long)s0[kSmHard0] + s0[kSmHard1];
-        info->sizes[11] = 0;
+        info->sizes[11] = h.dev.p.key_class;
         info->view_ptr[GD_VIEW_PERM] = (h.dev.passes & 1) ? h.dev.valB : h.dev.valA;
         info->view_bytes[GD_VIEW_PERM] = (size_t)n * 4;
         info->view_ptr[GD_VIEW_CELL_START] = h.dev.cell_start;

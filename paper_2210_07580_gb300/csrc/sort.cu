@@ -12,7 +12,11 @@
 //      its per-digit counts and finds the counts of all earlier tiles of its
 //      instance by a decoupled look-back, then writes each digit run out
 //      contiguously.
-// A pass reads and writes every key and value once.  Look-back waits are
+// A pass reads and writes every key and value once.  When the key and the
+// point index fit in 64 bits together, the index rides in the low bits of the
+// key (no separate values): a pass then moves 16 bytes per point, not 24,
+// and since the passes are stable and look only at key digits, the order is
+// the same.  Look-back waits are
 // bounded: a block only ever waits for tiles handed out before its own (tile
 // ids are taken in order from one counter over the whole batch), and gives
 // up with kDevTimeout after a fixed number of polls.
@@ -26,6 +30,7 @@ constexpr int kOsBlock = 256;
 constexpr int kOsWarps = kOsBlock / 32;
 constexpr unsigned kFlagAgg = 1u, kFlagInc = 2u;
 constexpr int kMaxPolls = 1 << 22;
+constexpr int kLookback = 8;
 
 template <typename K> struct SortKey;
 template <> struct SortKey<unsigned long long> {
@@ -112,7 +117,7 @@ __device__ __forceinline__ void zero_key(Key2& k) { k.lo = k.hi = 0; }
 // (input index) and the tile's histogram of every digit position, added to
 // the instance's histograms.  Runs of equal digits inside a warp are counted
 // once (warp match), which keeps shared-memory atomics cheap on clustered data.
-template <typename K>
+template <typename K, bool PACKED>
 __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restrict__ ins, Flat f) {
     extern __shared__ int sh_hist[];  // [passes][1 << bits]
     const int k = flat_find(f, blockIdx.x);
@@ -137,8 +142,13 @@ __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restri
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
                 if (j < d) pack_key(key, identifier(__ldg(row + j), p.mn[j], p.s), p.shift[j]);
-            keys[i] = key;
-            I.valA[i] = (int)i;
+            if constexpr (PACKED) {
+                // key above the point index: one word carries both
+                keys[i] = (unsigned long long)key << p.pack_bits | (unsigned long long)i;
+            } else {
+                keys[i] = key;
+                I.valA[i] = (int)i;
+            }
         }
         for (int ps = 0; ps < passes; ++ps) {
             const unsigned dg = valid ? SortKey<K>::digit(key, ps * bits, mask) : (unsigned)R + lane;
@@ -180,9 +190,9 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <typename K>
-__global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __restrict__ ins, Flat f, int pass,
-                                                               int* flat_counter) {
+template <typename K, bool PACKED>
+__global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
+    onesweep_kernel(const Inst* __restrict__ ins, Flat f, int pass, int* flat_counter) {
     constexpr int kItems = SortKey<K>::kItems;
     constexpr int kTile = os_tile<K>();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
     const int kk = flat_find(f, ft);
     const Inst& I = ins[f.idx[kk]];
     const int tile = ft - (int)f.off[kk];
-    const int n = I.p.n, bits = I.digit_bits, shift = pass * bits;
+    const int n = I.p.n, bits = I.digit_bits, shift = pass * bits + (PACKED ? I.p.pack_bits : 0);
     const int R = 1 << bits;
     const unsigned mask = (unsigned)R - 1u;
     const K* keys_in = (const K*)((pass & 1) ? I.keyB : I.keyA);
@@ -208,7 +218,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
     //         wcount [kOsWarps][R], ldstart [R], goff [R]
     K* skeys = reinterpret_cast<K*>(smem);
     int* svals = reinterpret_cast<int*>(smem + sizeof(K) * kTile);
-    int* wcount = svals + kTile;
+    int* wcount = svals + (PACKED ? 0 : kTile);
     int* ldstart = wcount + kOsWarps * R;
     int* goff = ldstart + R;
 
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
         const int t = wbase + i * 32 + lane;
         if (t < count) {
             key[i] = keys_in[base + t];
-            val[i] = vals_in[base + t];
+            if constexpr (!PACKED) val[i] = vals_in[base + t];
         }
     }
 #pragma unroll
@@ -285,7 +295,9 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
         __syncthreads();
     }
 
-    // decoupled look-back: one thread per digit
+    // decoupled look-back: one thread per digit, reading kLookback earlier
+    // tiles per round trip (loads of consecutive digits are coalesced) and
+    // adding their counts up to the nearest inclusive one (tile 0's always is)
     for (int b = threadIdx.x; b < R; b += kOsBlock) {
         const unsigned own = (unsigned)goff[b];
         unsigned long long* my = status + (long long)tile * R + b;
@@ -297,19 +309,30 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
             int t = tile - 1;
             int polls = 0;
             while (true) {
-                const unsigned long long v = ld_relaxed(status + (long long)t * R + b);
-                const unsigned flag = (unsigned)(v >> 32);
-                if (flag == 0u) {
+                unsigned long long v[kLookback];
+#pragma unroll
+                for (int j = 0; j < kLookback; ++j)
+                    v[j] = t - j >= 0 ? ld_relaxed(status + (long long)(t - j) * R + b) : 0ull;
+                int used = 0;
+                bool done = false;
+#pragma unroll
+                for (int j = 0; j < kLookback; ++j) {
+                    if (done || used < j) break;  // stop at the first unpublished tile
+                    const unsigned flag = (unsigned)(v[j] >> 32);
+                    if (flag == 0u) break;
+                    excl += (unsigned)v[j];
+                    used = j + 1;
+                    if (flag == kFlagInc) done = true;
+                }
+                if (done) break;
+                t -= used;
+                if (used == 0) {
                     if (++polls > kMaxPolls) {
                         set_status(I, kDevTimeout);
                         break;
                     }
                     __nanosleep(32);
-                    continue;
                 }
-                excl += (unsigned)v;
-                if (flag == kFlagInc || t == 0) break;
-                --t;
             }
             st_relaxed(my, ((unsigned long long)kFlagInc << 32) | (excl + own));
         }
@@ -325,7 +348,7 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
             const int dg = rk[i] >> 16;
             const int pos = ldstart[dg] + wcount[warp * R + dg] + (rk[i] & 0xffff);
             skeys[pos] = key[i];
-            svals[pos] = val[i];
+            if constexpr (!PACKED) svals[pos] = val[i];
         }
     }
     __syncthreads();
@@ -337,24 +360,26 @@ __global__ void __launch_bounds__(kOsBlock, 3) onesweep_kernel(const Inst* __res
             const unsigned dg = SortKey<K>::digit(k2, shift, mask);
             const int dst = goff[dg] + (t - ldstart[dg]);
             keys_out[dst] = k2;
-            vals_out[dst] = svals[t];
+            if constexpr (!PACKED) vals_out[dst] = svals[t];
         }
     }
 }
 
-template <typename K> static size_t onesweep_smem(int R) {
-    return sizeof(K) * os_tile<K>() + sizeof(int) * os_tile<K>() + sizeof(int) * (kOsWarps * R + 2 * R);
+template <typename K, bool PACKED> static size_t onesweep_smem(int R) {
+    return sizeof(K) * os_tile<K>() + (PACKED ? 0 : sizeof(int) * os_tile<K>()) + sizeof(int) * (kOsWarps * R + 2 * R);
 }
 
-cudaError_t launch_quantise_hist(const Inst* ins, Flat qtiles, long long total, int key_words, int max_hist_ints,
+cudaError_t launch_quantise_hist(const Inst* ins, Flat qtiles, long long total, int key_class, int max_hist_ints,
                                  cudaStream_t st) {
     const long long tiles = total;
     if (tiles <= 0) return cudaSuccess;
     const size_t smem = sizeof(int) * (size_t)(max_hist_ints > 0 ? max_hist_ints : 1);
-    if (key_words == 1)
-        quantise_hist_kernel<unsigned long long><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+    if (key_class == 0)
+        quantise_hist_kernel<unsigned long long, true><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+    else if (key_class == 1)
+        quantise_hist_kernel<unsigned long long, false><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
     else
-        quantise_hist_kernel<Key2><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+        quantise_hist_kernel<Key2, false><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -366,22 +391,28 @@ cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_pa
     return cudaGetLastError();
 }
 
-cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_words, int pass, int max_buckets,
+template <typename K, bool PACKED>
+static cudaError_t onesweep_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets,
+                                   int* flat_counter, cudaStream_t st) {
+    const size_t smem = onesweep_smem<K, PACKED>(max_buckets);
+    const cudaError_t e =
+        cudaFuncSetAttribute(onesweep_kernel<K, PACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    onesweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
+    return cudaSuccess;
+}
+
+cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
                             int* flat_counter, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     cudaError_t e;
-    if (key_words == 1) {
-        const size_t smem = onesweep_smem<unsigned long long>(max_buckets);
-        e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        onesweep_kernel<unsigned long long><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
-    } else {
-        const size_t smem = onesweep_smem<Key2>(max_buckets);
-        e = cudaFuncSetAttribute(onesweep_kernel<Key2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        onesweep_kernel<Key2><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
-    }
+    if (key_class == 0)
+        e = onesweep_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, flat_counter, st);
+    else if (key_class == 1)
+        e = onesweep_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, flat_counter, st);
+    else
+        e = onesweep_launch<Key2, false>(ins, tiles, total, pass, max_buckets, flat_counter, st);
+    if (e != cudaSuccess) return e;
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

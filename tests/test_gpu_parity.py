@@ -307,6 +307,30 @@ def test_batched_equals_single_and_oracle(ctx):
         np.testing.assert_array_equal(single[0], res[i][0].cpu().numpy())
 
 
+def clustered(rng, n, d, hi, sigma, k=6):
+    c = rng.integers(0, hi, size=(k, d))
+    X = c[np.arange(n) % k] + rng.normal(0, sigma, size=(n, d))
+    return np.ascontiguousarray(X.clip(0, hi - 1).astype(np.int32))
+
+
+@pytest.mark.parametrize("key_class,n,d,hi,eps2", [
+    (0, 5000, 2, 100_000, 800 ** 2),         # 16 key bits + 13 index bits: packed
+    (1, 5000, 6, 1 << 24, 6 << 28),          # 60 key bits + 13 index bits: 64-bit key + index
+    (2, 3000, 8, 1 << 24, 8 << 20),          # 112 key bits: 128-bit key + index
+])
+def test_every_sort_key_class(ctx, key_class, n, d, hi, eps2):
+    """Each sort key layout gives the oracle's labels and its stable grid
+    order (ties in input order)."""
+    rng = np.random.default_rng(key_class + 40)
+    X = clustered(rng, n, d, hi, sigma=float(np.sqrt(eps2)) * 0.2)
+    got = run_gpu(ctx, X, eps2, 4)
+    assert ctx.last_sizes()["key_class"] == key_class
+    assert_same(got, oracle.grid(X, eps2, 4), f"key class {key_class}")
+    assert len(np.unique(got[0][got[0] >= 0])) > 1
+    gs = oracle.grid_structure(X, eps2)
+    np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_PERM, np.int32, n), gs["order"])
+
+
 def test_batched_mixed_key_widths_and_tiny(ctx):
     """One batch mixing 64- and 128-bit keys, a one-point instance and d=1."""
     rng = np.random.default_rng(9)
