@@ -57,8 +57,11 @@ def estimate_footprint(n: int, d: int, workspace_bytes) -> int:
 
 class GpuBackend:
     """Runs jobs through the C ABI: one Context and one CUDA stream per slot.
-    Inputs are staged through pinned host memory, results come back to host
-    numpy arrays."""
+    Each slot keeps grow-only staging buffers: pinned host memory for the
+    inputs and results of a batch, and device memory they are copied to and
+    from (one host-to-device and one device-to-host copy per batch)."""
+
+    ALIGN = 256
 
     def __init__(self, device: int = 0, slots: int = 4):
         import torch
@@ -68,31 +71,72 @@ class GpuBackend:
         self.device = torch.device("cuda", device)
         self.ctxs = [Context(device) for _ in range(slots)]
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.bufs = [{} for _ in range(slots)]
         self.workspace_bytes = workspace_bytes
 
     def footprint(self, n: int, d: int) -> int:
         return estimate_footprint(n, d, self.workspace_bytes)
 
+    def _buf(self, slot: int, name: str, nbytes: int, pinned: bool):
+        torch = self.torch
+        b = self.bufs[slot].get(name)
+        if b is None or b.numel() < nbytes:
+            size = max(nbytes + nbytes // 4, 1 << 20)
+            if pinned:
+                b = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+            else:
+                b = torch.empty(size, dtype=torch.uint8, device=self.device)
+            self.bufs[slot][name] = b
+        return b
+
     def run(self, slot: int, jobs):
         torch = self.torch
         ctx, stream = self.ctxs[slot], self.streams[slot]
+        al = self.ALIGN
+        up = lambda v: (v + al - 1) // al * al  # noqa: E731
+        in_off, out_off, tin, tout = [], [], 0, 0
+        for j in jobs:
+            in_off.append(tin)
+            tin += up(j.X.nbytes)
+            out_off.append(tout)
+            tout += up(4 * j.n) + up(j.n)
         with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            dev = []
-            for j in jobs:
-                h = torch.from_numpy(j.X).pin_memory()
-                dev.append((h.to(self.device, non_blocking=True), j.eps2, j.minpts))
+            hin = self._buf(slot, "hin", tin, True)
+            hout = self._buf(slot, "hout", tout, True)
+            din = self._buf(slot, "din", tin, False)
+            dout = self._buf(slot, "dout", tout, False)
+            hin_np = hin.numpy()
+            for j, o in zip(jobs, in_off):
+                hin_np[o:o + j.X.nbytes] = j.X.reshape(-1).view(np.uint8)
+            din[:tin].copy_(hin[:tin], non_blocking=True)
+            dev, outs = [], []
+            for j, oi, oo in zip(jobs, in_off, out_off):
+                n, d = j.X.shape
+                Xd = din[oi:oi + 4 * n * d].view(torch.int32).view(n, d)
+                lab = dout[oo:oo + 4 * n].view(torch.int32)
+                core = dout[oo + up(4 * n):oo + up(4 * n) + n]
+                dev.append((Xd, j.eps2, j.minpts))
+                outs.append((lab, core))
             if len(dev) == 1:
                 Xd, e, m = dev[0]
-                outs = [ctx.dbscan(Xd, e, m, stream=stream)]
+                ctx.dbscan(Xd, e, m, labels=outs[0][0], is_core=outs[0][1], stream=stream)
             else:
-                outs = ctx.dbscan_batched(dev, stream=stream)
-            res = [(lab.to("cpu", non_blocking=True), core.to("cpu", non_blocking=True)) for lab, core in outs]
+                ctx.dbscan_batched(dev, outputs=outs, stream=stream)
+            hout[:tout].copy_(dout[:tout], non_blocking=True)
             stream.synchronize()
-        return [(lab.numpy(), core.numpy().astype(bool)) for lab, core in res]
+        hout_np = hout.numpy()
+        res = []
+        for j, oo in zip(jobs, out_off):
+            n = j.n
+            lab = hout_np[oo:oo + 4 * n].view(np.int32).copy()
+            core = hout_np[oo + up(4 * n):oo + up(4 * n) + n].astype(bool)
+            res.append((lab, core))
+        return res
 
     def close(self):
         for c in self.ctxs:
             c.close()
+        self.bufs = [{} for _ in self.bufs]
 
 
 class Server:
@@ -223,6 +267,11 @@ class Server:
                     j.future.set_result(results[k])
 
     # --------------------------------------------------------------- stats
+    def reset_stats(self):
+        """Forget the finished jobs (e.g. after a warm-up pass)."""
+        with self.cv:
+            self.done = []
+
     def latencies(self):
         with self.cv:
             return np.array([j.t_done - j.t_submit for j in self.done])

@@ -125,6 +125,32 @@ def workload(name: str, seed: int = 1, n: int | None = None):
     raise KeyError(name)
 
 
+def serve_jobs(count: int = 48, seed: int = 1, n_lo: float = 1e3, n_hi: float = 1e7):
+    """The serving workload: `count` clustering jobs with n log-uniform in
+    [n_lo, n_hi], d uniform in {2, ..., 7}, eps uniform in [200, 2000],
+    MinPts uniform in {5, 10, 50, 100}; each job is Gaussian blobs (2 to 8
+    blobs, sigma uniform in [300, 3000]) plus 5% uniform noise.
+    Returns a list of (X, eps2, minpts)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        d = int(rng.integers(2, 8))
+        eps = int(rng.uniform(200, 2000))
+        minpts = int(rng.choice([5, 10, 50, 100]))
+        X = blobs(n, d, k=int(rng.integers(2, 9)), sigma=float(rng.uniform(300, 3000)), noise=0.05,
+                  seed=int(rng.integers(1 << 30)))
+        out.append((X, eps * eps, minpts))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = 1) -> np.ndarray:
+    """Arrival times (seconds from 0) of a Poisson stream of `count` requests
+    at `rate` per second: cumulative sums of exponential gaps."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
 def batch_instances(k: int = 256, seed: int = 1, n_lo: float = 1e3, n_hi: float = 5e5):
     """The batched workload: k independent instances with n log-uniform in
     [n_lo, n_hi], d uniform in {2, 3, 5, 7}, eps uniform in [200, 2000],
