@@ -34,6 +34,35 @@ WORKLOADS = {
 }
 L2_FLUSH_BYTES = 256 << 20
 
+# DRAM bytes (read + write) per onesweep launch, from one `ncu --set full`
+# capture of the kernel on the default workload, keyed by a digest of the sort
+# source it was taken on: a changed kernel reports no traffic until it is
+# captured again.
+ONESWEEP_TRAFFIC = {
+    "7585df61684318c5": {"workload": "ss3d_10m", "key_class": 0, "bytes": 127.8e6},
+}
+
+
+def sort_source_digest() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2210_07580_gb300", "csrc", "sort.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def reduce_over_ranks(ms: float, e2e_ms: float, points: int, ws: int, device):
+    """Job-wide values from rank-local ones: the max over ranks of the step
+    and end-to-end times, and the sum of the points the ranks clustered."""
+    if ws == 1:
+        return ms, e2e_ms, points
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([points], dtype=torch.int64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), float(t[1].item()), int(p[0].item())
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -43,9 +72,10 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling (every 10 ms) of SM clocks and throttle reasons;
+    only samples whose timestamps fall inside the marked window count."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -53,46 +83,64 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling and wait (up to 3 s) for the first sample."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 3.0
+        while time.time() < t_end and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        import datetime
+        self.t0 = datetime.datetime.now()
+
+    def mark_stop(self):
+        import datetime
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
+        import datetime
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        time.sleep(0.03)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() in ("active", "1")}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(nm)
         try:
             os.remove(self.path)
         except OSError:
             pass
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        sm = [r[1] for r in use]
+        reasons = set().union(*[r[3] for r in use]) if use else set()
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": use[-1][2] if use else None,
+                "reasons": sorted(reasons), "samples": len(sm), "in_timed_region": bool(inside)}
 
 
 def peaks():
@@ -288,10 +336,11 @@ def run_gpu(args):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stage_acc = {}
     launches = 0
+    sampler.start()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
+    sampler.mark_start()
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(k + 2)  # L2 flush, outside the timed events
@@ -303,14 +352,11 @@ def run_gpu(args):
         launches += ctx.last_sizes()["launches"]
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    sampler.mark_stop()
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     sizes = ctx.last_sizes()
     stages = {k: round(v / args.steps, 4) for k, v in stage_acc.items()}
     ctx.set_timing(False)
@@ -331,13 +377,9 @@ def run_gpu(args):
         ctx.dbscan_host(Xh, eps2, minpts, labels=Lh, is_core=Ch, stream=stream)
         e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = sum(e_ms) / len(e_ms)
-    e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e_t.item())
+    ms_max, e2e_ms, total_pts = reduce_over_ranks(ms, e2e_ms, n, ws, dev)
 
     if rank == 0:
-        total_pts = n * ws
         value = total_pts / (ms_max / 1e3) / 1e6
         peak, peak_kind = peaks()
         # dominant kernel: the onesweep radix-sort pass.  Algorithmic bytes
@@ -349,6 +391,9 @@ def run_gpu(args):
         launch_bytes = 2 * unit_bytes * n
         launch_ms = stages.get("sort", 0.0) / passes
         achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
+        tr = ONESWEEP_TRAFFIC.get(sort_source_digest())
+        traffic = (int(tr["bytes"]) if tr and tr["workload"] == args.workload and tr["key_class"] == sizes["key_class"]
+                   else None)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
@@ -366,7 +411,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "kernel": "onesweep_kernel (one radix-sort pass)",
                          "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                         "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
                          "bytes_per_launch": int(launch_bytes), "launch_ms": round(launch_ms, 4),
                          "launches_per_step": passes},
             "wall_s_timed": round(t_wall, 3),
@@ -393,7 +438,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gdbscan", "reference"], default="gdbscan")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ss3d_10m")
