@@ -300,18 +300,22 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 }
 
 // ----------------------------------------------------- the warp-level test
-// One warp per candidate pair of a wave:
+// A warp takes 32 consecutive candidate pairs of a wave, one per lane:
 //   1. skip if the grids are already in one set;
-//   2. the two box tests;
-//   3. the exact test over core points in 32 x 32 tiles (lane l holds a point
-//      of s_j, points of s_i are broadcast), stopping at the first pair within
-//      eps.  Pairs of two small sets (both at most kSmallSet points) are
-//      decided here in full (at most 16 tiles); any other pair gets `budget`
-//      diagonal tiles (distinct chunks of both sets), which finds a witness
-//      for nearly every pair that has many, and is otherwise handed to the
-//      block-level FastMerging kernel -- in particular a few points against
-//      thousands, where one scan of the large set usually decides.
+//   2. the two box tests (they alone decide pairs of one-point grids);
+//   3. pairs of at most kLaneDistances point pairs are decided by the lane
+//      itself.
+// The pairs still open are then taken one at a time by the whole warp: the
+// exact test over core points in 32 x 32 tiles (lane l holds a point of s_j,
+// points of s_i are broadcast), stopping at the first pair within eps.  Pairs
+// of two small sets (both at most kSmallSet points) are decided in full (at
+// most 16 tiles); any other pair gets `budget` diagonal tiles (distinct chunks
+// of both sets), which finds a witness for nearly every pair that has many,
+// and is otherwise handed to the block-level FastMerging kernel -- in
+// particular a few points against thousands, where one scan of the large set
+// usually decides.
 constexpr int kSmallSet = 128;
+constexpr int kLaneDistances = 16;
 
 template <int D>
 __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict__ ins, Flat f, int wave, int budget) {
@@ -319,33 +323,80 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict_
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long total = flat_total(f);
-    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
-        const int kk = flat_find(f, w);
-        const Inst& I = ins[f.idx[kk]];
-        const long long lw = w - f.off[kk];
-        const long long eps2 = I.p.eps2;
-        const int base = wave == 0 ? 0 : I.small[kSmPairsT];
-        const int2 pr = I.pairs[base + lw];
-        int* parent = I.parent;
-        int same = 0;
-        if (lane == 0) {
+    for (long long w0 = ((((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5)) * 32; w0 < total;
+         w0 += warps * 32) {
+        // ---- one pair per lane
+        const long long i = w0 + lane;
+        int inst = 0;
+        int2 pr = make_int2(0, 0);
+        bool open = false;
+        if (i < total) {
+            const int kk = flat_find(f, i);
+            inst = f.idx[kk];
+            const Inst& I = ins[inst];
+            const long long eps2 = I.p.eps2;
+            const int base = wave == 0 ? 0 : I.small[kSmPairsT];
+            pr = I.pairs[base + (i - f.off[kk])];
+            int* parent = I.parent;
             const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
-            if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
-            same = ra == rb;
+            if (ra < 0 || rb < 0) {
+                set_status(I, kDevTimeout);
+            } else if (ra != rb) {
+                const int dec =
+                    box_decision<D>(I.bbox + (long long)pr.x * 2 * D, I.bbox + (long long)pr.y * 2 * D, eps2);
+                bool yes = dec == 1;
+                if (dec < 0) {
+                    const int ai = I.core_start[pr.x], mi = I.core_start[pr.x + 1] - ai;
+                    const int aj = I.core_start[pr.y], mj = I.core_start[pr.y + 1] - aj;
+                    if (mi * mj <= kLaneDistances) {
+                        const int* Xc = I.Xc;
+                        for (int u = 0; u < mi && !yes; ++u) {
+                            int P[D];
+#pragma unroll
+                            for (int j = 0; j < D; ++j) P[j] = Xc[(long long)(ai + u) * DP + j];
+                            for (int v = 0; v < mj; ++v) {
+                                int Q[D];
+#pragma unroll
+                                for (int j = 0; j < D; ++j) Q[j] = Xc[(long long)(aj + v) * DP + j];
+                                if (sqdist<D>(P, Q) <= eps2) {
+                                    yes = true;
+                                    break;
+                                }
+                            }
+                        }
+                    } else {
+                        open = true;
+                    }
+                }
+                if (yes && !uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
+            }
         }
-        if (__shfl_sync(kFull, same, 0)) continue;
-
-        const int dec = box_decision<D>(I.bbox + (long long)pr.x * 2 * D, I.bbox + (long long)pr.y * 2 * D, eps2);
-        bool yes = dec == 1;
-        bool handed = false;
-        if (dec < 0) {
+        // ---- the open pairs, one at a time, by the whole warp
+        unsigned pend = __ballot_sync(kFull, open);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int oi = __shfl_sync(kFull, inst, src);
+            const int px = __shfl_sync(kFull, pr.x, src), py = __shfl_sync(kFull, pr.y, src);
+            const Inst& I = ins[oi];
+            const long long eps2 = I.p.eps2;
+            const int base = wave == 0 ? 0 : I.small[kSmPairsT];
+            int* parent = I.parent;
+            int same = 0;
+            if (lane == 0) {
+                const int ra = uf_find(parent, px), rb = uf_find(parent, py);
+                if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
+                same = ra == rb;
+            }
+            if (__shfl_sync(kFull, same, 0)) continue;
             const int* Xc = I.Xc;
-            const int ai = I.core_start[pr.x], mi = I.core_start[pr.x + 1] - ai;
-            const int aj = I.core_start[pr.y], mj = I.core_start[pr.y + 1] - aj;
+            const int ai = I.core_start[px], mi = I.core_start[px + 1] - ai;
+            const int aj = I.core_start[py], mj = I.core_start[py + 1] - aj;
             const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
             const long long tiles = (long long)na * nb;
             const bool exhaustive = mi <= kSmallSet && mj <= kSmallSet;
             const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
+            bool yes = false;
             for (long long t = 0; t < limit; ++t) {
                 const int ta = exhaustive ? (int)(t / nb) : (int)(t % na);
                 const int tb = (int)(t % nb);
@@ -370,13 +421,13 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict_
                     break;
                 }
             }
-            handed = !yes && limit < tiles;
-        }
-        if (lane == 0) {
-            if (yes) {
-                if (!uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
-            } else if (handed) {
-                I.hard[base + atomicAdd(I.small + kSmHard0 + wave, 1)] = pr;
+            const bool handed = !yes && limit < tiles;
+            if (lane == 0) {
+                if (yes) {
+                    if (!uf_union(parent, px, py)) set_status(I, kDevTimeout);
+                } else if (handed) {
+                    I.hard[base + atomicAdd(I.small + kSmHard0 + wave, 1)] = make_int2(px, py);
+                }
             }
         }
     }
