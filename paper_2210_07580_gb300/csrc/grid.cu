@@ -144,11 +144,13 @@ cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long lo
 
 // ---------------------------------------------------------------- bounds
 
-// Per-dimension min and max (mn_j of Eq. 1).  Each thread accumulates in
-// registers while its items stay in one instance and flushes with atomics
-// when it moves to another; at the end, a warp whose lanes all hold the same
-// instance reduces with shuffles and applies one atomic per dimension.  The
-// small blocks' mnmx must hold INT_MAX / INT_MIN first.
+// Per-dimension min and max (mn_j of Eq. 1).  Each warp takes a contiguous
+// chunk of the flat point space (lanes on consecutive points, so rows are read
+// coalesced); a lane accumulates in registers while its points stay in one
+// instance and flushes with atomics when it moves to the next one (rare: only
+// at instance boundaries inside the chunk).  At the end, a warp whose lanes
+// all hold the same instance reduces with shuffles and applies one atomic per
+// dimension.  The small blocks' mnmx must hold INT_MAX / INT_MIN first.
 __device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const int* mx) {
     for (int j = 0; j < I.p.d; ++j) {
         atomicMin(I.small + kSmMnmx + j, mn[j]);
@@ -157,7 +159,10 @@ __device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const
 }
 
 __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
+    const long long per = (((total + nwarps - 1) / nwarps) + 31) & ~31ll;
+    const long long beg = wid * per, end = min(total, beg + per);
     int mn[kMaxD], mx[kMaxD];
 #pragma unroll
     for (int j = 0; j < kMaxD; ++j) {
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ in
     int kk = -1;  // instance index of the accumulated values
     const int* X = nullptr;
     int d = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    for (long long i = beg + lane_id(); i < end; i += 32) {
         if (cur.seek(f, i)) {
             if (kk >= 0) bounds_flush(ins[kk], mn, mx);
 #pragma unroll

@@ -129,13 +129,16 @@ cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, cudaStr
 // that later checks can be skipped).
 
 template <bool FILL>
-__global__ void pair_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+__global__ void __launch_bounds__(256) pair_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    // one warp per grid; the lanes take 32 list entries at a time
+    const int lane = lane_id();
+    const unsigned lt = lanemask_lt();
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     FlatCursor cur;
-    GD_FOR_FLAT(i, total) {
-        cur.seek(f, i);
-        const int k = cur.k;
-        const Inst& I = ins[f.idx[k]];
-        const long long c = i - cur.lo;
+    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
+        cur.seek(f, w);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = w - cur.lo;
         const int d = I.p.d, C = I.small[kSmCells];
         const int* core_start = I.core_start;
         const int* coord = I.cell_coord;
@@ -147,42 +150,55 @@ __global__ void pair_kernel(const Inst* __restrict__ ins, Flat f, long long tota
                 out_t = I.pairs + I.pair_start[c];
                 out_f = I.pairs + I.pair_start[C] + I.pair_start_f[c];
             }
-            int g[kMaxD];
-            for (int j = 0; j < d; ++j) g[j] = coord[c * d + j];
-            for (int t = I.nbr_start[c]; t < I.nbr_start[c + 1]; ++t) {
-                const int j2 = I.nbr[t];
-                if (j2 <= c || core_start[j2 + 1] == core_start[j2]) continue;
+            const int gl = lane < d ? coord[c * d + lane] : 0;
+            const int t_end = I.nbr_start[c + 1];
+            for (int t0 = I.nbr_start[c]; t0 < t_end; t0 += 32) {
+                const int t = t0 + lane;
+                const int j2 = t < t_end ? I.nbr[t] : -1;
+                const bool keep = j2 > c && core_start[j2 + 1] > core_start[j2];
                 bool touching = true;
                 for (int j = 0; j < d; ++j) {
-                    const int dl = coord[(long long)j2 * d + j] - g[j];
-                    if (dl > 1 || dl < -1) touching = false;
+                    const int gj = __shfl_sync(kFull, gl, j);
+                    if (keep) {
+                        const int dl = coord[(long long)j2 * d + j] - gj;
+                        if (dl > 1 || dl < -1) touching = false;
+                    }
                 }
-                if (touching) {
-                    if (FILL) out_t[kt] = make_int2((int)c, j2);
-                    kt++;
-                } else {
-                    if (FILL) out_f[kf] = make_int2((int)c, j2);
-                    kf++;
+                const unsigned mt = __ballot_sync(kFull, keep && touching);
+                const unsigned mf = __ballot_sync(kFull, keep && !touching);
+                if (FILL && keep) {
+                    if (touching)
+                        out_t[kt + __popc(mt & lt)] = make_int2((int)c, j2);
+                    else
+                        out_f[kf + __popc(mf & lt)] = make_int2((int)c, j2);
                 }
+                kt += __popc(mt);
+                kf += __popc(mf);
             }
         }
-        if (!FILL) {
+        if (!FILL && lane == 0) {
             I.pair_start[c] = kt;
             I.pair_start_f[c] = kf;
         }
     }
 }
 
+static int warp_blocks_for(long long warps) {
+    long long b = (warps * 32 + 255) / 256;
+    if (b > kPersistBlocks) b = kPersistBlocks;
+    return b < 1 ? 1 : (int)b;
+}
+
 cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    pair_kernel<false><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    pair_kernel<false><<<warp_blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    pair_kernel<true><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    pair_kernel<true><<<warp_blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
