@@ -23,6 +23,11 @@ constexpr int kMaxD = 8;
 // Largest stencil radius r = 1 + (isqrt(eps2) - 1) / s with s = 1 + isqrt(eps2 / d):
 // s > sqrt(eps2 / d) gives (isqrt(eps2) - 1) / s < sqrt(d), so r <= 1 + floor(sqrt(8)) = 3.
 constexpr int kMaxR = 3;
+// Size buckets of instances (points): <= 2^12, 2^15, 2^18, 2^21, larger.
+constexpr int kSizeBuckets = 5;
+inline int size_bucket(long long n) {
+    return n <= (1 << 12) ? 0 : n <= (1 << 15) ? 1 : n <= (1 << 18) ? 2 : n <= (1 << 21) ? 3 : 4;
+}
 constexpr unsigned kFull = 0xffffffffu;
 
 // Bits of an instance's device status word (OR-ed by kernels).
@@ -235,6 +240,18 @@ __device__ __forceinline__ int uf_find(int* parent, int x) {
     return -1;
 }
 
+// The root of x without writing anything.  Used where every grid's pointer
+// must end at its root: a halving store by one thread can put back an older
+// ancestor over the root another thread has just written.
+__device__ __forceinline__ int uf_find_ro(const int* parent, int x) {
+    for (int it = 0; it < kMaxUfRetries; ++it) {
+        const int px = __ldcg(parent + x);
+        if (px == x) return x;
+        x = px;
+    }
+    return -1;
+}
+
 __device__ __forceinline__ void set_status(const Inst& I, unsigned bits) {
     atomicOr(reinterpret_cast<unsigned*>(I.small + kSmStatus), bits);
 }
@@ -342,14 +359,15 @@ struct WalkPool {
     long long cap, seg_cap;
 };
 enum WalkMode { kWalkCount = 0, kWalkFill = 1, kWalkPool = 2 };
-cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, cudaStream_t st);
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
+                        cudaStream_t st);
 cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st);
 
 // Core points (core.cu).
 cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st);
 cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Non-full points of instances with dimension d (flat offsets on the device).
-cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, cudaStream_t st);
+cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limit, cudaStream_t st);
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
@@ -365,13 +383,13 @@ cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStr
 cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Warp-level test of the candidate pairs of one wave (0: touching, 1: others)
 // of instances with dimension d; undecided pairs go to the instance's hard list.
-cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, cudaStream_t st);
+cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, int lane_limit,
+                              int small_set, cudaStream_t st);
 // FastMerging (Alg. 5) of the hard pairs of one wave: `blocks` blocks, block b
 // using the 2 * wpb bitmap words at scratch + 2 * wpb * b (wpb >= the largest
 // grid of the batch / 32 + 1).
 cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
                                cudaStream_t st);
-int merge_fm_blocks();
 
 // Labels (label.cu).
 cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cudaStream_t st);

@@ -31,7 +31,8 @@ __global__ void uf_compress_kernel(const Inst* __restrict__ ins, Flat f, long lo
         const int c = (int)(i - cur.lo);
         I.cid_root[c] = INT_MAX;
         if (I.core_start[c + 1] > I.core_start[c]) {
-            const int r = uf_find(I.parent, c);
+            // read-only: concurrent halving could undo this grid's pointer
+            const int r = uf_find_ro(I.parent, c);
             if (r < 0)
                 set_status(I, kDevTimeout);
             else

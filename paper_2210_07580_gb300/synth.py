@@ -151,20 +151,23 @@ def poisson_arrivals(count: int, rate: float, seed: int = 1) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-def batch_instances(k: int = 256, seed: int = 1, n_lo: float = 1e3, n_hi: float = 5e5):
+def batch_instances(k: int = 256, seed: int = 1, n_lo: float = 1e3, n_hi: float = 5e5, only=None):
     """The batched workload: k independent instances with n log-uniform in
     [n_lo, n_hi], d uniform in {2, 3, 5, 7}, eps uniform in [200, 2000],
     MinPts uniform in {5, 10, 50, 100}; each instance is Gaussian blobs (2 to
     8 blobs, sigma uniform in [300, 3000]) plus 5% uniform noise.
-    Returns a list of (X, eps2, minpts)."""
+    Returns a list of (X, eps2, minpts); with `only` (instance numbers), just
+    those instances, identical to their entries in the full list."""
     rng = np.random.default_rng(seed)
     out = []
-    for _ in range(k):
+    for i in range(k):
         n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
         d = int(rng.choice([2, 3, 5, 7]))
         eps = int(rng.uniform(200, 2000))
         minpts = int(rng.choice([5, 10, 50, 100]))
-        X = blobs(n, d, k=int(rng.integers(2, 9)), sigma=float(rng.uniform(300, 3000)), noise=0.05,
-                  seed=int(rng.integers(1 << 30)))
+        nblob, sigma, bseed = int(rng.integers(2, 9)), float(rng.uniform(300, 3000)), int(rng.integers(1 << 30))
+        if only is not None and i not in only:
+            continue
+        X = blobs(n, d, k=nblob, sigma=sigma, noise=0.05, seed=bseed)
         out.append((X, eps * eps, minpts))
     return out

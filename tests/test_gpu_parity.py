@@ -331,6 +331,22 @@ def test_every_sort_key_class(ctx, key_class, n, d, hi, eps2):
     np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_PERM, np.int32, n), gs["order"])
 
 
+def test_cluster_ids_identical_over_repeated_runs(ctx):
+    """A sparse 7-d instance (124,710 points, one-point grids) on which a race
+    in resolving cluster ids once left a grid with a private id in about one
+    run of 60: every run, in a reused or a fresh context, equals the oracle."""
+    (X, e, m), = synth.batch_instances(256, seed=21, only={66})
+    want = oracle.grid(X, e, m)
+    Xd = torch.from_numpy(X).cuda()
+    for rep in range(60):
+        c = ctx if rep % 2 else Context(0)
+        lab, core = c.dbscan(Xd, e, m)
+        torch.cuda.synchronize()
+        assert_same((lab.cpu().numpy(), core.cpu().numpy()), want, f"run {rep}")
+        if c is not ctx:
+            c.close()
+
+
 def test_batched_mixed_key_widths_and_tiny(ctx):
     """One batch mixing 64- and 128-bit keys, a one-point instance and d=1."""
     rng = np.random.default_rng(9)
