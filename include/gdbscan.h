@@ -137,6 +137,61 @@ typedef enum {
     GD_VIEW_CELL_CID = 6     /* int32 [C]: cluster id of each grid's core points, -1 if none */
 } gd_view;
 
+/* ---------------------------------------------------------------------
+ * Tuning knobs (no counterpart in the paper: launch and tile shapes of the
+ * GPU kernels).  A context resolves each knob for a group of instances of
+ * dimension d whose largest instance has n points: the first table entry
+ * with that knob, d (or 0 = any dimension) and n <= n_max gives the value;
+ * without one the built-in default applies.  Every value gives the same
+ * labels; only the speed changes.
+ *
+ *   GD_KNOB_MERGE_BUDGET  32x32 point tiles one warp tries on a candidate
+ *                         pair of core grids before it hands the pair to the
+ *                         block-level FastMerging kernel (Alg. 5); 1..64,
+ *                         default 2.
+ *   GD_KNOB_MERGE_LANE    pairs of core grids with at most this many point
+ *                         pairs are decided by one lane; 1..256, default 16.
+ *   GD_KNOB_MERGE_SMALL   pairs of core grids of at most this many core
+ *                         points each are decided in full by one warp;
+ *                         32..1024, default 128.
+ *   GD_KNOB_CORE_BANDS    a point's neighbour grids are scanned nearest band
+ *                         first when the list has at most this many grids;
+ *                         0..65536, default 128.
+ *   GD_KNOB_FM_BLOCKS     blocks of the FastMerging kernel; 152..19456,
+ *                         default 1216 (per batch: resolved for the batch's
+ *                         largest dimension and instance).
+ *   GD_KNOB_WALK_BLOCKS   blocks of the neighbour walk (4 warps each);
+ *                         152..19456, default 4864 (per batch, likewise).
+ *
+ * Groups: instances of one dimension whose sizes fall in one bucket (at most
+ * 2^12, 2^15, 2^18, 2^21 points, or more) are launched together and share
+ * the per-group knobs.
+ * --------------------------------------------------------------------- */
+typedef enum {
+    GD_KNOB_MERGE_BUDGET = 1,
+    GD_KNOB_MERGE_LANE = 2,
+    GD_KNOB_MERGE_SMALL = 3,
+    GD_KNOB_CORE_BANDS = 4,
+    GD_KNOB_FM_BLOCKS = 5,
+    GD_KNOB_WALK_BLOCKS = 6
+} gd_knob;
+
+typedef struct {
+    int32_t knob;  /* gd_knob */
+    int32_t d;     /* dimension the entry applies to, 0 = any */
+    int64_t n_max; /* applies to groups whose largest instance has <= n_max points */
+    int32_t value;
+} gd_tuning;
+
+/* Replace the context's tuning table with a copy of entries[0..count)
+ * (count = 0 clears it).  GD_EINVAL for an unknown knob, d outside [0,8],
+ * n_max < 0, a value outside the knob's range, or more than 1024 entries;
+ * the table is then unchanged. */
+gd_status gd_set_tuning(gd_ctx *ctx, const gd_tuning *entries, int count);
+
+/* The value a knob resolves to for dimension d and largest instance size n. */
+gd_status gd_get_knob(const gd_ctx *ctx, int knob, int d, int64_t n, int32_t *value);
+
 /* Sizes of the last run: out[0]=n, out[1]=d, out[2]=C (non-empty grids),
  * out[3]=nnbr (neighbour list length), out[4]=cell side s, out[5]=key bits,
  * out[6]=kernel launches of the run, out[7]=candidate merge pairs,

@@ -26,6 +26,17 @@ class GdInstance(ctypes.Structure):
                 ("minpts", ctypes.c_int32), ("labels", ctypes.c_void_p), ("is_core", ctypes.c_void_p)]
 
 
+class GdTuning(ctypes.Structure):
+    """gd_tuning of include/gdbscan.h."""
+    _fields_ = [("knob", ctypes.c_int32), ("d", ctypes.c_int32), ("n_max", ctypes.c_int64), ("value", ctypes.c_int32)]
+
+
+# gd_knob of include/gdbscan.h
+KNOBS = {"merge_budget": 1, "merge_lane": 2, "merge_small": 3, "core_bands": 4, "fm_blocks": 5, "walk_blocks": 6}
+# tuning table shipped with the package (written by autotune.py on a GB300)
+DEFAULT_TUNING = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+
+
 class GdError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"gdbscan error {status}: {msg}")
@@ -80,9 +91,21 @@ def load_library(path: str | None = None):
         lib.gd_dbscan_batched.restype = ctypes.c_int
         lib.gd_dbscan_noalloc.argtypes = [vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan_noalloc.restype = ctypes.c_int
+        lib.gd_set_tuning.argtypes = [vp, vp, ctypes.c_int]
+        lib.gd_set_tuning.restype = ctypes.c_int
+        lib.gd_get_knob.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int32)]
+        lib.gd_get_knob.restype = ctypes.c_int
         if path is None:
             _lib = lib
         return lib
+
+
+def load_tuning(path: str):
+    """A tuning table written by autotune.py: a list of (knob, d, n_max, value)."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    return [(e["knob"], e["d"], e["n_max"], e["value"]) for e in doc["entries"]]
 
 
 def eps2_from_eps(eps) -> int:
@@ -106,7 +129,10 @@ def _stream_handle(stream) -> int:
 class Context:
     """One gd_ctx: a device workspace reused across calls.  Not thread-safe."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, tuning="default"):
+        """tuning: "default" loads the table shipped with the package (if
+        present), None keeps the built-in defaults, or a list of entries as
+        for set_tuning."""
         self._lib = load_library()
         self.device = int(device)
         h = ctypes.c_void_p()
@@ -114,6 +140,26 @@ class Context:
         if st != GD_OK:
             raise GdError(st, self._lib.gd_status_str(st).decode())
         self._h = h
+        if tuning == "default":
+            if os.path.exists(DEFAULT_TUNING):
+                self.set_tuning(load_tuning(DEFAULT_TUNING))
+        elif tuning is not None:
+            self.set_tuning(tuning)
+
+    def set_tuning(self, entries):
+        """Replace the tuning table: entries of (knob, d, n_max, value), knob
+        a name of KNOBS or its number, d = 0 for any dimension.  The first
+        entry matching a group's dimension and largest size wins."""
+        arr = (GdTuning * max(len(entries), 1))()
+        for i, (kn, d, n_max, value) in enumerate(entries):
+            arr[i] = GdTuning(KNOBS[kn] if isinstance(kn, str) else int(kn), int(d), int(n_max), int(value))
+        self._check(self._lib.gd_set_tuning(self._h, ctypes.cast(arr, ctypes.c_void_p), len(entries)))
+
+    def get_knob(self, knob, d: int, n: int) -> int:
+        v = ctypes.c_int32()
+        self._check(self._lib.gd_get_knob(self._h, KNOBS[knob] if isinstance(knob, str) else int(knob), int(d),
+                                          int(n), ctypes.byref(v)))
+        return int(v.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -106,6 +106,7 @@ struct gd_ctx {
     std::string err;
     bool have_run = false;
     RunInfo info;
+    Tuning tuning;
 };
 
 namespace {
@@ -127,7 +128,7 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     ctx->mem.err = &ctx->err;
     ctx->info = RunInfo();
     const long long l0 = t_launches;
-    gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, merge_fm_blocks());
+    gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning);
     ctx->info.sizes[6] = t_launches - l0;
     if (s != GD_OK) {
         if (ctx->err.empty()) ctx->err = ctx->info.error;
@@ -259,6 +260,26 @@ gd_status gd_ctx_trim(gd_ctx* ctx) {
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     ctx->io = DevBuf();
     ctx->have_run = false;
+    return GD_OK;
+}
+
+gd_status gd_set_tuning(gd_ctx* ctx, const gd_tuning* entries, int count) {
+    if (!ctx) return GD_EINVAL;
+    if (count < 0 || count > kMaxTuning || (count > 0 && !entries))
+        return ctx->err = "tuning table: bad entry count or pointer", GD_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const gd_tuning& t = entries[i];
+        if (t.d < 0 || t.d > kMaxD || t.n_max < 0 || !knob_in_range(t.knob, t.value))
+            return ctx->err = "tuning table: bad entry " + std::to_string(i), GD_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) ctx->tuning.e[i] = entries[i];
+    ctx->tuning.count = count;
+    return GD_OK;
+}
+
+gd_status gd_get_knob(const gd_ctx* ctx, int knob, int d, int64_t n, int32_t* value) {
+    if (!ctx || !value || knob_default(knob) == 0) return GD_EINVAL;
+    *value = ctx->tuning.value(knob, d, n);
     return GD_OK;
 }
 

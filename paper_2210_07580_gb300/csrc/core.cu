@@ -90,7 +90,7 @@ __device__ __forceinline__ BoxDist box_dist(const long long* x, const int* __res
 // eps/2, eps), so that a core point usually reaches MinPts among the nearest
 // points.  The warp stops as soon as the count reaches MinPts.
 template <int D>
-__global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict__ ins, Flat f) {
+__global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict__ ins, Flat f, int band_limit) {
     constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
         }
         // straddling grids, nearest band first when the list is short (dense
         // neighbourhoods: few grids, many points each); one pass otherwise
-        const int nbands = (t_end - t_begin) <= 128 ? 3 : 1;
+        const int nbands = (t_end - t_begin) <= band_limit ? 3 : 1;
         for (int band = 0; band < nbands && cnt < minpts; ++band) {
             const long long blo = band == 0 ? -1 : (band == 1 ? eps2 / 16 : eps2 / 4);
             const long long bhi = nbands == 1 ? eps2 : (band == 0 ? eps2 / 16 : (band == 1 ? eps2 / 4 : eps2));
@@ -187,10 +187,10 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
     }
 }
 
-cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, cudaStream_t st) {
+cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limit, cudaStream_t st) {
     switch (d) {
 #define GD_CORE(DD) \
-    case DD: core_point_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, nf_pts); break;
+    case DD: core_point_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, nf_pts, band_limit); break;
         GD_CORE(1) GD_CORE(2) GD_CORE(3) GD_CORE(4) GD_CORE(5) GD_CORE(6) GD_CORE(7) GD_CORE(8)
 #undef GD_CORE
         default: return cudaErrorInvalidValue;

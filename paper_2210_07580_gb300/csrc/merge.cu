@@ -319,22 +319,19 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 // A warp takes 32 consecutive candidate pairs of a wave, one per lane:
 //   1. skip if the grids are already in one set;
 //   2. the two box tests (they alone decide pairs of one-point grids);
-//   3. pairs of at most kLaneDistances point pairs are decided by the lane
+//   3. pairs of at most `lane_limit` point pairs are decided by the lane
 //      itself.
 // The pairs still open are then taken one at a time by the whole warp: the
 // exact test over core points in 32 x 32 tiles (lane l holds a point of s_j,
 // points of s_i are broadcast), stopping at the first pair within eps.  Pairs
-// of two small sets (both at most kSmallSet points) are decided in full (at
-// most 16 tiles); any other pair gets `budget` diagonal tiles (distinct chunks
+// of two small sets (both at most `small_set` points) are decided in full; any other pair gets `budget` diagonal tiles (distinct chunks
 // of both sets), which finds a witness for nearly every pair that has many,
 // and is otherwise handed to the block-level FastMerging kernel -- in
 // particular a few points against thousands, where one scan of the large set
 // usually decides.
-constexpr int kSmallSet = 128;
-constexpr int kLaneDistances = 16;
-
 template <int D>
-__global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict__ ins, Flat f, int wave, int budget) {
+__global__ void __launch_bounds__(256)
+    merge_warp_kernel(const Inst* __restrict__ ins, Flat f, int wave, int budget, int lane_limit, int small_set) {
     constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -364,7 +361,7 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict_
                 if (dec < 0) {
                     const int ai = I.core_start[pr.x], mi = I.core_start[pr.x + 1] - ai;
                     const int aj = I.core_start[pr.y], mj = I.core_start[pr.y + 1] - aj;
-                    if (mi * mj <= kLaneDistances) {
+                    if ((long long)mi * mj <= lane_limit) {
                         const int* Xc = I.Xc;
                         for (int u = 0; u < mi && !yes; ++u) {
                             int P[D];
@@ -410,7 +407,7 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict_
             const int aj = I.core_start[py], mj = I.core_start[py + 1] - aj;
             const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
             const long long tiles = (long long)na * nb;
-            const bool exhaustive = mi <= kSmallSet && mj <= kSmallSet;
+            const bool exhaustive = mi <= small_set && mj <= small_set;
             const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
             bool yes = false;
             for (long long t = 0; t < limit; ++t) {
@@ -449,10 +446,13 @@ __global__ void __launch_bounds__(256) merge_warp_kernel(const Inst* __restrict_
     }
 }
 
-cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, cudaStream_t st) {
+cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, int lane_limit,
+                              int small_set, cudaStream_t st) {
     switch (d) {
-#define GD_MW(DD) \
-    case DD: merge_warp_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, pairs, wave, budget); break;
+#define GD_MW(DD)                                                                                          \
+    case DD:                                                                                               \
+        merge_warp_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, pairs, wave, budget, lane_limit, small_set); \
+        break;
         GD_MW(1) GD_MW(2) GD_MW(3) GD_MW(4) GD_MW(5) GD_MW(6) GD_MW(7) GD_MW(8)
 #undef GD_MW
         default: return cudaErrorInvalidValue;
@@ -666,7 +666,6 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
     }
 }
 
-int merge_fm_blocks() { return 152 * 8; }
 
 cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
                                cudaStream_t st) {

@@ -423,10 +423,11 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     }
 }
 
-cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, cudaStream_t st) {
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
+                        cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     long long b = (total + kWalkWarps - 1) / kWalkWarps;
-    if (b > kPersistBlocks * 2) b = kPersistBlocks * 2;
+    if (b > blocks) b = blocks;
     if (mode == kWalkFill)
         walk_kernel<kWalkFill><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
     else if (mode == kWalkPool)

@@ -61,6 +61,17 @@ struct StaticMem : MemProvider {
     }
 };
 
+// The FastMerging kernel's bitmaps come from the static array too: few blocks.
+const Tuning& noalloc_tuning() {
+    static Tuning t = [] {
+        Tuning u;
+        u.e[0] = gd_tuning{GD_KNOB_FM_BLOCKS, 0, INT64_MAX, 152};
+        u.count = 1;
+        return u;
+    }();
+    return t;
+}
+
 }  // namespace
 
 extern "C" gd_status gd_dbscan_noalloc(const int32_t* X, int64_t n, int d, int64_t eps2, int32_t minpts,
@@ -87,5 +98,5 @@ extern "C" gd_status gd_dbscan_noalloc(const int32_t* X, int64_t n, int d, int64
     // The driver clears every piece of device state it reads before it reads
     // it, so nothing left in the array by an earlier call leaks into this one.
     const gd_instance g{X, n, d, eps2, minpts, labels, is_core};
-    return run_batch(mem, 1, &g, (cudaStream_t)stream, nullptr, nullptr, 152);
+    return run_batch(mem, 1, &g, (cudaStream_t)stream, nullptr, nullptr, &noalloc_tuning());
 }

@@ -161,7 +161,8 @@ struct Run {
     cudaStream_t st;
     cudaEvent_t* ev;
     RunInfo* info;
-    int fm_blocks;
+    const Tuning* tune;
+    int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
 
     HI* hi = nullptr;
     int* hsmall = nullptr;   // host mirror of the small blocks [K][kSmallInts]
@@ -483,6 +484,10 @@ gd_status Run::go() {
         if (hi[k].maxcell > max_cell) max_cell = hi[k].maxcell;
     }
     const int wpb = (int)((max_cell + 31) / 32 + 1);
+    long long n_largest = 1;
+    for (int k = 0; k < K; ++k) n_largest = in[k].n > n_largest ? in[k].n : n_largest;
+    const int fm_blocks = knob(GD_KNOB_FM_BLOCKS, dmax, n_largest);
+    const int walk_blocks = knob(GD_KNOB_WALK_BLOCKS, dmax, n_largest);
     void* scr = nullptr;
     RUN_TRY(mem.device(kMemScratch, (size_t)fm_blocks * 2 * wpb * 4, &scr));
 
@@ -543,7 +548,8 @@ gd_status Run::go() {
         }
     }
     const bool pooled = pool.data != nullptr;
-    RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, st), "walk");
+    RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
+             "walk");
     RUN_TRY(scan(nseg, K, nseg_tiles));
     RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
     RUN_TRY(readback());
@@ -581,25 +587,34 @@ gd_status Run::go() {
     RUN_TRY(begin_desc());
     const Flat cells = flat(members, K, C_of, &tot);
     const Flat pts = flat(members, K, n_of, &tot);
-    // per-dimension groups
-    int dgroups[kMaxD], ng = 0;
+    // groups of instances by dimension and size bucket: the kernels that
+    // take the dimension as a template argument, and the tuning knobs, go
+    // by group
+    constexpr int kGroups = kMaxD * kSizeBuckets;
+    int dgroups[kGroups], gbucket[kGroups], ng = 0;
+    long long gn[kGroups];
     for (int d = 1; d <= kMaxD; ++d)
-        for (int k = 0; k < K; ++k)
-            if (hi[k].dev.p.d == d) {
-                dgroups[ng++] = d;
-                break;
+        for (int bk = 0; bk < kSizeBuckets; ++bk) {
+            long long nmax = 0;
+            for (int k = 0; k < K; ++k)
+                if (hi[k].dev.p.d == d && size_bucket(in[k].n) == bk && in[k].n > nmax) nmax = in[k].n;
+            if (nmax > 0) {
+                dgroups[ng] = d;
+                gbucket[ng] = bk;
+                gn[ng++] = nmax;
             }
-    Flat g_pts[kMaxD], g_nf[kMaxD], g_pair[2][kMaxD], g_hard[2][kMaxD];
-    long long* g_nf_off[kMaxD];
-    long long* g_pair_off[2][kMaxD];
-    long long* g_hard_off[2][kMaxD];
-    long long g_pts_tot[kMaxD];
-    int g_m[kMaxD];
-    const int* g_idx[kMaxD];
+        }
+    Flat g_pts[kGroups], g_nf[kGroups], g_pair[2][kGroups], g_hard[2][kGroups];
+    long long* g_nf_off[kGroups];
+    long long* g_pair_off[2][kGroups];
+    long long* g_hard_off[2][kGroups];
+    long long g_pts_tot[kGroups];
+    int g_m[kGroups];
+    const int* g_idx[kGroups];
     for (int gi = 0; gi < ng; ++gi) {
         int m = 0;
         for (int k = 0; k < K; ++k)
-            if (hi[k].dev.p.d == dgroups[gi]) members2[m++] = k;
+            if (hi[k].dev.p.d == dgroups[gi] && size_bucket(in[k].n) == gbucket[gi]) members2[m++] = k;
         g_m[gi] = m;
         g_pts[gi] = flat(members2, m, n_of, &g_pts_tot[gi]);
         g_idx[gi] = g_pts[gi].idx;
@@ -630,7 +645,7 @@ gd_status Run::go() {
     if (pool_segs >= 0)
         RUN_CUDA(launch_pool_scatter(dins, pool, pool_segs, st), "neighbour scatter");
     else
-        RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, st), "walk fill");
+        RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
     mark(6);
     RUN_CUDA(launch_core_full(dins, pts, total_pts, st), "core (full grids)");
     RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
@@ -638,7 +653,8 @@ gd_status Run::go() {
     RUN_CUDA(launch_totals(dins, idx, K, 2, st), "totals");
     for (int gi = 0; gi < ng; ++gi) {
         RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
-        RUN_CUDA(launch_core_point(dins, g_nf[gi], dgroups[gi], st), "core (counting)");
+        RUN_CUDA(launch_core_point(dins, g_nf[gi], dgroups[gi], knob(GD_KNOB_CORE_BANDS, dgroups[gi], gn[gi]), st),
+                 "core (counting)");
     }
     mark(7);
     RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
@@ -656,7 +672,10 @@ gd_status Run::go() {
         for (int gi = 0; gi < ng; ++gi) {
             RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], w == 0 ? kSmPairsT : kSmPairsF, g_pair_off[w][gi], st),
                      "flat offsets");
-            RUN_CUDA(launch_merge_warp(dins, g_pair[w][gi], w, dgroups[gi], 2, st), "merge (warp)");
+            const int d = dgroups[gi];
+            RUN_CUDA(launch_merge_warp(dins, g_pair[w][gi], w, d, knob(GD_KNOB_MERGE_BUDGET, d, gn[gi]),
+                                       knob(GD_KNOB_MERGE_LANE, d, gn[gi]), knob(GD_KNOB_MERGE_SMALL, d, gn[gi]), st),
+                     "merge (warp)");
         }
         for (int gi = 0; gi < ng; ++gi) {
             RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmHard0 + w, g_hard_off[w][gi], st), "flat offsets");
@@ -712,9 +731,39 @@ gd_status Run::go() {
 
 }  // namespace
 
+int knob_default(int knob) {
+    switch (knob) {
+        case GD_KNOB_MERGE_BUDGET: return 2;
+        case GD_KNOB_MERGE_LANE: return 16;
+        case GD_KNOB_MERGE_SMALL: return 128;
+        case GD_KNOB_CORE_BANDS: return 128;
+        case GD_KNOB_FM_BLOCKS: return 152 * 8;
+        case GD_KNOB_WALK_BLOCKS: return 152 * 32;
+        default: return 0;
+    }
+}
+
+bool knob_in_range(int knob, int v) {
+    switch (knob) {
+        case GD_KNOB_MERGE_BUDGET: return v >= 1 && v <= 64;
+        case GD_KNOB_MERGE_LANE: return v >= 1 && v <= 256;
+        case GD_KNOB_MERGE_SMALL: return v >= 32 && v <= 1024;
+        case GD_KNOB_CORE_BANDS: return v >= 0 && v <= 65536;
+        case GD_KNOB_FM_BLOCKS:
+        case GD_KNOB_WALK_BLOCKS: return v >= 152 && v <= 152 * 128;
+        default: return false;
+    }
+}
+
+int Tuning::value(int knob, int d, long long n) const {
+    for (int i = 0; i < count; ++i)
+        if (e[i].knob == knob && (e[i].d == 0 || e[i].d == d) && n <= e[i].n_max) return e[i].value;
+    return knob_default(knob);
+}
+
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, int fm_blocks) {
-    Run r{mem, K, inst, st, events, info, fm_blocks};
+                    RunInfo* info, const Tuning* tuning) {
+    Run r{mem, K, inst, st, events, info, tuning};
     const long long l0 = t_launches;
     const gd_status s = r.go();
     if (info) info->launches = t_launches - l0;

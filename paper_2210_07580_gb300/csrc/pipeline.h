@@ -46,9 +46,22 @@ struct RunInfo {
     std::string error;
 };
 
+// A context's tuning table (knobs of gdbscan.h).
+constexpr int kMaxTuning = 1024;
+struct Tuning {
+    int count = 0;
+    gd_tuning e[kMaxTuning];
+    // The value of `knob` for a group of dimension d whose largest instance
+    // has n points: the first matching entry, else the default.
+    int value(int knob, int d, long long n) const;
+};
+int knob_default(int knob);
+bool knob_in_range(int knob, int value);
+
 // Runs K instances.  The result of instance k is in inst[k].labels /
-// is_core (device pointers).  Returns the first error; `info` may be null.
+// is_core (device pointers).  Returns the first error; `info` and `tuning`
+// may be null (defaults).
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, int fm_blocks);
+                    RunInfo* info, const Tuning* tuning);
 
 }  // namespace gd
