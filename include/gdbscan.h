@@ -192,6 +192,18 @@ gd_status gd_set_tuning(gd_ctx *ctx, const gd_tuning *entries, int count);
 /* The value a knob resolves to for dimension d and largest instance size n. */
 gd_status gd_get_knob(const gd_ctx *ctx, int knob, int d, int64_t n, int32_t *value);
 
+/* CUDA graphs (no counterpart in the paper).  A call reads sizes back from
+ * the device three times, which splits its launches into four phases.  With
+ * graphs on, each phase's launches are captured from the call's stream into
+ * a graph that the context keeps (one per phase): the next call updates it
+ * in place when only launch parameters differ (re-instantiating it when the
+ * launch sequence differs) and launches the phase as one graph.  Results are
+ * identical either way.  Off by default for a new context; the stream must
+ * not be capturing already.  gd_graph_stats: out[0] = graph launches,
+ * out[1] = in-place updates, out[2] = instantiations, since creation. */
+gd_status gd_set_graphs(gd_ctx *ctx, int enable);
+gd_status gd_graph_stats(const gd_ctx *ctx, int64_t out[3]);
+
 /* Sizes of the last run: out[0]=n, out[1]=d, out[2]=C (non-empty grids),
  * out[3]=nnbr (neighbour list length), out[4]=cell side s, out[5]=key bits,
  * out[6]=kernel launches of the run, out[7]=candidate merge pairs,

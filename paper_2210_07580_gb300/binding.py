@@ -91,6 +91,10 @@ def load_library(path: str | None = None):
         lib.gd_dbscan_batched.restype = ctypes.c_int
         lib.gd_dbscan_noalloc.argtypes = [vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan_noalloc.restype = ctypes.c_int
+        lib.gd_set_graphs.argtypes = [vp, ctypes.c_int]
+        lib.gd_set_graphs.restype = ctypes.c_int
+        lib.gd_graph_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.gd_graph_stats.restype = ctypes.c_int
         lib.gd_set_tuning.argtypes = [vp, vp, ctypes.c_int]
         lib.gd_set_tuning.restype = ctypes.c_int
         lib.gd_get_knob.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int32)]
@@ -129,10 +133,11 @@ def _stream_handle(stream) -> int:
 class Context:
     """One gd_ctx: a device workspace reused across calls.  Not thread-safe."""
 
-    def __init__(self, device: int = 0, tuning="default"):
+    def __init__(self, device: int = 0, tuning="default", graphs: bool = True):
         """tuning: "default" loads the table shipped with the package (if
         present), None keeps the built-in defaults, or a list of entries as
-        for set_tuning."""
+        for set_tuning.  graphs: launch each phase of a call as a CUDA graph
+        kept by the context (gd_set_graphs)."""
         self._lib = load_library()
         self.device = int(device)
         h = ctypes.c_void_p()
@@ -140,6 +145,8 @@ class Context:
         if st != GD_OK:
             raise GdError(st, self._lib.gd_status_str(st).decode())
         self._h = h
+        if graphs:
+            self.set_graphs(True)
         if tuning == "default":
             if os.path.exists(DEFAULT_TUNING):
                 self.set_tuning(load_tuning(DEFAULT_TUNING))
@@ -154,6 +161,15 @@ class Context:
         for i, (kn, d, n_max, value) in enumerate(entries):
             arr[i] = GdTuning(KNOBS[kn] if isinstance(kn, str) else int(kn), int(d), int(n_max), int(value))
         self._check(self._lib.gd_set_tuning(self._h, ctypes.cast(arr, ctypes.c_void_p), len(entries)))
+
+    def set_graphs(self, enable: bool):
+        """Launch each phase of a call as a CUDA graph kept by the context."""
+        self._check(self._lib.gd_set_graphs(self._h, 1 if enable else 0))
+
+    def graph_stats(self) -> dict:
+        out = (ctypes.c_int64 * 3)()
+        self._check(self._lib.gd_graph_stats(self._h, out))
+        return {"launches": int(out[0]), "updates": int(out[1]), "instantiations": int(out[2])}
 
     def get_knob(self, knob, d: int, n: int) -> int:
         v = ctypes.c_int32()

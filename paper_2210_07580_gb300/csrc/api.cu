@@ -107,6 +107,11 @@ struct gd_ctx {
     bool have_run = false;
     RunInfo info;
     Tuning tuning;
+    PhaseGraphs graphs;
+    // graphs cannot be captured from the legacy default stream: such calls
+    // run on this stream, ordered after the caller's by an event
+    cudaStream_t own = nullptr;
+    cudaEvent_t own_ev = nullptr;
 };
 
 namespace {
@@ -124,11 +129,26 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     ctx->have_run = false;
     ctx->nstages = 0;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
+    if (ctx->graphs.enabled && (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)) {
+        if (!ctx->own) {
+            if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->own_ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return ctx->err = "stream creation failed", GD_ECUDA;
+            }
+        }
+        // the call returns after its work on `own` is done, so later work on
+        // the caller's stream is ordered after it
+        if (cudaEventRecord(ctx->own_ev, st) != cudaSuccess || cudaStreamWaitEvent(ctx->own, ctx->own_ev, 0) != cudaSuccess)
+            return ctx->err = "stream ordering failed", GD_ECUDA;
+        st = ctx->own;
+    }
     ctx->mem.st = st;
     ctx->mem.err = &ctx->err;
     ctx->info = RunInfo();
     const long long l0 = t_launches;
-    gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning);
+    gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning,
+                            &ctx->graphs);
     ctx->info.sizes[6] = t_launches - l0;
     if (s != GD_OK) {
         if (ctx->err.empty()) ctx->err = ctx->info.error;
@@ -167,6 +187,9 @@ void gd_destroy(gd_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    ctx->graphs.release();
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    if (ctx->own_ev) cudaEventDestroy(ctx->own_ev);
     ctx->mem.release();
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     for (int i = 0; i <= kStages; ++i)
@@ -256,10 +279,25 @@ gd_status gd_ctx_trim(gd_ctx* ctx) {
     if (!ctx) return GD_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return GD_ECUDA;
     if (ctx->mem.st) cudaStreamSynchronize(ctx->mem.st);
+    ctx->graphs.release();
     ctx->mem.release();
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     ctx->io = DevBuf();
     ctx->have_run = false;
+    return GD_OK;
+}
+
+gd_status gd_set_graphs(gd_ctx* ctx, int enable) {
+    if (!ctx) return GD_EINVAL;
+    ctx->graphs.enabled = enable != 0;
+    return GD_OK;
+}
+
+gd_status gd_graph_stats(const gd_ctx* ctx, int64_t out[3]) {
+    if (!ctx || !out) return GD_EINVAL;
+    out[0] = ctx->graphs.launches;
+    out[1] = ctx->graphs.updates;
+    out[2] = ctx->graphs.instantiations;
     return GD_OK;
 }
 

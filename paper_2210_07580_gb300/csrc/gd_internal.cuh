@@ -330,6 +330,9 @@ cudaError_t launch_quantise_hist(const Inst* ins, Flat tiles, long long total, i
 cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st);
 // One onesweep pass over the tiles of the instances in `tiles` (each with
 // more than `pass` passes and the given key width).
+// Sets the onesweep kernels' shared-memory limit on the current device (once
+// per device; before any stream capture).
+cudaError_t prepare_onesweep();
 cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
                             int* flat_counter, cudaStream_t st);
 

@@ -162,7 +162,53 @@ struct Run {
     cudaEvent_t* ev;
     RunInfo* info;
     const Tuning* tune;
+    PhaseGraphs* graphs;
     int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
+
+    // Runs the launches of phase `id` (body issues them on st): directly, or
+    // captured into the phase's executable graph and launched as one graph.
+    // A capture that fails is discarded and the launches are issued directly.
+    template <typename F> gd_status phase(int id, F&& body) {
+        if (!graphs || !graphs->enabled) return body();
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return body();
+        }
+        const gd_status s = body();
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (s != GD_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (s != GD_OK) return s;
+            return body();
+        }
+        cudaGraphExec_t& ex = graphs->exec[id];
+        bool ready = false;
+        if (ex) {
+            cudaGraphExecUpdateResultInfo ri;
+            if (cudaGraphExecUpdate(ex, g, &ri) == cudaSuccess) {
+                ready = true;
+                graphs->updates++;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ex);
+                ex = nullptr;
+            }
+        }
+        if (!ready) {
+            if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+                cudaGetLastError();
+                ex = nullptr;
+                cudaGraphDestroy(g);
+                return body();
+            }
+            graphs->instantiations++;
+        }
+        cudaGraphDestroy(g);
+        graphs->launches++;
+        return cuda(cudaGraphLaunch(ex, st), "graph launch");
+    }
 
     HI* hi = nullptr;
     int* hsmall = nullptr;   // host mirror of the small blocks [K][kSmallInts]
@@ -187,7 +233,14 @@ struct Run {
         return GD_ECUDA;
     }
     void mark(int s) {
-        if (ev) cudaEventRecord(ev[s], st);
+        if (!ev) return;
+        // inside a captured phase an external record becomes a graph node
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(ev[s], st, cudaEventRecordExternal);
+        else
+            cudaEventRecord(ev[s], st);
     }
 
     gd_status begin_desc() {
@@ -354,8 +407,11 @@ gd_status Run::go() {
     RUN_TRY(begin_desc());
     const Flat pts0 = flat(members, K, n_of, &tot);
     RUN_TRY(upload_desc());
-    RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
-    RUN_CUDA(launch_bounds(dins, pts0, total_pts, st), "bounds");
+    RUN_TRY(phase(0, [&]() -> gd_status {
+        RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
+        RUN_CUDA(launch_bounds(dins, pts0, total_pts, st), "bounds");
+        return GD_OK;
+    }));
     RUN_TRY(readback());
 
     // ------------------------- phase 2: keys, sort, compaction (sync 2)
@@ -458,7 +514,9 @@ gd_status Run::go() {
         &cseg_tiles);
     const int* idx = idx_all();
     RUN_TRY(upload_desc());
+    RUN_CUDA(prepare_onesweep(), "sort set-up");
 
+    RUN_TRY(phase(1, [&]() -> gd_status {
     mark(1);
     RUN_CUDA(zero_ranges(zr_dev, K, zr_total, st), "clear sort state");
     for (int w = 0; w < 3; ++w)
@@ -474,6 +532,8 @@ gd_status Run::go() {
     RUN_TRY(scan(cseg, K, cseg_tiles));
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w, st), "compact write");
     RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
+    return GD_OK;
+    }));
     RUN_TRY(readback());
 
     // ------------------------ phase 3: levels, walk count (sync 3)
@@ -524,15 +584,6 @@ gd_status Run::go() {
     idx = idx_all();
     RUN_TRY(upload_desc());
 
-    mark(4);
-    RUN_CUDA(launch_point_boxes(dins, cells2, total_cells, st), "point boxes");
-    RUN_CUDA(launch_level_diff(dins, cells2, total_cells, st), "levels");
-    for (int j = 0; j + 1 < dmax; ++j) {
-        RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
-        RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
-    }
-    RUN_CUDA(launch_level_write(dins, cells2, total_cells, st), "level write");
-    mark(5);
     // Single pass when a pool can be had: sized from the most neighbour
     // entries per grid this memory has seen (a first run guesses).
     WalkPool pool{};
@@ -548,10 +599,22 @@ gd_status Run::go() {
         }
     }
     const bool pooled = pool.data != nullptr;
+    RUN_TRY(phase(2, [&]() -> gd_status {
+    mark(4);
+    RUN_CUDA(launch_point_boxes(dins, cells2, total_cells, st), "point boxes");
+    RUN_CUDA(launch_level_diff(dins, cells2, total_cells, st), "levels");
+    for (int j = 0; j + 1 < dmax; ++j) {
+        RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
+        RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
+    }
+    RUN_CUDA(launch_level_write(dins, cells2, total_cells, st), "level write");
+    mark(5);
     RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
              "walk");
     RUN_TRY(scan(nseg, K, nseg_tiles));
     RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
+    return GD_OK;
+    }));
     RUN_TRY(readback());
     long long pool_segs = -1;  // -1: fill by a second walk
     if (pooled) {
@@ -642,6 +705,7 @@ gd_status Run::go() {
     idx = idx_all();
     RUN_TRY(upload_desc());
 
+    RUN_TRY(phase(3, [&]() -> gd_status {
     if (pool_segs >= 0)
         RUN_CUDA(launch_pool_scatter(dins, pool, pool_segs, st), "neighbour scatter");
     else
@@ -689,6 +753,8 @@ gd_status Run::go() {
     for (int gi = 0; gi < ng; ++gi)
         RUN_CUDA(launch_labels(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "labels");
     mark(11);
+    return GD_OK;
+    }));
     RUN_TRY(readback());
     for (int k = 0; k < K; ++k)
         if ((unsigned)sm(k)[kSmStatus] & kDevTimeout)
@@ -762,8 +828,8 @@ int Tuning::value(int knob, int d, long long n) const {
 }
 
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, const Tuning* tuning) {
-    Run r{mem, K, inst, st, events, info, tuning};
+                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs) {
+    Run r{mem, K, inst, st, events, info, tuning, graphs};
     const long long l0 = t_launches;
     const gd_status s = r.go();
     if (info) info->launches = t_launches - l0;

@@ -58,10 +58,28 @@ struct Tuning {
 int knob_default(int knob);
 bool knob_in_range(int knob, int value);
 
+// Executable graphs of the driver's four launch phases (the work between two
+// reads of sizes), one per phase, kept by a context between calls.  Each call
+// captures a phase's launches from its stream and updates the executable
+// graph in place when only parameters changed (re-instantiating it when the
+// launch sequence changed), then launches it.
+struct PhaseGraphs {
+    bool enabled = false;
+    cudaGraphExec_t exec[4] = {};
+    long long launches = 0, updates = 0, instantiations = 0;
+    void release() {
+        for (auto& e : exec)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    }
+};
+
 // Runs K instances.  The result of instance k is in inst[k].labels /
 // is_core (device pointers).  Returns the first error; `info` and `tuning`
 // may be null (defaults).
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, const Tuning* tuning);
+                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs = nullptr);
 
 }  // namespace gd

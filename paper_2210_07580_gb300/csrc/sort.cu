@@ -20,6 +20,8 @@
 // bounded: a block only ever waits for tiles handed out before its own (tile
 // ids are taken in order from one counter over the whole batch), and gives
 // up with kDevTimeout after a fixed number of polls.
+#include <atomic>
+
 #include "gd_internal.cuh"
 
 namespace gd {
@@ -395,11 +397,28 @@ template <typename K, bool PACKED>
 static cudaError_t onesweep_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets,
                                    int* flat_counter, cudaStream_t st) {
     const size_t smem = onesweep_smem<K, PACKED>(max_buckets);
-    const cudaError_t e =
-        cudaFuncSetAttribute(onesweep_kernel<K, PACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     onesweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
     return cudaSuccess;
+}
+
+cudaError_t prepare_onesweep() {
+    static std::atomic<unsigned long long> done{0};  // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)onesweep_smem<unsigned long long, true>(kMaxBuckets));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<unsigned long long, false>(kMaxBuckets));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(onesweep_kernel<Key2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<Key2, false>(kMaxBuckets));
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
 }
 
 cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
