@@ -9,6 +9,9 @@ overlaps on the device.  Scheduling:
 - admission by HBM footprint: a job is started only when a slot is free and
   its estimated device footprint fits in what the budget has left; jobs that
   do not fit wait (small jobs behind them may go first -- backfill);
+- a large job (more than `large_job_points` points) keeps the whole GPU busy
+  by itself, so at most `max_large` of them run at a time (running two only
+  makes them compete for L2); batches of small jobs may run beside them;
 - continuous batching: a slot that takes a small job also takes the other
   small jobs queued at that moment (up to a point and job budget) and runs
   them as one gd_dbscan_batched call; large jobs run alone;
@@ -145,7 +148,7 @@ class Server:
 
     def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int | None = None,
                  small_job_points: int = 200_000, batch_max_jobs: int = 64, batch_max_points: int = 4_000_000,
-                 backend=None):
+                 large_job_points: int = 1_000_000, max_large: int = 1, backend=None):
         self.backend = backend if backend is not None else GpuBackend(device, slots)
         if hbm_budget is None:
             import torch
@@ -156,6 +159,9 @@ class Server:
         self.small = small_job_points
         self.batch_max_jobs = batch_max_jobs
         self.batch_max_points = batch_max_points
+        self.large = large_job_points
+        self.max_large = max_large
+        self.large_inflight = 0
         self.queue: collections.deque[Job] = collections.deque()
         self.cv = threading.Condition()
         self.closed = False
@@ -207,6 +213,9 @@ class Server:
             return None
         room = self.budget - self.in_use
         head = self.queue[0]
+        if head.n > self.large and self.large_inflight >= self.max_large:
+            # the GPU is taken by large jobs: only small jobs may start now
+            return self._take_small(room)
         if head.footprint <= room:
             if head.n > self.small:
                 self.queue.popleft()
@@ -224,10 +233,25 @@ class Server:
                 self.queue.remove(j)
             return batch
         for j in self.queue:
-            if j.footprint <= room:
+            if j.footprint <= room and not (j.n > self.large and self.large_inflight >= self.max_large):
                 self.queue.remove(j)
                 return [j]
         return None
+
+    def _take_small(self, room):
+        """Small queued jobs (FIFO, coalesced) that fit in `room`, or None."""
+        batch, pts, fp = [], 0, 0
+        for j in self.queue:
+            if j.n > self.small:
+                continue
+            if len(batch) >= self.batch_max_jobs or pts + j.n > self.batch_max_points or fp + j.footprint > room:
+                break
+            batch.append(j)
+            pts += j.n
+            fp += j.footprint
+        for j in batch:
+            self.queue.remove(j)
+        return batch or None
 
     def _worker(self, slot: int):
         while True:
@@ -243,7 +267,9 @@ class Server:
                 if work is None:
                     return
                 fp = sum(j.footprint for j in work)
+                nlarge = sum(1 for j in work if j.n > self.large)
                 self.in_use += fp
+                self.large_inflight += nlarge
             t0 = time.perf_counter()
             for j in work:
                 j.t_start = t0
@@ -256,6 +282,7 @@ class Server:
             t1 = time.perf_counter()
             with self.cv:
                 self.in_use -= fp
+                self.large_inflight -= nlarge
                 for k, j in enumerate(work):
                     j.t_done = t1
                     self.done.append(j)

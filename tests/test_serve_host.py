@@ -24,15 +24,21 @@ class FakeBackend:
     def footprint(self, n, d):
         return n * 10
 
+    large_at = 2000  # jobs above this many points count as large here
+
     def run(self, slot, jobs):
         fp = sum(j.footprint for j in jobs)
+        nl = sum(1 for j in jobs if j.n > self.large_at)
         with self.lock:
             self.in_use += fp
             self.max_in_use = max(self.max_in_use, self.in_use)
             self.calls.append([j.n for j in jobs])
+            self.large_now = getattr(self, "large_now", 0) + nl
+            self.max_large_now = max(getattr(self, "max_large_now", 0), self.large_now)
         time.sleep(0.002 + 1e-7 * sum(j.n for j in jobs))
         with self.lock:
             self.in_use -= fp
+            self.large_now -= nl
         if self.fail_on is not None and any(j.n == self.fail_on for j in jobs):
             raise RuntimeError("planted failure")
         return [(j.X[:, 0].copy(), j.X[:, 0] % 2 == 0) for j in jobs]
@@ -96,3 +102,19 @@ def test_close_drains_the_queue_and_stats():
     assert st["jobs"] == 40 and st["p99_ms"] >= st["p50_ms"] >= 0
     with pytest.raises(RuntimeError):
         srv.submit(job(10, 1), 1, 1)
+
+
+def test_large_jobs_never_overlap_and_small_ones_keep_flowing():
+    fb = FakeBackend()
+    with Server(slots=3, hbm_budget=10**9, small_job_points=1000, large_job_points=FakeBackend.large_at,
+                max_large=1, backend=fb) as srv:
+        big = [srv.submit(job(200_000, 5000 + t), 1, 1) for t in range(4)]
+        small = [srv.submit(job(100, t), 1, 1) for t in range(30)]
+        for t, f in enumerate(small):
+            assert (f.result(timeout=30)[0] == t).all()
+        small_done_at = time.perf_counter()
+        for f in big:
+            f.result(timeout=30)
+        big_done_at = time.perf_counter()
+    assert fb.max_large_now == 1
+    assert small_done_at < big_done_at, "small jobs waited behind the large ones"
