@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # source it was taken on: a changed kernel reports no traffic until it is
 # captured again.
 ONESWEEP_TRAFFIC = {
-    "7585df61684318c5": {"workload": "ss3d_10m", "key_class": 0, "bytes": 127.8e6},
+    "a4f9489c670e4c58": {"workload": "ss3d_10m", "key_class": 0, "bytes": 128.0e6},
 }
 
 
