@@ -46,6 +46,11 @@ struct Params {
     long long eps2;   // squared radius (clamped below 2^62)
     int minpts;
     long long s;      // integer cell side: largest s with d*(s-1)^2 <= eps2
+    // floor(x / s) for 32-bit x as the high word of s_mul * x (s_mul =
+    // floor((2^64 - 1) / s) + 1; exact for every 32-bit x and 2 <= s < 2^32:
+    // Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019);
+    // 0 when s = 1
+    unsigned long long s_mul;
     long long r;      // largest |delta| per dimension whose gap alone is <= eps
     int key_bits;     // total bits of the packed grid key
     int key_words;    // 1 or 2 64-bit words

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ in
     int kk = -1;  // instance index of the accumulated values
     const int* X = nullptr;
     int d = 0;
-    for (long long i = beg + lane_id(); i < end; i += 32) {
+    long long i = beg + lane_id();
+    while (i < end) {
         if (cur.seek(f, i)) {
             if (kk >= 0) bounds_flush(ins[kk], mn, mx);
 #pragma unroll
@@ -185,14 +186,29 @@ __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ in
             X = ins[kk].X;
             d = ins[kk].p.d;
         }
-        const int* row = X + (i - cur.lo) * d;
+        // the lane's points of this instance, four rows in flight at a time
+        const long long stop = min(end, cur.hi);
+        for (; i < stop; i += 4 * 32) {
+            int v[4][kMaxD];
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j)
-            if (j < d) {
-                const int v = __ldg(row + j);
-                mn[j] = min(mn[j], v);
-                mx[j] = max(mx[j], v);
+            for (int u = 0; u < 4; ++u) {
+                const long long q = i + u * 32;
+                const int* row = X + (q - cur.lo) * d;
+#pragma unroll
+                for (int j = 0; j < kMaxD; ++j) v[u][j] = (q < stop && j < d) ? __ldg(row + j) : 0;
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * 32 < stop) {
+#pragma unroll
+                    for (int j = 0; j < kMaxD; ++j)
+                        if (j < d) {
+                            mn[j] = min(mn[j], v[u][j]);
+                            mx[j] = max(mx[j], v[u][j]);
+                        }
+                }
+        }
+        if (i >= stop && stop < end) i = stop + ((i - stop) & 31);
     }
     const unsigned uniform = __match_any_sync(kFull, kk);
     if (uniform == kFull) {

@@ -51,63 +51,74 @@ cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cuda
 }
 
 // Core points of each grid packed contiguously (s_i of Section 4.3.1), one
-// thread per point in grid order, and the bounding box of each grid's core
-// points: a warp's lanes hold consecutive points, so the lanes of one grid
-// (of one instance) form a run; the run is min/max-reduced with shuffles and
-// its first lane applies one atomic per dimension.
+// thread per point in grid order (a point of a full grid keeps its offset in
+// the grid; in other grids it counts the core points before it), and the
+// bounding box of each grid's core points by atomics: a warp whose 32 points
+// are all core points of one grid (the common case in dense data) reduces
+// them first and applies one atomic per bound.
 __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     const int lane = lane_id();
-    const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (total + 31) & ~31ll;
     FlatCursor cur;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_round;
+         i += (long long)gridDim.x * blockDim.x) {
         const bool valid = i < total;
-        if (valid) cur.seek(f, i);
-        const int k = valid ? cur.k : 0;
-        const Inst* I = ins + (valid ? f.idx[k] : 0);
-        const long long q = valid ? i - cur.lo : 0;
-        const int c = valid ? I->pt_cell[q] : -1;
-        const long long key = valid ? (((long long)k << 32) | (unsigned)c) : (-1ll - lane);
-        const bool core = valid && I->core_s[q];
-        const int d = valid ? I->p.d : 0, dp = valid ? I->p.dp : 0;
-        int x[kMaxD];
+        int inst = -1, c = -1;
+        bool core = false;
+        const Inst* I = nullptr;
+        int x[kMaxD] = {};
+        if (valid) {
+            cur.seek(f, i);
+            inst = f.idx[cur.k];
+            I = ins + inst;
+            const long long q = i - cur.lo;
+            core = I->core_s[q] != 0;
+            if (core) {
+                const int dp = I->p.dp;
+                c = I->pt_cell[q];
+                const int b = I->cell_start[c];
+                long long pos;
+                if (I->cell_start[c + 1] - b >= I->p.minpts) {
+                    pos = I->core_start[c] + (q - b);
+                } else {
+                    int r = 0;
+                    for (long long u = b; u < q; ++u) r += I->core_s[u];
+                    pos = I->core_start[c] + r;
+                }
+                if (dp == 4) {
+                    const int4 v = *reinterpret_cast<const int4*>(I->Xs + q * 4);
+                    *reinterpret_cast<int4*>(I->Xc + pos * 4) = v;
+                    x[0] = v.x;
+                    x[1] = v.y;
+                    x[2] = v.z;
+                    x[3] = v.w;
+                } else {
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j) x[j] = (core && j < dp) ? I->Xs[q * dp + j] : 0;
-        if (core) {
-            const int b = I->cell_start[c];
-            long long pos;
-            if (I->cell_start[c + 1] - b >= I->p.minpts) {
-                pos = I->core_start[c] + (q - b);
-            } else {
-                int r = 0;
-                for (long long u = b; u < q; ++u) r += I->core_s[u];
-                pos = I->core_start[c] + r;
-            }
-#pragma unroll
-            for (int j = 0; j < kMaxD; ++j)
-                if (j < dp) I->Xc[pos * dp + j] = x[j];
-        }
-        const unsigned peers = __match_any_sync(kFull, key);
-        const bool leader = lane == __ffs(peers) - 1;
-        const bool any_core = (__ballot_sync(kFull, core) & peers) != 0;
-        const int dmax = __reduce_max_sync(kFull, (unsigned)d);
-#pragma unroll
-        for (int j = 0; j < kMaxD; ++j) {
-            if (j >= dmax) break;
-            int lo = core ? x[j] : 0x7fffffff, hi = core ? x[j] : (int)0x80000000;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int olo = __shfl_down_sync(kFull, lo, o);
-                const int ohi = __shfl_down_sync(kFull, hi, o);
-                const long long ok = __shfl_down_sync(kFull, key, o);
-                if (lane + o < 32 && ok == key) {
-                    lo = min(lo, olo);
-                    hi = max(hi, ohi);
+                    for (int j = 0; j < kMaxD; ++j)
+                        if (j < dp) {
+                            x[j] = I->Xs[q * dp + j];
+                            I->Xc[pos * dp + j] = x[j];
+                        }
                 }
             }
-            if (leader && any_core && j < d) {
-                atomicMin(I->bbox + (long long)c * 2 * d + j, lo);
-                atomicMax(I->bbox + (long long)c * 2 * d + d + j, hi);
+        }
+        const int c0 = __shfl_sync(kFull, c, 0), i0 = __shfl_sync(kFull, inst, 0);
+        if (__all_sync(kFull, core && c == c0 && inst == i0)) {
+            const int d = I->p.d;
+#pragma unroll
+            for (int j = 0; j < kMaxD; ++j) {
+                if (j >= d) break;
+                const int lo = __reduce_min_sync(kFull, x[j]), hi = __reduce_max_sync(kFull, x[j]);
+                if (lane == 0) {
+                    atomicMin(I->bbox + (long long)c * 2 * d + j, lo);
+                    atomicMax(I->bbox + (long long)c * 2 * d + d + j, hi);
+                }
+            }
+        } else if (core) {
+            const int d = I->p.d;
+            for (int j = 0; j < d; ++j) {
+                atomicMin(I->bbox + (long long)c * 2 * d + j, x[j]);
+                atomicMax(I->bbox + (long long)c * 2 * d + d + j, x[j]);
             }
         }
     }
@@ -119,6 +130,8 @@ cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, cudaStr
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
+
+
 
 // -------------------------------------------------------- candidate pairs
 // Pairs (i, j) of core grids with j in Nei(i) and j > i, in two waves:

@@ -376,6 +376,7 @@ gd_status Run::go() {
         p.eps2 = g.eps2 > cap ? cap : g.eps2;
         p.minpts = g.minpts;
         p.s = 1 + (long long)isqrt_u64((unsigned long long)p.eps2 / (unsigned long long)g.d);
+        p.s_mul = p.s >= 2 ? ~0ull / (unsigned long long)p.s + 1 : 0;
         p.r = p.eps2 == 0 ? 0 : 1 + ((long long)isqrt_u64((unsigned long long)p.eps2) - 1) / p.s;
         if (p.r > kMaxR) return fail(GD_ERANGE, "stencil radius above its bound", k);
         h.dev.X = g.X;

@@ -93,11 +93,12 @@ void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** hist, 
 
 // ------------------------------------------------------------- quantise
 
-__device__ __forceinline__ unsigned identifier(int x, int mn, long long s) {
+__device__ __forceinline__ unsigned identifier(int x, int mn, unsigned long long s_mul) {
     // (x - mn) fits in 32 unsigned bits; an identifier is at most 2^31 - 1
-    // because d * range^2 < 2^62 is checked before this runs.
-    const unsigned long long diff = (unsigned)(x - mn);
-    return (unsigned)(diff / (unsigned long long)s);
+    // because d * range^2 < 2^62 is checked before this runs.  The division
+    // by the cell side is a multiply-high (Params::s_mul).
+    const unsigned diff = (unsigned)(x - mn);
+    return s_mul ? (unsigned)__umul64hi(s_mul, (unsigned long long)diff) : diff;
 }
 
 __device__ __forceinline__ void pack_key(unsigned long long& k, unsigned v, int sh) {
@@ -117,8 +118,8 @@ __device__ __forceinline__ void zero_key(Key2& k) { k.lo = k.hi = 0; }
 
 // One block per tile of kQuantTile points of one instance: keys, values
 // (input index) and the tile's histogram of every digit position, added to
-// the instance's histograms.  Runs of equal digits inside a warp are counted
-// once (warp match), which keeps shared-memory atomics cheap on clustered data.
+// the instance's histograms.  Runs of equal digits over consecutive lanes are
+// counted once, which keeps shared-memory atomics cheap on clustered data.
 template <typename K, bool PACKED>
 __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restrict__ ins, Flat f) {
     extern __shared__ int sh_hist[];  // [passes][1 << bits]
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restri
             const int* row = I.X + i * d;
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
-                if (j < d) pack_key(key, identifier(__ldg(row + j), p.mn[j], p.s), p.shift[j]);
+                if (j < d) pack_key(key, identifier(__ldg(row + j), p.mn[j], p.s_mul), p.shift[j]);
             if constexpr (PACKED) {
                 // key above the point index: one word carries both
                 keys[i] = (unsigned long long)key << p.pack_bits | (unsigned long long)i;
@@ -153,9 +154,17 @@ __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restri
             }
         }
         for (int ps = 0; ps < passes; ++ps) {
+            // runs of equal digits over consecutive lanes (clustered inputs
+            // give long runs) are added once, by their first lane
             const unsigned dg = valid ? SortKey<K>::digit(key, ps * bits, mask) : (unsigned)R + lane;
-            const unsigned peers = __match_any_sync(kFull, dg);
-            if (valid && lane == (int)(__ffs(peers) - 1)) atomicAdd(&sh_hist[ps * R + dg], __popc(peers));
+            const unsigned prev = __shfl_up_sync(kFull, dg, 1);
+            const bool start = lane == 0 || dg != prev;
+            const unsigned starts = __ballot_sync(kFull, start);
+            if (valid && start) {
+                const unsigned above = starts & ~((2u << lane) - 1u);
+                const int next = above ? __ffs(above) - 1 : 32;
+                atomicAdd(&sh_hist[ps * R + dg], next - lane);
+            }
         }
     }
     __syncthreads();
