@@ -80,59 +80,93 @@ cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cud
     return cudaGetLastError();
 }
 
-// One thread per point in grid order; writes labels and core flags in input
-// order.  Non-core points scan their neighbour grids' core points, skipping
-// grids whose cluster id cannot improve the best found so far or whose core
-// box is farther than eps.
+// The label of non-core point q (grid c): the smallest cluster id among the
+// core points within eps, scanning the neighbour grids' core points and
+// skipping grids whose cluster id cannot improve the best found so far or
+// whose core box is farther than eps; -1 (noise) if there is none.
+template <int D>
+__device__ __forceinline__ int border_label(const Inst& I, long long q, int c) {
+    constexpr int DP = Padded<D>::value;
+    int x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = I.Xs[q * DP + j];
+    const long long eps2 = I.p.eps2;
+    int best = INT_MAX;
+    for (int t = I.nbr_start[c]; t < I.nbr_start[c + 1]; ++t) {
+        const int c2 = I.nbr[t];
+        const int id = I.cell_cid[c2];
+        if (id < 0 || id >= best) continue;
+        const int* bb = I.bbox + (long long)c2 * 2 * D;
+        long long g2 = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            long long g = 0;
+            if (bb[j] > x[j]) g = (long long)bb[j] - x[j];
+            else if (x[j] > bb[D + j]) g = (long long)x[j] - bb[D + j];
+            g2 += g * g;
+        }
+        if (g2 > eps2) continue;
+        for (int u = I.core_start[c2]; u < I.core_start[c2 + 1]; ++u) {
+            int y[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) y[j] = I.Xc[(long long)u * DP + j];
+            if (sqdist<D>(x, y) <= eps2) {
+                best = id;
+                break;
+            }
+        }
+    }
+    return best == INT_MAX ? -1 : best;
+}
+
+// Labels and core flags in input order (Alg. 6 step 4).  Warps take chunks
+// of kLabelChunk consecutive points of the flat space (grid order) in turn,
+// lanes on consecutive points, four points per lane in flight: a core point
+// takes its grid's cluster id, a non-core point searches its neighbour grids
+// (border_label).  Small chunks spread regions of costly (non-core) points
+// over many warps.
+constexpr int kLabelChunk = 128;
+
 template <int D>
 __global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
-    constexpr int DP = Padded<D>::value;
+    constexpr int U = 4;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     FlatCursor cur;
-    GD_FOR_FLAT(i, total) {
-        cur.seek(f, i);
-        const int k = cur.k;
-        const Inst& I = ins[f.idx[k]];
-        const long long q = i - cur.lo;
-        const int c = I.pt_cell[q];
-        const unsigned char core = I.core_s[q];
-        int lab;
-        if (core) {
-            lab = I.cell_cid[c];
-        } else {
-            int x[D];
+    for (long long beg = wid * kLabelChunk; beg < total; beg += nwarps * kLabelChunk) {
+        const long long end = min(total, beg + kLabelChunk);
+        long long i = beg + lane_id();
+        while (i < end) {
+            cur.seek(f, i);
+            const Inst& I = ins[f.idx[cur.k]];
+            const int* perm = perm_of(I);
+            const long long stop = min(end, cur.hi);
+            for (; i < stop; i += 32 * U) {
+                int c[U], o[U];
+                unsigned char core[U];
 #pragma unroll
-            for (int j = 0; j < D; ++j) x[j] = I.Xs[q * DP + j];
-            const long long eps2 = I.p.eps2;
-            int best = INT_MAX;
-            for (int t = I.nbr_start[c]; t < I.nbr_start[c + 1]; ++t) {
-                const int c2 = I.nbr[t];
-                const int id = I.cell_cid[c2];
-                if (id < 0 || id >= best) continue;
-                const int* bb = I.bbox + (long long)c2 * 2 * D;
-                long long g2 = 0;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    long long g = 0;
-                    if (bb[j] > x[j]) g = (long long)bb[j] - x[j];
-                    else if (x[j] > bb[D + j]) g = (long long)x[j] - bb[D + j];
-                    g2 += g * g;
+                for (int u = 0; u < U; ++u) {
+                    const long long q = i - cur.lo + 32 * u;
+                    const bool v = i + 32 * u < stop;
+                    c[u] = v ? I.pt_cell[q] : 0;
+                    core[u] = v ? I.core_s[q] : 0;
+                    o[u] = v ? perm[q] : -1;
                 }
-                if (g2 > eps2) continue;
-                for (int u = I.core_start[c2]; u < I.core_start[c2 + 1]; ++u) {
-                    int y[D];
+                int lab[U];
 #pragma unroll
-                    for (int j = 0; j < D; ++j) y[j] = I.Xc[(long long)u * DP + j];
-                    if (sqdist<D>(x, y) <= eps2) {
-                        best = id;
-                        break;
+                for (int u = 0; u < U; ++u) lab[u] = (o[u] >= 0 && core[u]) ? I.cell_cid[c[u]] : -1;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (o[u] >= 0 && !core[u]) lab[u] = border_label<D>(I, i - cur.lo + 32 * u, c[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (o[u] >= 0) {
+                        I.labels[o[u]] = lab[u];
+                        if (I.is_core) I.is_core[o[u]] = core[u];
                     }
-                }
             }
-            lab = best == INT_MAX ? -1 : best;
+            if (i >= stop && stop < end) i = stop + ((i - stop) & 31);
         }
-        const int o = perm_of(I)[q];
-        I.labels[o] = lab;
-        if (I.is_core) I.is_core[o] = core;
     }
 }
 
