@@ -305,7 +305,8 @@ cudaError_t zero_ranges(const ZeroRange* r, int n_ranges, long long total, cudaS
 cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st);
 
 // Grid construction (grid.cu).
-cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+// Over the instances of dimension d.
+cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
 constexpr int kCompactTile = 1024;
 cudaError_t launch_compact_count(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);
 cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);

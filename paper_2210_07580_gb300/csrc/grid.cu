@@ -151,61 +151,62 @@ cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long lo
 // at instance boundaries inside the chunk).  At the end, a warp whose lanes
 // all hold the same instance reduces with shuffles and applies one atomic per
 // dimension.  The small blocks' mnmx must hold INT_MAX / INT_MIN first.
+template <int D>
 __device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const int* mx) {
-    for (int j = 0; j < I.p.d; ++j) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
         atomicMin(I.small + kSmMnmx + j, mn[j]);
         atomicMax(I.small + kSmMnmx + kMaxD + j, mx[j]);
     }
 }
 
+// Over the instances of dimension D.
+template <int D>
 __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     const long long per = (((total + nwarps - 1) / nwarps) + 31) & ~31ll;
     const long long beg = wid * per, end = min(total, beg + per);
-    int mn[kMaxD], mx[kMaxD];
+    int mn[D], mx[D];
 #pragma unroll
-    for (int j = 0; j < kMaxD; ++j) {
+    for (int j = 0; j < D; ++j) {
         mn[j] = INT_MAX;
         mx[j] = INT_MIN;
     }
     FlatCursor cur;
     int kk = -1;  // instance index of the accumulated values
     const int* X = nullptr;
-    int d = 0;
     long long i = beg + lane_id();
     while (i < end) {
         if (cur.seek(f, i)) {
-            if (kk >= 0) bounds_flush(ins[kk], mn, mx);
+            if (kk >= 0) bounds_flush<D>(ins[kk], mn, mx);
 #pragma unroll
-            for (int j = 0; j < kMaxD; ++j) {
+            for (int j = 0; j < D; ++j) {
                 mn[j] = INT_MAX;
                 mx[j] = INT_MIN;
             }
             kk = f.idx[cur.k];
             X = ins[kk].X;
-            d = ins[kk].p.d;
         }
         // the lane's points of this instance, four rows in flight at a time
         const long long stop = min(end, cur.hi);
         for (; i < stop; i += 4 * 32) {
-            int v[4][kMaxD];
+            int v[4][D];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const long long q = i + u * 32;
-                const int* row = X + (q - cur.lo) * d;
+                const int* row = X + (q - cur.lo) * D;
 #pragma unroll
-                for (int j = 0; j < kMaxD; ++j) v[u][j] = (q < stop && j < d) ? __ldg(row + j) : 0;
+                for (int j = 0; j < D; ++j) v[u][j] = q < stop ? __ldg(row + j) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (i + u * 32 < stop) {
 #pragma unroll
-                    for (int j = 0; j < kMaxD; ++j)
-                        if (j < d) {
-                            mn[j] = min(mn[j], v[u][j]);
-                            mx[j] = max(mx[j], v[u][j]);
-                        }
+                    for (int j = 0; j < D; ++j) {
+                        mn[j] = min(mn[j], v[u][j]);
+                        mx[j] = max(mx[j], v[u][j]);
+                    }
                 }
         }
         if (i >= stop && stop < end) i = stop + ((i - stop) & 31);
@@ -214,22 +215,27 @@ __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ in
     if (uniform == kFull) {
         if (kk < 0) return;
 #pragma unroll
-        for (int j = 0; j < kMaxD; ++j)
-            for (int o = 16; o > 0; o >>= 1) {
-                mn[j] = min(mn[j], __shfl_xor_sync(kFull, mn[j], o));
-                mx[j] = max(mx[j], __shfl_xor_sync(kFull, mx[j], o));
-            }
-        if (lane_id() == 0) bounds_flush(ins[kk], mn, mx);
+        for (int j = 0; j < D; ++j) {
+            mn[j] = __reduce_min_sync(kFull, mn[j]);
+            mx[j] = __reduce_max_sync(kFull, mx[j]);
+        }
+        if (lane_id() == 0) bounds_flush<D>(ins[kk], mn, mx);
     } else if (kk >= 0) {
-        bounds_flush(ins[kk], mn, mx);
+        bounds_flush<D>(ins[kk], mn, mx);
     }
 }
 
-cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
+cudaError_t launch_bounds(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    bounds_kernel<<<(int)blocks, 256, 0, st>>>(ins, pts, total);
+    switch (d) {
+#define GD_BK(DD) \
+    case DD: bounds_kernel<DD><<<(int)blocks, 256, 0, st>>>(ins, pts, total); break;
+        GD_BK(1) GD_BK(2) GD_BK(3) GD_BK(4) GD_BK(5) GD_BK(6) GD_BK(7) GD_BK(8)
+#undef GD_BK
+        default: return cudaErrorInvalidValue;
+    }
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

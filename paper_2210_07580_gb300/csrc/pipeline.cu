@@ -406,11 +406,18 @@ gd_status Run::go() {
     // --------------------------------------------- phase 1: bounds (sync 1)
     mark(0);
     RUN_TRY(begin_desc());
-    const Flat pts0 = flat(members, K, n_of, &tot);
+    Flat pts_d[kMaxD];
+    long long tot_d[kMaxD] = {};
+    for (int d = 1; d <= kMaxD; ++d) {
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (in[k].d == d) members2[m++] = k;
+        pts_d[d - 1] = flat(members2, m, n_of, &tot_d[d - 1]);
+    }
     RUN_TRY(upload_desc());
     RUN_TRY(phase(0, [&]() -> gd_status {
         RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
-        RUN_CUDA(launch_bounds(dins, pts0, total_pts, st), "bounds");
+        for (int d = 1; d <= kMaxD; ++d) RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
         return GD_OK;
     }));
     RUN_TRY(readback());
