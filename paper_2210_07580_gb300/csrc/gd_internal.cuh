@@ -122,10 +122,9 @@ struct Inst {
     int* cid_root;
     int* cell_cid;
     int* bcnt;  // compaction: per-tile grid starts (scanned)
-    int* sort_hist;
-    int* sort_dstart;
-    int* sort_counters;
-    unsigned long long* sort_status;
+    int* sort_tcnt;    // [tiles][R] per-tile digit counts, then offsets over the tiles
+    int* sort_dtot;    // [R] digit totals of the current pass
+    int* sort_dstart;  // [R] digit starts of the current pass
 };
 
 // Flat item space over the instances of a launch: item i belongs to instance
@@ -318,29 +317,24 @@ struct SortPlan {
     int passes;   // digit positions
     int bits;     // bits per digit (<= 9)
     int buckets;  // 1 << bits
-    int tile;     // keys per onesweep tile
+    int tile;     // keys per sort tile
     int tiles;
 };
 SortPlan sort_plan(int n, int key_words, int key_bits);
 // ints of workspace for one instance's sort (histograms, tile counters,
 // look-back status); layout in sort.cu.
 size_t sort_tmp_ints(int n, int key_words, int key_bits);
-void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** hist, int** dstart, int** counters,
-                     unsigned long long** status, size_t* zero_ints);
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** dtot, int** dstart);
 constexpr int kQuantTile = 4096;  // points per quantise block
-// keys, values and digit histograms; `tiles` is the flat space of quantise
-// tiles (kQuantTile points) of instances with the given key width.
-// Histograms, counters and status must be zeroed first.
-cudaError_t launch_quantise_hist(const Inst* ins, Flat tiles, long long total, int key_class, int max_hist_ints,
-                                 cudaStream_t st);
-cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st);
-// One onesweep pass over the tiles of the instances in `tiles` (each with
-// more than `pass` passes and the given key width).
-// Sets the onesweep kernels' shared-memory limit on the current device (once
+// Keys (and, unpacked, index values) of every point, over quantisation tiles.
+cudaError_t launch_quantise(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);
+// Sets the downsweep kernels' shared-memory limit on the current device (once
 // per device; before any stream capture).
-cudaError_t prepare_onesweep();
-cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                            int* flat_counter, cudaStream_t st);
+cudaError_t prepare_sort();
+// One radix-sort pass (upsweep, tile scan, digit starts, downsweep) of digit
+// position `pass` over the sort tiles of the instances of one key class.
+cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
+                             cudaStream_t st);
 
 // Grid-tree levels and neighbour walk (neighbors.cu).
 cudaError_t launch_point_boxes(const Inst* ins, Flat cells, long long total, cudaStream_t st);

@@ -138,21 +138,10 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     I.cell_cid = (int*)take(N * 4);
     I.bcnt = (int*)take(((N + kCompactTile - 1) / kCompactTile + 1) * 4);
     int* sort_base = (int*)take(sort_tmp_ints(n, key_words, key_bits) * 4);
-    if (base) {
-        size_t zero_ints = 0;
-        sort_tmp_layout(sort_base, n, key_words, key_bits, &I.sort_hist, &I.sort_dstart, &I.sort_counters,
-                        &I.sort_status, &zero_ints);
-    }
+    if (base) sort_tmp_layout(sort_base, n, key_words, key_bits, &I.sort_tcnt, &I.sort_dtot, &I.sort_dstart);
     return align256(off) + 256;
 }
 
-size_t sort_zero_ints(int n, int key_words, int key_bits) {
-    int *h, *ds, *c;
-    unsigned long long* s;
-    size_t z = 0;
-    sort_tmp_layout(nullptr, n, key_words, key_bits, &h, &ds, &c, &s, &z);
-    return z;
-}
 
 struct Run {
     MemProvider& mem;
@@ -423,7 +412,7 @@ gd_status Run::go() {
     RUN_TRY(readback());
 
     // ------------------------- phase 2: keys, sort, compaction (sync 2)
-    int max_passes = 0, max_buckets = 1, max_hist = 1;
+    int max_buckets = 1;
     size_t arena = 0;
     for (int k = 0; k < K; ++k) {
         HI& h = hi[k];
@@ -459,9 +448,7 @@ gd_status Run::go() {
         h.dev.tiles = sp.tiles;
         h.q_tiles = (p.n + kQuantTile - 1) / kQuantTile;
         h.c_tiles = (p.n + kCompactTile - 1) / kCompactTile;
-        if (sp.passes > max_passes) max_passes = sp.passes;
         if (sp.buckets > max_buckets) max_buckets = sp.buckets;
-        if (sp.passes * sp.buckets > max_hist) max_hist = sp.passes * sp.buckets;
         h.arena_off = arena;
         h.arena_bytes = carve(h.dev, nullptr, p.n, p.d, p.key_words, p.key_bits);
         arena += h.arena_bytes;
@@ -475,21 +462,6 @@ gd_status Run::go() {
 
     RUN_TRY(begin_desc());
     const Flat pts1 = flat(members, K, n_of, &tot);
-    const size_t zr_at = b.take(sizeof(ZeroRange) * K);
-    long long zr_total = 0;
-    {
-        ZeroRange* zr = reinterpret_cast<ZeroRange*>(b.host + zr_at);
-        for (int k = 0; k < K; ++k) {
-            const Params& p = hi[k].dev.p;
-            const long long z = (long long)sort_zero_ints(p.n, p.key_words, p.key_bits);
-            if (!b.overflow) zr[k] = ZeroRange{hi[k].dev.sort_hist, z, zr_total};
-            zr_total += z;
-        }
-    }
-    const ZeroRange* zr_dev = reinterpret_cast<const ZeroRange*>(b.dev + zr_at);
-    const size_t counters_at = b.take(sizeof(int) * 64);
-    int* counters = reinterpret_cast<int*>(b.dev + counters_at);
-    if (!b.overflow) memset(b.host + counters_at, 0, sizeof(int) * 64);
     // one group per key class (packed 64-bit, 64-bit + values, 128-bit + values)
     Flat qflat[3], cflat[3];
     long long qtot[3] = {0, 0, 0}, ctot[3] = {0, 0, 0};
@@ -522,19 +494,15 @@ gd_status Run::go() {
         &cseg_tiles);
     const int* idx = idx_all();
     RUN_TRY(upload_desc());
-    RUN_CUDA(prepare_onesweep(), "sort set-up");
+    RUN_CUDA(prepare_sort(), "sort set-up");
 
     RUN_TRY(phase(1, [&]() -> gd_status {
     mark(1);
-    RUN_CUDA(zero_ranges(zr_dev, K, zr_total, st), "clear sort state");
-    for (int w = 0; w < 3; ++w)
-        RUN_CUDA(launch_quantise_hist(dins, qflat[w], qtot[w], w, max_hist, st), "quantise");
-    RUN_CUDA(launch_digit_scan(dins, idx, K, max_passes, st), "digit scan");
+    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_quantise(dins, qflat[w], qtot[w], w, st), "quantise");
     mark(2);
     for (int w = 0; w < 3; ++w)
         for (int ps = 0; ps < gpasses[w]; ++ps)
-            RUN_CUDA(launch_onesweep(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, counters + w * 16 + ps, st),
-                     "sort pass");
+            RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st), "sort pass");
     mark(3);
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w, st), "compact count");
     RUN_TRY(scan(cseg, K, cseg_tiles));

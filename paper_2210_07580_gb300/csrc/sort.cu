@@ -3,23 +3,17 @@
 // The paper sorts by counting sort one dimension at a time; here the
 // identifiers are packed into one 64- or 128-bit key (dimension 1 most
 // significant, so key order is the lexicographic order of Alg. 1) and sorted
-// by digits of up to 9 bits:
-//   1. quantise_hist: computes every key and, in the same pass, the
-//      histogram of every digit position;
-//   2. digit_scan: exclusive scan of each digit position's histogram;
-//   3. one onesweep pass per digit position: each block takes the next tile
-//      (dynamic tile ids), ranks its keys stably in shared memory, publishes
-//      its per-digit counts and finds the counts of all earlier tiles of its
-//      instance by a decoupled look-back, then writes each digit run out
-//      contiguously.
-// A pass reads and writes every key and value once.  When the key and the
-// point index fit in 64 bits together, the index rides in the low bits of the
-// key (no separate values): a pass then moves 16 bytes per point, not 24,
-// and since the passes are stable and look only at key digits, the order is
-// the same.  Look-back waits are
-// bounded: a block only ever waits for tiles handed out before its own (tile
-// ids are taken in order from one counter over the whole batch), and gives
-// up with kDevTimeout after a fixed number of polls.
+// by digits of up to 9 bits.  Quantisation computes the keys; then every
+// digit position is one pass of three steps over tiles of consecutive keys:
+//   1. upsweep: each tile's digit histogram;
+//   2. tile scan: per digit, exclusive offsets over the tiles and the digit's
+//      total; digit starts: exclusive scan of the totals;
+//   3. downsweep: each tile ranks its keys stably in shared memory and writes
+//      each digit run to its start plus the tile's offset.
+// No tile waits for another.  When the key and the point index fit in 64
+// bits together, the index rides in the low bits of the key (no separate
+// values): a pass then moves 8 bytes per point each way, not 12, and since
+// the passes are stable and look only at key digits, the order is the same.
 #include <atomic>
 
 #include "gd_internal.cuh"
@@ -30,9 +24,6 @@ constexpr int kMaxDigitBits = 9;
 constexpr int kMaxBuckets = 1 << kMaxDigitBits;
 constexpr int kOsBlock = 256;
 constexpr int kOsWarps = kOsBlock / 32;
-constexpr unsigned kFlagAgg = 1u, kFlagInc = 2u;
-constexpr int kMaxPolls = 1 << 22;
-constexpr int kLookback = 8;
 
 template <typename K> struct SortKey;
 template <> struct SortKey<unsigned long long> {
@@ -67,28 +58,19 @@ SortPlan sort_plan(int n, int key_words, int key_bits) {
     return sp;
 }
 
-// Layout of one instance's sort workspace (ints): hist [P][R],
-// dstart [P][R], tile counters [P], status [P][tiles][R] (64-bit words).
-// Everything but dstart must be zero before quantise_hist runs.
+// One instance's sort workspace (ints): per-tile digit counts (then offsets)
+// [tiles][R], digit totals [R], digit starts [R].  Nothing needs clearing:
+// every pass writes all of it before reading it.
 size_t sort_tmp_ints(int n, int key_words, int key_bits) {
     const SortPlan sp = sort_plan(n, key_words, key_bits);
-    const size_t pr = (size_t)sp.passes * sp.buckets;
-    return 2 * pr + (size_t)sp.passes + 8 + 2 * (size_t)sp.passes * sp.tiles * sp.buckets + 64;
+    return (size_t)sp.tiles * sp.buckets + 2 * (size_t)sp.buckets + 64;
 }
 
-void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** hist, int** dstart, int** counters,
-                     unsigned long long** status, size_t* zero_ints) {
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** dtot, int** dstart) {
     const SortPlan sp = sort_plan(n, key_words, key_bits);
-    const size_t pr = (size_t)sp.passes * sp.buckets;
-    // hist, counters and status first (one region to clear), dstart last
-    *hist = base;
-    *counters = base + pr;
-    size_t off = pr + sp.passes + 8;
-    off = (off + 1) & ~(size_t)1;  // 8-byte alignment (base is 256-byte aligned)
-    *status = reinterpret_cast<unsigned long long*>(base + off);
-    off += 2 * (size_t)sp.passes * sp.tiles * sp.buckets;
-    *zero_ints = off;
-    *dstart = base + off;
+    *tcnt = base;
+    *dtot = base + (size_t)sp.tiles * sp.buckets;
+    *dstart = *dtot + sp.buckets;
 }
 
 // ------------------------------------------------------------- quantise
@@ -116,24 +98,27 @@ __device__ __forceinline__ void pack_key(Key2& k, unsigned v, int sh) {
 __device__ __forceinline__ void zero_key(unsigned long long& k) { k = 0; }
 __device__ __forceinline__ void zero_key(Key2& k) { k.lo = k.hi = 0; }
 
-// One block per tile of kQuantTile points of one instance: keys, values
-// (input index) and the tile's histogram of every digit position, added to
-// the instance's histograms.  Runs of equal digits over consecutive lanes are
-// counted once, which keeps shared-memory atomics cheap on clustered data.
+// One block per tile of kQuantTile points of one instance: the keys and (for
+// unpacked keys) the values, the input index.  For 64-bit keys a quantise tile
+// is a sort tile, so the block also writes the tile's histogram of the first
+// digit position (the first pass then needs no upsweep).
 template <typename K, bool PACKED>
-__global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restrict__ ins, Flat f) {
-    extern __shared__ int sh_hist[];  // [passes][1 << bits]
+__global__ void __launch_bounds__(256) quantise_kernel(const Inst* __restrict__ ins, Flat f) {
+    constexpr bool kHist = os_tile<K>() == kQuantTile;
+    __shared__ int hist[kHist ? kMaxBuckets : 1];
     const int k = flat_find(f, blockIdx.x);
     const Inst& I = ins[f.idx[k]];
     const long long tile = blockIdx.x - f.off[k];
-    const int passes = I.passes, bits = I.digit_bits;
-    const int R = 1 << bits;
-    const unsigned mask = (unsigned)R - 1u;
-    for (int i = threadIdx.x; i < passes * R; i += blockDim.x) sh_hist[i] = 0;
-    __syncthreads();
-    const int lane = lane_id();
     const Params& p = I.p;
     const int n = p.n, d = p.d;
+    const int R = 1 << I.digit_bits;
+    const unsigned mask = (unsigned)R - 1u;
+    const bool hist_on = kHist && I.passes > 0;
+    if (hist_on) {
+        for (int b = threadIdx.x; b < R; b += 256) hist[b] = 0;
+        __syncthreads();
+    }
+    const int lane = lane_id();
     K* keys = (K*)I.keyA;
     for (int r = 0; r < kQuantTile; r += 256) {
         const long long i = tile * kQuantTile + r + threadIdx.x;
@@ -153,79 +138,144 @@ __global__ void __launch_bounds__(256) quantise_hist_kernel(const Inst* __restri
                 I.valA[i] = (int)i;
             }
         }
-        for (int ps = 0; ps < passes; ++ps) {
-            // runs of equal digits over consecutive lanes (clustered inputs
-            // give long runs) are added once, by their first lane
-            const unsigned dg = valid ? SortKey<K>::digit(key, ps * bits, mask) : (unsigned)R + lane;
+        if (hist_on) {
+            // runs of equal digits over consecutive lanes are added once
+            const unsigned dg = valid ? SortKey<K>::digit(key, 0, mask) : (unsigned)R + lane;
             const unsigned prev = __shfl_up_sync(kFull, dg, 1);
             const bool start = lane == 0 || dg != prev;
             const unsigned starts = __ballot_sync(kFull, start);
             if (valid && start) {
                 const unsigned above = starts & ~((2u << lane) - 1u);
-                const int next = above ? __ffs(above) - 1 : 32;
-                atomicAdd(&sh_hist[ps * R + dg], next - lane);
+                atomicAdd(&hist[dg], (above ? __ffs(above) - 1 : 32) - lane);
             }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < passes * R; i += blockDim.x)
-        if (sh_hist[i]) atomicAdd(I.sort_hist + i, sh_hist[i]);
+    if (hist_on) {
+        __syncthreads();
+        int* out = I.sort_tcnt + tile * R;
+        for (int b = threadIdx.x; b < R; b += 256) out[b] = hist[b];
+    }
 }
 
-// One block per (instance, pass): exclusive scan of the pass's histogram.
-__global__ void digit_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx) {
+// ------------------------------------------------------------- one pass
+
+template <typename K, bool PACKED> __device__ __forceinline__ int pass_shift(const Inst& I, int pass) {
+    return pass * I.digit_bits + (PACKED ? I.p.pack_bits : 0);
+}
+
+// Upsweep: the digit histogram of each tile (one block per tile) into
+// sort_tcnt[tile][*].  Runs of equal digits over consecutive lanes are added
+// once, which keeps the shared-memory atomics cheap on clustered data.
+template <typename K, bool PACKED>
+__global__ void __launch_bounds__(kOsBlock) upsweep_kernel(const Inst* __restrict__ ins, Flat f, int pass) {
+    constexpr int kTile = os_tile<K>();
+    __shared__ int hist[kMaxBuckets];
+    const int kk = flat_find(f, blockIdx.x);
+    const Inst& I = ins[f.idx[kk]];
+    const int tile = blockIdx.x - (int)f.off[kk];
+    const int R = 1 << I.digit_bits, shift = pass_shift<K, PACKED>(I, pass);
+    const unsigned mask = (unsigned)R - 1u;
+    for (int b = threadIdx.x; b < R; b += kOsBlock) hist[b] = 0;
+    __syncthreads();
+    const K* keys = (const K*)((pass & 1) ? I.keyB : I.keyA);
+    const long long base = (long long)tile * kTile;
+    const int count = (int)min((long long)kTile, (long long)I.p.n - base);
+    const int lane = lane_id();
+    for (int t = threadIdx.x; t < kTile; t += kOsBlock) {
+        const bool valid = t < count;
+        const unsigned dg = valid ? SortKey<K>::digit(keys[base + t], shift, mask) : (unsigned)R + lane;
+        const unsigned prev = __shfl_up_sync(kFull, dg, 1);
+        const bool start = lane == 0 || dg != prev;
+        const unsigned starts = __ballot_sync(kFull, start);
+        if (valid && start) {
+            const unsigned above = starts & ~((2u << lane) - 1u);
+            atomicAdd(&hist[dg], (above ? __ffs(above) - 1 : 32) - lane);
+        }
+    }
+    __syncthreads();
+    int* out = I.sort_tcnt + (long long)tile * R;
+    for (int b = threadIdx.x; b < R; b += kOsBlock) out[b] = hist[b];
+}
+
+// Tile scan: one block per (member instance, digit): exclusive offsets of the
+// digit over the tiles, in place, and the digit's total.  Each thread takes a
+// run of consecutive tiles (its loads are independent), then one block scan
+// joins the runs.
+constexpr int kTileScanBlock = 256;
+constexpr int kTileScanRun = 16;  // tiles per thread held in registers
+
+__global__ void __launch_bounds__(kTileScanBlock)
+    tile_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int m, int pass) {
+    __shared__ int sm[33];
+    const int t = blockIdx.x / kMaxBuckets, dg = blockIdx.x % kMaxBuckets;
+    if (t >= m) return;
+    const Inst& I = ins[idx[t]];
+    const int R = 1 << I.digit_bits;
+    if (pass >= I.passes || dg >= R) return;
+    const int tiles = I.tiles;
+    int* col = I.sort_tcnt + dg;
+    int carry = 0;
+    // chunks of kTileScanBlock * kTileScanRun tiles (one chunk up to 1M keys)
+    for (int c0 = 0; c0 < tiles; c0 += kTileScanBlock * kTileScanRun) {
+        const int r0 = c0 + threadIdx.x * kTileScanRun;
+        int v[kTileScanRun];
+        int sum = 0;
+#pragma unroll
+        for (int u = 0; u < kTileScanRun; ++u) {
+            v[u] = r0 + u < tiles ? col[(long long)(r0 + u) * R] : 0;
+            sum += v[u];
+        }
+        int total;
+        int ex = carry + block_exclusive_scan(sum, sm, &total);
+#pragma unroll
+        for (int u = 0; u < kTileScanRun; ++u)
+            if (r0 + u < tiles) {
+                col[(long long)(r0 + u) * R] = ex;
+                ex += v[u];
+            }
+        carry += total;
+    }
+    if (threadIdx.x == 0) I.sort_dtot[dg] = carry;
+}
+
+// Digit starts: one block per member instance, exclusive scan of the totals.
+__global__ void digit_start_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int pass) {
     __shared__ int sm[33];
     const Inst& I = ins[idx[blockIdx.x]];
-    const int ps = blockIdx.y;
-    if (ps >= I.passes) return;
+    if (pass >= I.passes) return;
     const int R = 1 << I.digit_bits;
     int carry = 0;
     for (int base = 0; base < R; base += blockDim.x) {
         const int b = base + threadIdx.x;
-        const int v = b < R ? I.sort_hist[ps * R + b] : 0;
+        const int v = b < R ? I.sort_dtot[b] : 0;
         int total;
         const int ex = block_exclusive_scan(v, sm, &total);
-        if (b < R) I.sort_dstart[ps * R + b] = carry + ex;
+        if (b < R) I.sort_dstart[b] = carry + ex;
         carry += total;
     }
 }
 
-// ------------------------------------------------------------- onesweep
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
+// Downsweep: one block per tile ranks its keys stably in shared memory and
+// writes each digit run to (digit start + the tile's offset of the digit).
 template <typename K, bool PACKED>
 __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
-    onesweep_kernel(const Inst* __restrict__ ins, Flat f, int pass, int* flat_counter) {
+    downsweep_kernel(const Inst* __restrict__ ins, Flat f, int pass) {
     constexpr int kItems = SortKey<K>::kItems;
     constexpr int kTile = os_tile<K>();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sm[33];
-    __shared__ int s_tile;
-    if (threadIdx.x == 0) s_tile = atomicAdd(flat_counter, 1);
-    __syncthreads();
-    const int ft = s_tile;
-    const int kk = flat_find(f, ft);
+    const int kk = flat_find(f, blockIdx.x);
     const Inst& I = ins[f.idx[kk]];
-    const int tile = ft - (int)f.off[kk];
-    const int n = I.p.n, bits = I.digit_bits, shift = pass * bits + (PACKED ? I.p.pack_bits : 0);
-    const int R = 1 << bits;
+    const int tile = blockIdx.x - (int)f.off[kk];
+    const int n = I.p.n, shift = pass_shift<K, PACKED>(I, pass);
+    const int R = 1 << I.digit_bits;
     const unsigned mask = (unsigned)R - 1u;
     const K* keys_in = (const K*)((pass & 1) ? I.keyB : I.keyA);
     K* keys_out = (K*)((pass & 1) ? I.keyA : I.keyB);
     const int* vals_in = (pass & 1) ? I.valB : I.valA;
     int* vals_out = (pass & 1) ? I.valA : I.valB;
-    const int* dstart_g = I.sort_dstart + pass * R;
-    unsigned long long* status = I.sort_status + (size_t)pass * I.tiles * R;
 
-    // layout: exchange keys [kTile] K, exchange vals [kTile] int,
+    // layout: exchange keys [kTile] K, exchange vals [kTile] int (unpacked),
     //         wcount [kOsWarps][R], ldstart [R], goff [R]
     K* skeys = reinterpret_cast<K*>(smem);
     int* svals = reinterpret_cast<int*>(smem + sizeof(K) * kTile);
@@ -235,6 +285,9 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
 
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kOsWarps * R; i += kOsBlock) wcount[i] = 0;
+    // the tile's global start of each digit
+    for (int b = threadIdx.x; b < R; b += kOsBlock)
+        goff[b] = I.sort_dstart[b] + I.sort_tcnt[(long long)tile * R + b];
     __syncthreads();
     const long long base = (long long)tile * kTile;
     const int count = (int)min((long long)kTile, (long long)n - base);
@@ -268,9 +321,9 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
     }
     __syncthreads();
 
-    // per digit: exclusive prefix over warps and the tile's count of it;
-    // then the exclusive prefix over digits (local start of each digit run).
-    // Thread t owns the `per` consecutive digits starting at t * per.
+    // per digit: exclusive prefix over warps; then the exclusive prefix over
+    // digits (local start of each digit run).  Thread t owns the `per`
+    // consecutive digits starting at t * per.
     {
         const int per = (R + kOsBlock - 1) / kOsBlock;  // 1 or 2 (R <= 512)
         constexpr int kPerMax = (kMaxBuckets + kOsBlock - 1) / kOsBlock;
@@ -288,7 +341,6 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
                     wcount[w * R + b] = tot;
                     tot += c;
                 }
-                goff[b] = tot;  // tile count of digit b, published by the look-back
                 tots[u] = tot;
                 sum += tot;
             }
@@ -305,51 +357,6 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
         }
         __syncthreads();
     }
-
-    // decoupled look-back: one thread per digit, reading kLookback earlier
-    // tiles per round trip (loads of consecutive digits are coalesced) and
-    // adding their counts up to the nearest inclusive one (tile 0's always is)
-    for (int b = threadIdx.x; b < R; b += kOsBlock) {
-        const unsigned own = (unsigned)goff[b];
-        unsigned long long* my = status + (long long)tile * R + b;
-        unsigned excl = 0;
-        if (tile == 0) {
-            st_relaxed(my, ((unsigned long long)kFlagInc << 32) | own);
-        } else {
-            st_relaxed(my, ((unsigned long long)kFlagAgg << 32) | own);
-            int t = tile - 1;
-            int polls = 0;
-            while (true) {
-                unsigned long long v[kLookback];
-#pragma unroll
-                for (int j = 0; j < kLookback; ++j)
-                    v[j] = t - j >= 0 ? ld_relaxed(status + (long long)(t - j) * R + b) : 0ull;
-                int used = 0;
-                bool done = false;
-#pragma unroll
-                for (int j = 0; j < kLookback; ++j) {
-                    if (done || used < j) break;  // stop at the first unpublished tile
-                    const unsigned flag = (unsigned)(v[j] >> 32);
-                    if (flag == 0u) break;
-                    excl += (unsigned)v[j];
-                    used = j + 1;
-                    if (flag == kFlagInc) done = true;
-                }
-                if (done) break;
-                t -= used;
-                if (used == 0) {
-                    if (++polls > kMaxPolls) {
-                        set_status(I, kDevTimeout);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            st_relaxed(my, ((unsigned long long)kFlagInc << 32) | (excl + own));
-        }
-        goff[b] = dstart_g[b] + (int)excl;
-    }
-    __syncthreads();
 
     // keys and values into tile-local digit order through shared memory
 #pragma unroll
@@ -376,72 +383,69 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
     }
 }
 
-template <typename K, bool PACKED> static size_t onesweep_smem(int R) {
+template <typename K, bool PACKED> static size_t downsweep_smem(int R) {
     return sizeof(K) * os_tile<K>() + (PACKED ? 0 : sizeof(int) * os_tile<K>()) + sizeof(int) * (kOsWarps * R + 2 * R);
 }
 
-cudaError_t launch_quantise_hist(const Inst* ins, Flat qtiles, long long total, int key_class, int max_hist_ints,
-                                 cudaStream_t st) {
-    const long long tiles = total;
-    if (tiles <= 0) return cudaSuccess;
-    const size_t smem = sizeof(int) * (size_t)(max_hist_ints > 0 ? max_hist_ints : 1);
+// ------------------------------------------------------------- launches
+
+cudaError_t launch_quantise(const Inst* ins, Flat qtiles, long long total, int key_class, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
     if (key_class == 0)
-        quantise_hist_kernel<unsigned long long, true><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+        quantise_kernel<unsigned long long, true><<<(unsigned)total, 256, 0, st>>>(ins, qtiles);
     else if (key_class == 1)
-        quantise_hist_kernel<unsigned long long, false><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+        quantise_kernel<unsigned long long, false><<<(unsigned)total, 256, 0, st>>>(ins, qtiles);
     else
-        quantise_hist_kernel<Key2, false><<<(unsigned)tiles, 256, smem, st>>>(ins, qtiles);
+        quantise_kernel<Key2, false><<<(unsigned)total, 256, 0, st>>>(ins, qtiles);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
-cudaError_t launch_digit_scan(const Inst* ins, const int* idx, int K, int max_passes, cudaStream_t st) {
-    if (K <= 0 || max_passes <= 0) return cudaSuccess;
-    digit_scan_kernel<<<dim3(K, max_passes), 256, 0, st>>>(ins, idx);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-template <typename K, bool PACKED>
-static cudaError_t onesweep_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets,
-                                   int* flat_counter, cudaStream_t st) {
-    const size_t smem = onesweep_smem<K, PACKED>(max_buckets);
-    onesweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, smem, st>>>(ins, tiles, pass, flat_counter);
-    return cudaSuccess;
-}
-
-cudaError_t prepare_onesweep() {
+cudaError_t prepare_sort() {
     static std::atomic<unsigned long long> done{0};  // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)onesweep_smem<unsigned long long, true>(kMaxBuckets));
+    e = cudaFuncSetAttribute(downsweep_kernel<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)downsweep_smem<unsigned long long, true>(kMaxBuckets));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(onesweep_kernel<unsigned long long, false>,
+        e = cudaFuncSetAttribute(downsweep_kernel<unsigned long long, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)onesweep_smem<unsigned long long, false>(kMaxBuckets));
+                                 (int)downsweep_smem<unsigned long long, false>(kMaxBuckets));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(onesweep_kernel<Key2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)onesweep_smem<Key2, false>(kMaxBuckets));
+        e = cudaFuncSetAttribute(downsweep_kernel<Key2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)downsweep_smem<Key2, false>(kMaxBuckets));
     if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
 
-cudaError_t launch_onesweep(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                            int* flat_counter, cudaStream_t st) {
-    if (total <= 0) return cudaSuccess;
-    cudaError_t e;
-    if (key_class == 0)
-        e = onesweep_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, flat_counter, st);
-    else if (key_class == 1)
-        e = onesweep_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, flat_counter, st);
-    else
-        e = onesweep_launch<Key2, false>(ins, tiles, total, pass, max_buckets, flat_counter, st);
-    if (e != cudaSuccess) return e;
+template <typename K, bool PACKED>
+static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets, cudaStream_t st) {
+    if (pass > 0 || os_tile<K>() != kQuantTile) {  // quantisation wrote the first histograms
+        upsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, 0, st>>>(ins, tiles, pass);
+        GD_COUNT_LAUNCH();
+    }
+    tile_scan_kernel<<<(unsigned)((long long)tiles.K * kMaxBuckets), kTileScanBlock, 0, st>>>(ins, tiles.idx,
+                                                                                          tiles.K, pass);
     GD_COUNT_LAUNCH();
+    digit_start_kernel<<<(unsigned)tiles.K, 256, 0, st>>>(ins, tiles.idx, pass);
+    GD_COUNT_LAUNCH();
+    downsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, downsweep_smem<K, PACKED>(max_buckets), st>>>(ins, tiles,
+                                                                                                      pass);
+    GD_COUNT_LAUNCH();
+}
+
+cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
+                             cudaStream_t st) {
+    if (total <= 0 || tiles.K <= 0) return cudaSuccess;
+    if (key_class == 0)
+        pass_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, st);
+    else if (key_class == 1)
+        pass_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, st);
+    else
+        pass_launch<Key2, false>(ins, tiles, total, pass, max_buckets, st);
     return cudaGetLastError();
 }
 
