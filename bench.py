@@ -34,12 +34,12 @@ WORKLOADS = {
 }
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) per onesweep launch, from one `ncu --set full`
+# DRAM bytes (read + write) per downsweep launch, from one `ncu --set full`
 # capture of the kernel on the default workload, keyed by a digest of the sort
 # source it was taken on: a changed kernel reports no traffic until it is
 # captured again.
-ONESWEEP_TRAFFIC = {
-    "a4f9489c670e4c58": {"workload": "ss3d_10m", "key_class": 0, "bytes": 128.0e6},
+SORT_PASS_TRAFFIC = {
+    "8e9cef104532108c": {"workload": "ss3d_10m", "key_class": 0, "bytes": 118.3e6},
 }
 
 
@@ -382,16 +382,18 @@ def run_gpu(args):
     if rank == 0:
         value = total_pts / (ms_max / 1e3) / 1e6
         peak, peak_kind = peaks()
-        # dominant kernel: the onesweep radix-sort pass.  Algorithmic bytes
-        # of one launch: every key and value read once and written once.
+        # dominant kernel: the radix sort's downsweep (one per pass), timed
+        # by the library's events around each launch.  Algorithmic bytes of
+        # one launch: every key (and value) of the pass read once and
+        # written once.
         passes = max(1, sizes["sort_passes"])
         # bytes one pass reads and writes per point: the packed key word, or
         # the key plus the 32-bit index
         unit_bytes = {0: 8, 1: 12, 2: 20}[sizes["key_class"]]
         launch_bytes = 2 * unit_bytes * n
-        launch_ms = stages.get("sort", 0.0) / passes
+        launch_ms = stages.get("sort_downsweep", 0.0) / passes
         achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
-        tr = ONESWEEP_TRAFFIC.get(sort_source_digest())
+        tr = SORT_PASS_TRAFFIC.get(sort_source_digest())
         traffic = (int(tr["bytes"]) if tr and tr["workload"] == args.workload and tr["key_class"] == sizes["key_class"]
                    else None)
         line = {
@@ -408,7 +410,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(n * 4 + n)},
             "gpu_launches": int(launches),
             "stages_ms": stages,
-            "roofline": {"bound": "hbm", "kernel": "onesweep_kernel (one radix-sort pass)",
+            "roofline": {"bound": "hbm", "kernel": "downsweep_kernel (radix-sort pass: rank and scatter)",
                          "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,

@@ -101,7 +101,8 @@ struct gd_ctx {
     DevBuf io;  // device copies for gd_dbscan_host
     cudaEvent_t ev[kStages + 1] = {};
     bool timing = false;
-    float stage_ms[kStages] = {};
+    float stage_ms[kStages + 1] = {};   // the stages, then the sort's downsweeps
+    cudaEvent_t sev[2 * kSortEventPairs] = {};
     int nstages = 0;
     std::string err;
     bool have_run = false;
@@ -148,7 +149,7 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     ctx->info = RunInfo();
     const long long l0 = t_launches;
     gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning,
-                            &ctx->graphs);
+                            &ctx->graphs, ctx->timing ? ctx->sev : nullptr);
     ctx->info.sizes[6] = t_launches - l0;
     if (s != GD_OK) {
         if (ctx->err.empty()) ctx->err = ctx->info.error;
@@ -156,7 +157,14 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     }
     if (ctx->timing) {
         for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&ctx->stage_ms[i], ctx->ev[i], ctx->ev[i + 1]);
-        ctx->nstages = kStages;
+        float ds = 0.f;
+        for (int i = 0; i < ctx->info.sort_event_pairs; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->sev[2 * i], ctx->sev[2 * i + 1]);
+            ds += t;
+        }
+        ctx->stage_ms[kStages] = ds;
+        ctx->nstages = kStages + 1;
     }
     ctx->have_run = true;
     return GD_OK;
@@ -174,6 +182,7 @@ gd_status gd_create(gd_ctx** out, int device) {
     ctx->device = device;
     cudaError_t e = cudaSetDevice(device);
     for (int i = 0; e == cudaSuccess && i <= kStages; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; e == cudaSuccess && i < 2 * kSortEventPairs; ++i) e = cudaEventCreate(&ctx->sev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         gd_destroy(ctx);
@@ -194,6 +203,8 @@ void gd_destroy(gd_ctx* ctx) {
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     for (int i = 0; i <= kStages; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 2 * kSortEventPairs; ++i)
+        if (ctx->sev[i]) cudaEventDestroy(ctx->sev[i]);
     delete ctx;
 }
 
@@ -364,7 +375,7 @@ int gd_stage_times(const gd_ctx* ctx, float* ms, const char** names, int max) {
     int k = ctx->nstages < max ? ctx->nstages : max;
     for (int i = 0; i < k; ++i) {
         if (ms) ms[i] = ctx->stage_ms[i];
-        if (names) names[i] = kStageNames[i];
+        if (names) names[i] = i < kStages ? kStageNames[i] : "sort_downsweep";
     }
     return k;
 }

@@ -333,8 +333,11 @@ cudaError_t launch_quantise(const Inst* ins, Flat tiles, long long total, int ke
 cudaError_t prepare_sort();
 // One radix-sort pass (upsweep, tile scan, digit starts, downsweep) of digit
 // position `pass` over the sort tiles of the instances of one key class.
+// ev_a / ev_b, when set, are recorded just before and after the downsweep.
 cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                             cudaStream_t st);
+                             cudaStream_t st, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr);
+// Records ev on st; inside a stream capture, as an external graph node.
+void record_event(cudaEvent_t ev, cudaStream_t st);
 
 // Grid-tree levels and neighbour walk (neighbors.cu).
 cudaError_t launch_point_boxes(const Inst* ins, Flat cells, long long total, cudaStream_t st);

@@ -152,6 +152,7 @@ struct Run {
     RunInfo* info;
     const Tuning* tune;
     PhaseGraphs* graphs;
+    cudaEvent_t* sort_ev;  // kSortEventPairs pairs, or null
     int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
 
     // Runs the launches of phase `id` (body issues them on st): directly, or
@@ -222,14 +223,7 @@ struct Run {
         return GD_ECUDA;
     }
     void mark(int s) {
-        if (!ev) return;
-        // inside a captured phase an external record becomes a graph node
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        cudaStreamIsCapturing(st, &cs);
-        if (cs == cudaStreamCaptureStatusActive)
-            cudaEventRecordWithFlags(ev[s], st, cudaEventRecordExternal);
-        else
-            cudaEventRecord(ev[s], st);
+        if (ev) record_event(ev[s], st);
     }
 
     gd_status begin_desc() {
@@ -500,9 +494,18 @@ gd_status Run::go() {
     mark(1);
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_quantise(dins, qflat[w], qtot[w], w, st), "quantise");
     mark(2);
+    int pairs = 0;
     for (int w = 0; w < 3; ++w)
-        for (int ps = 0; ps < gpasses[w]; ++ps)
-            RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st), "sort pass");
+        for (int ps = 0; ps < gpasses[w]; ++ps) {
+            cudaEvent_t a = nullptr, b2 = nullptr;
+            if (sort_ev && otot[w][ps] > 0 && pairs < kSortEventPairs) {
+                a = sort_ev[2 * pairs];
+                b2 = sort_ev[2 * pairs + 1];
+                ++pairs;
+            }
+            RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st, a, b2), "sort pass");
+        }
+    if (info) info->sort_event_pairs = pairs;
     mark(3);
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w, st), "compact count");
     RUN_TRY(scan(cseg, K, cseg_tiles));
@@ -804,8 +807,8 @@ int Tuning::value(int knob, int d, long long n) const {
 }
 
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs) {
-    Run r{mem, K, inst, st, events, info, tuning, graphs};
+                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs, cudaEvent_t* sort_events) {
+    Run r{mem, K, inst, st, events, info, tuning, graphs, sort_events};
     const long long l0 = t_launches;
     const gd_status s = r.go();
     if (info) info->launches = t_launches - l0;

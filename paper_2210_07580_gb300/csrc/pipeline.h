@@ -37,12 +37,18 @@ struct MemProvider {
 constexpr int kStages = 11;
 extern const char* const kStageNames[kStages];
 
+// Kernel timing of the sort's downsweeps: when the driver is given sort
+// events, it records a pair around each downsweep launch (at most
+// kSortEventPairs) and reports how many pairs it used.
+constexpr int kSortEventPairs = 48;
+
 // What the driver reports about the run (instance 0 for the views).
 struct RunInfo {
     long long sizes[12];
     const void* view_ptr[7];
     size_t view_bytes[7];
     long long launches;
+    int sort_event_pairs = 0;
     std::string error;
 };
 
@@ -80,6 +86,7 @@ struct PhaseGraphs {
 // is_core (device pointers).  Returns the first error; `info` and `tuning`
 // may be null (defaults).
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs = nullptr);
+                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs = nullptr,
+                    cudaEvent_t* sort_events = nullptr);
 
 }  // namespace gd

@@ -421,8 +421,18 @@ cudaError_t prepare_sort() {
     return e;
 }
 
+void record_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 template <typename K, bool PACKED>
-static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets, cudaStream_t st) {
+static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets, cudaStream_t st,
+                        cudaEvent_t ev_a, cudaEvent_t ev_b) {
     if (pass > 0 || os_tile<K>() != kQuantTile) {  // quantisation wrote the first histograms
         upsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, 0, st>>>(ins, tiles, pass);
         GD_COUNT_LAUNCH();
@@ -432,20 +442,22 @@ static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, 
     GD_COUNT_LAUNCH();
     digit_start_kernel<<<(unsigned)tiles.K, 256, 0, st>>>(ins, tiles.idx, pass);
     GD_COUNT_LAUNCH();
+    if (ev_a) record_event(ev_a, st);
     downsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, downsweep_smem<K, PACKED>(max_buckets), st>>>(ins, tiles,
                                                                                                       pass);
     GD_COUNT_LAUNCH();
+    if (ev_b) record_event(ev_b, st);
 }
 
 cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t ev_a, cudaEvent_t ev_b) {
     if (total <= 0 || tiles.K <= 0) return cudaSuccess;
     if (key_class == 0)
-        pass_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, st);
+        pass_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
     else if (key_class == 1)
-        pass_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, st);
+        pass_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
     else
-        pass_launch<Key2, false>(ins, tiles, total, pass, max_buckets, st);
+        pass_launch<Key2, false>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
     return cudaGetLastError();
 }
 

@@ -10,8 +10,10 @@ overlaps on the device.  Scheduling:
   its estimated device footprint fits in what the budget has left; jobs that
   do not fit wait (small jobs behind them may go first -- backfill);
 - a large job (more than `large_job_points` points) keeps the whole GPU busy
-  by itself, so at most `max_large` of them run at a time (running two only
-  makes them compete for L2); batches of small jobs may run beside them;
+  by itself, so at most `max_large` of them compute at a time (running two
+  only makes them compete for L2); their host staging (copies in and out)
+  overlaps the other's compute, and batches of small jobs may run beside
+  them;
 - continuous batching: a slot that takes a small job also takes the other
   small jobs queued at that moment (up to a point and job budget) and runs
   them as one gd_dbscan_batched call; large jobs run alone;
@@ -92,7 +94,9 @@ class GpuBackend:
             self.bufs[slot][name] = b
         return b
 
-    def run(self, slot: int, jobs):
+    def run(self, slot: int, jobs, gate=None):
+        """Stage the jobs in, cluster them (holding `gate`, if given, only
+        around the library call) and stage the results out."""
         torch = self.torch
         ctx, stream = self.ctxs[slot], self.streams[slot]
         al = self.ALIGN
@@ -120,11 +124,18 @@ class GpuBackend:
                 core = dout[oo + up(4 * n):oo + up(4 * n) + n]
                 dev.append((Xd, j.eps2, j.minpts))
                 outs.append((lab, core))
-            if len(dev) == 1:
-                Xd, e, m = dev[0]
-                ctx.dbscan(Xd, e, m, labels=outs[0][0], is_core=outs[0][1], stream=stream)
-            else:
-                ctx.dbscan_batched(dev, outputs=outs, stream=stream)
+            if gate is not None:
+                stream.synchronize()  # inputs on the device before taking the GPU
+                gate.acquire()
+            try:
+                if len(dev) == 1:
+                    Xd, e, m = dev[0]
+                    ctx.dbscan(Xd, e, m, labels=outs[0][0], is_core=outs[0][1], stream=stream)
+                else:
+                    ctx.dbscan_batched(dev, outputs=outs, stream=stream)
+            finally:
+                if gate is not None:
+                    gate.release()
             hout[:tout].copy_(dout[:tout], non_blocking=True)
             stream.synchronize()
         hout_np = hout.numpy()
@@ -161,7 +172,7 @@ class Server:
         self.batch_max_points = batch_max_points
         self.large = large_job_points
         self.max_large = max_large
-        self.large_inflight = 0
+        self.large_gate = threading.Semaphore(max_large)
         self.queue: collections.deque[Job] = collections.deque()
         self.cv = threading.Condition()
         self.closed = False
@@ -213,9 +224,6 @@ class Server:
             return None
         room = self.budget - self.in_use
         head = self.queue[0]
-        if head.n > self.large and self.large_inflight >= self.max_large:
-            # the GPU is taken by large jobs: only small jobs may start now
-            return self._take_small(room)
         if head.footprint <= room:
             if head.n > self.small:
                 self.queue.popleft()
@@ -233,25 +241,10 @@ class Server:
                 self.queue.remove(j)
             return batch
         for j in self.queue:
-            if j.footprint <= room and not (j.n > self.large and self.large_inflight >= self.max_large):
+            if j.footprint <= room:
                 self.queue.remove(j)
                 return [j]
         return None
-
-    def _take_small(self, room):
-        """Small queued jobs (FIFO, coalesced) that fit in `room`, or None."""
-        batch, pts, fp = [], 0, 0
-        for j in self.queue:
-            if j.n > self.small:
-                continue
-            if len(batch) >= self.batch_max_jobs or pts + j.n > self.batch_max_points or fp + j.footprint > room:
-                break
-            batch.append(j)
-            pts += j.n
-            fp += j.footprint
-        for j in batch:
-            self.queue.remove(j)
-        return batch or None
 
     def _worker(self, slot: int):
         while True:
@@ -267,22 +260,20 @@ class Server:
                 if work is None:
                     return
                 fp = sum(j.footprint for j in work)
-                nlarge = sum(1 for j in work if j.n > self.large)
                 self.in_use += fp
-                self.large_inflight += nlarge
             t0 = time.perf_counter()
             for j in work:
                 j.t_start = t0
                 j.batch_size = len(work)
             try:
-                results = self.backend.run(slot, work)
+                large = any(j.n > self.large for j in work)
+                results = self.backend.run(slot, work, self.large_gate if large else None)
                 err = None
             except Exception as e:  # the jobs fail, the server goes on
                 results, err = None, e
             t1 = time.perf_counter()
             with self.cv:
                 self.in_use -= fp
-                self.large_inflight -= nlarge
                 for k, j in enumerate(work):
                     j.t_done = t1
                     self.done.append(j)

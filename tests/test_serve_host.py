@@ -26,7 +26,13 @@ class FakeBackend:
 
     large_at = 2000  # jobs above this many points count as large here
 
-    def run(self, slot, jobs):
+    def run(self, slot, jobs, gate=None):
+        if gate is not None:
+            with gate:
+                return self._run(jobs)
+        return self._run(jobs)
+
+    def _run(self, jobs):
         fp = sum(j.footprint for j in jobs)
         nl = sum(1 for j in jobs if j.n > self.large_at)
         with self.lock:
