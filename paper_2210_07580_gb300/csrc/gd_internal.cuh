@@ -256,6 +256,15 @@ __device__ __forceinline__ int uf_find_ro(const int* parent, int x) {
     return -1;
 }
 
+// The core points of grid c (rows of dp ints): a grid with at least MinPts
+// points has only core points (G13 rule) and they stay in place in the
+// grid-order coordinates Xs; the core points of other grids are packed in Xc
+// from core_start[c].  Either way core_start[c+1] - core_start[c] rows.
+__device__ __forceinline__ const int* core_rows(const Inst& I, int c, int dp) {
+    const int b = I.cell_start[c];
+    return I.cell_start[c + 1] - b >= I.p.minpts ? I.Xs + (long long)b * dp : I.Xc + (long long)I.core_start[c] * dp;
+}
+
 __device__ __forceinline__ void set_status(const Inst& I, unsigned bits) {
     atomicOr(reinterpret_cast<unsigned*>(I.small + kSmStatus), bits);
 }

@@ -106,10 +106,12 @@ __device__ __forceinline__ int border_label(const Inst& I, long long q, int c) {
             g2 += g * g;
         }
         if (g2 > eps2) continue;
-        for (int u = I.core_start[c2]; u < I.core_start[c2 + 1]; ++u) {
+        const int* Y = core_rows(I, c2, DP);
+        const int m2 = I.core_start[c2 + 1] - I.core_start[c2];
+        for (int u = 0; u < m2; ++u) {
             int y[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) y[j] = I.Xc[(long long)u * DP + j];
+            for (int j = 0; j < D; ++j) y[j] = Y[(long long)u * DP + j];
             if (sqdist<D>(x, y) <= eps2) {
                 best = id;
                 break;

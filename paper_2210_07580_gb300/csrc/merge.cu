@@ -50,9 +50,10 @@ cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cuda
     return cudaGetLastError();
 }
 
-// Core points of each grid packed contiguously (s_i of Section 4.3.1), one
-// thread per point in grid order (a point of a full grid keeps its offset in
-// the grid; in other grids it counts the core points before it), and the
+// Core points of the grids that are not full packed contiguously (s_i of
+// Section 4.3.1; a full grid's core points are its rows in Xs, see
+// core_rows), one thread per point in grid order (a point counts the core
+// points of its grid before it), and the
 // bounding box of each grid's core points by atomics: a warp whose 32 points
 // are all core points of one grid (the common case in dense data) reduces
 // them first and applies one atomic per bound.
@@ -77,17 +78,17 @@ __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__
                 const int dp = I->p.dp;
                 c = I->pt_cell[q];
                 const int b = I->cell_start[c];
-                long long pos;
-                if (I->cell_start[c + 1] - b >= I->p.minpts) {
-                    pos = I->core_start[c] + (q - b);
-                } else {
+                // a full grid's core rows are its rows in Xs (core_rows)
+                const bool full = I->cell_start[c + 1] - b >= I->p.minpts;
+                long long pos = 0;
+                if (!full) {
                     int r = 0;
                     for (long long u = b; u < q; ++u) r += I->core_s[u];
                     pos = I->core_start[c] + r;
                 }
                 if (dp == 4) {
                     const int4 v = *reinterpret_cast<const int4*>(I->Xs + q * 4);
-                    *reinterpret_cast<int4*>(I->Xc + pos * 4) = v;
+                    if (!full) *reinterpret_cast<int4*>(I->Xc + pos * 4) = v;
                     x[0] = v.x;
                     x[1] = v.y;
                     x[2] = v.z;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__
                     for (int j = 0; j < kMaxD; ++j)
                         if (j < dp) {
                             x[j] = I->Xs[q * dp + j];
-                            I->Xc[pos * dp + j] = x[j];
+                            if (!full) I->Xc[pos * dp + j] = x[j];
                         }
                 }
             }
@@ -372,18 +373,19 @@ __global__ void __launch_bounds__(256)
                     box_decision<D>(I.bbox + (long long)pr.x * 2 * D, I.bbox + (long long)pr.y * 2 * D, eps2);
                 bool yes = dec == 1;
                 if (dec < 0) {
-                    const int ai = I.core_start[pr.x], mi = I.core_start[pr.x + 1] - ai;
-                    const int aj = I.core_start[pr.y], mj = I.core_start[pr.y + 1] - aj;
+                    const int mi = I.core_start[pr.x + 1] - I.core_start[pr.x];
+                    const int mj = I.core_start[pr.y + 1] - I.core_start[pr.y];
                     if ((long long)mi * mj <= lane_limit) {
-                        const int* Xc = I.Xc;
+                        const int* A = core_rows(I, pr.x, DP);
+                        const int* B = core_rows(I, pr.y, DP);
                         for (int u = 0; u < mi && !yes; ++u) {
                             int P[D];
 #pragma unroll
-                            for (int j = 0; j < D; ++j) P[j] = Xc[(long long)(ai + u) * DP + j];
+                            for (int j = 0; j < D; ++j) P[j] = A[(long long)u * DP + j];
                             for (int v = 0; v < mj; ++v) {
                                 int Q[D];
 #pragma unroll
-                                for (int j = 0; j < D; ++j) Q[j] = Xc[(long long)(aj + v) * DP + j];
+                                for (int j = 0; j < D; ++j) Q[j] = B[(long long)v * DP + j];
                                 if (sqdist<D>(P, Q) <= eps2) {
                                     yes = true;
                                     break;
@@ -415,9 +417,10 @@ __global__ void __launch_bounds__(256)
                 same = ra == rb;
             }
             if (__shfl_sync(kFull, same, 0)) continue;
-            const int* Xc = I.Xc;
-            const int ai = I.core_start[px], mi = I.core_start[px + 1] - ai;
-            const int aj = I.core_start[py], mj = I.core_start[py + 1] - aj;
+            const int* A = core_rows(I, px, DP);
+            const int* B = core_rows(I, py, DP);
+            const int mi = I.core_start[px + 1] - I.core_start[px];
+            const int mj = I.core_start[py + 1] - I.core_start[py];
             const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
             const long long tiles = (long long)na * nb;
             const bool exhaustive = mi <= small_set && mj <= small_set;
@@ -432,8 +435,8 @@ __global__ void __launch_bounds__(256)
                 const bool vq = b0 + lane < mj;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    P[j] = lane < ca ? Xc[(long long)(ai + a0 + lane) * DP + j] : 0;
-                    Q[j] = vq ? Xc[(long long)(aj + b0 + lane) * DP + j] : 0;
+                    P[j] = lane < ca ? A[(long long)(a0 + lane) * DP + j] : 0;
+                    Q[j] = vq ? B[(long long)(b0 + lane) * DP + j] : 0;
                 }
                 bool hit = false;
                 for (int u = 0; u < ca; ++u) {
@@ -625,8 +628,8 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
             gi = pr.y;
             gj = pr.x;
         }
-        const int* A = I.Xc + (long long)core_start[gi] * DP;
-        const int* B = I.Xc + (long long)core_start[gj] * DP;
+        const int* A = core_rows(I, gi, DP);
+        const int* B = core_rows(I, gj, DP);
         const int ma = core_start[gi + 1] - core_start[gi];
         const int mb = core_start[gj + 1] - core_start[gj];
         const int wa = (ma + 31) >> 5, wb = (mb + 31) >> 5;
