@@ -390,20 +390,30 @@ cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, i
     return cudaGetLastError();
 }
 
-// Largest grid of each instance (bounds the merge's bitmaps), over the flat
-// space of points: the point that starts a grid looks the grid's size up.
-// small[kSmMaxCell] must be 0 first.
+// Largest grid of each instance (bounds the merge's bitmaps).  The flat
+// space is the instances' points, an upper bound of their grids: a warp-sized
+// grid-stride loop visits only c < C (read on the device), reduces the sizes
+// in the warp and applies one atomic.  small[kSmMaxCell] must be 0 first.
 __global__ void cell_max_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
     FlatCursor cur;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        cur.seek(f, i);
-        const int k = cur.k;
-        const Inst& I = ins[f.idx[k]];
-        const long long q = i - cur.lo;
-        const int c = I.pt_cell[q];
-        if (I.cell_start[c] != q) continue;
-        atomicMax(I.small + kSmMaxCell, I.cell_start[c + 1] - (int)q);
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const long long i = base + lane_id();
+        int kk = -1, size = 0;
+        if (i < total) {
+            cur.seek(f, i);
+            kk = f.idx[cur.k];
+            const Inst& I = ins[kk];
+            const long long c = i - cur.lo;
+            if (c < I.small[kSmCells]) size = I.cell_start[c + 1] - I.cell_start[c];
+        }
+        const int k0 = __shfl_sync(kFull, kk, 0);
+        if (__all_sync(kFull, kk == k0)) {
+            const int m = __reduce_max_sync(kFull, (unsigned)size);
+            if (lane_id() == 0 && k0 >= 0 && m > 0) atomicMax(ins[k0].small + kSmMaxCell, m);
+        } else if (kk >= 0 && size > 0) {
+            atomicMax(ins[kk].small + kSmMaxCell, size);
+        }
     }
 }
 

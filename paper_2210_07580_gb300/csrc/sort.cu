@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kOsBlock) upsweep_kernel(const Inst* __restric
     for (int b = threadIdx.x; b < R; b += kOsBlock) out[b] = hist[b];
 }
 
-// Tile scan: one block per (member instance, digit): exclusive offsets of the
+// Tile scan: one block per (member instance, digit < max_buckets): exclusive offsets of the
 // digit over the tiles, in place, and the digit's total.  Each thread takes a
 // run of consecutive tiles (its loads are independent), then one block scan
 // joins the runs.
@@ -205,9 +205,9 @@ constexpr int kTileScanBlock = 256;
 constexpr int kTileScanRun = 16;  // tiles per thread held in registers
 
 __global__ void __launch_bounds__(kTileScanBlock)
-    tile_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int m, int pass) {
+    tile_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int m, int pass, int max_buckets) {
     __shared__ int sm[33];
-    const int t = blockIdx.x / kMaxBuckets, dg = blockIdx.x % kMaxBuckets;
+    const int t = blockIdx.x / max_buckets, dg = blockIdx.x % max_buckets;
     if (t >= m) return;
     const Inst& I = ins[idx[t]];
     const int R = 1 << I.digit_bits;
@@ -437,8 +437,8 @@ static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, 
         upsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, 0, st>>>(ins, tiles, pass);
         GD_COUNT_LAUNCH();
     }
-    tile_scan_kernel<<<(unsigned)((long long)tiles.K * kMaxBuckets), kTileScanBlock, 0, st>>>(ins, tiles.idx,
-                                                                                          tiles.K, pass);
+    tile_scan_kernel<<<(unsigned)((long long)tiles.K * max_buckets), kTileScanBlock, 0, st>>>(ins, tiles.idx,
+                                                                                          tiles.K, pass, max_buckets);
     GD_COUNT_LAUNCH();
     digit_start_kernel<<<(unsigned)tiles.K, 256, 0, st>>>(ins, tiles.idx, pass);
     GD_COUNT_LAUNCH();
