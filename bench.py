@@ -35,19 +35,48 @@ WORKLOADS = {
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) per downsweep launch, from one `ncu --set full`
-# capture of the kernel on the default workload, keyed by a digest of the sort
-# source it was taken on: a changed kernel reports no traffic until it is
+# capture of the kernel on the default workload, keyed by a digest of the
+# kernel's source text: a changed kernel reports no traffic until it is
 # captured again.
 SORT_PASS_TRAFFIC = {
-    "8e9cef104532108c": {"workload": "ss3d_10m", "key_class": 0, "bytes": 118.3e6},
+    "96004fb889c98175": {"workload": "ss3d_10m", "key_class": 0, "bytes": 118.3e6},
 }
 
 
 def sort_source_digest() -> str:
+    """Digest of the downsweep kernel's source text (the kernel the traffic
+    table describes)."""
     import hashlib
     path = os.path.join(ROOT, "paper_2210_07580_gb300", "csrc", "sort.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path) as f:
+        text = f.read()
+    a = text.find("// Downsweep: one block per tile ranks its keys stably")
+    b = text.find("template <typename K, bool PACKED> static size_t downsweep_smem")
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16] if 0 <= a < b else ""
+
+
+def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float) -> dict:
+    """Achieved bandwidth of the grid-build stages: algorithmic bytes (each
+    array the stage must read or write, once) over the stage's device time."""
+    dp = 1 if d == 1 else 2 if d == 2 else 4 if d <= 4 else 8
+    kc = sizes["key_class"]
+    key_b = 16 if kc == 2 else 8
+    val_b = 0 if kc == 0 else 4
+    P = sizes["sort_passes"]
+    first_hist = kc != 2  # quantisation writes the first pass's tile histograms for 64-bit keys
+    bytes_ = {
+        "bounds": 4 * d * n,
+        "quantise": (4 * d + key_b + val_b) * n,
+        "sort": (P * 2 * (key_b + val_b) + (P - (1 if first_hist else 0)) * key_b) * n,
+        "compact": (2 * key_b + val_b + 4 + 4 + 4 * d + 4 * dp) * n,
+    }
+    out = {}
+    for st, b in bytes_.items():
+        ms = stages.get(st, 0.0)
+        if ms > 0:
+            gbs = b / (ms / 1e3) / 1e9
+            out[st] = {"bytes": int(b), "ms": round(ms, 4), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    return out
 
 
 def reduce_over_ranks(ms: float, e2e_ms: float, points: int, ws: int, device):
@@ -417,6 +446,7 @@ def run_gpu(args):
                          "bytes_per_launch": int(launch_bytes), "launch_ms": round(launch_ms, 4),
                          "launches_per_step": passes},
             "wall_s_timed": round(t_wall, 3),
+            "stage_bandwidth": stage_bandwidth(stages, n, d, sizes, peak),
         }
         if not args.no_batch:
             line["batched"] = bench_batched(ctx, dev, args)

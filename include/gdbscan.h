@@ -220,8 +220,10 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
 /* Per-stage device timing (CUDA events around each stage of gd_dbscan).
  * Off by default; when on, gd_stage_times fills up to max entries of
  * milliseconds and names for the last run and returns the count: the 11
- * stages in order, then "sort_downsweep", the summed time of the radix
- * sort's downsweep kernels (part of the "sort" stage). */
+ * stages in order (device time from a stage's first launch to its last; the
+ * host's work between the call's phases is in none of them), then
+ * "sort_downsweep", the summed time of the radix sort's downsweep kernels
+ * (part of the "sort" stage). */
 gd_status gd_set_timing(gd_ctx *ctx, int enable);
 int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
 

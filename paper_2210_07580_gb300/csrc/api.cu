@@ -99,7 +99,7 @@ struct gd_ctx {
     int device = 0;
     CtxMem mem;
     DevBuf io;  // device copies for gd_dbscan_host
-    cudaEvent_t ev[kStages + 1] = {};
+    cudaEvent_t ev[kStageEvents] = {};
     bool timing = false;
     float stage_ms[kStages + 1] = {};   // the stages, then the sort's downsweeps
     cudaEvent_t sev[2 * kSortEventPairs] = {};
@@ -156,7 +156,11 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
         return s;
     }
     if (ctx->timing) {
-        for (int i = 0; i < kStages; ++i) cudaEventElapsedTime(&ctx->stage_ms[i], ctx->ev[i], ctx->ev[i + 1]);
+        for (int i = 0; i < kStages; ++i) {
+            // stages ending at a read-back of sizes have their own end event
+            const int end = i == 0 ? kStages + 1 : i == 3 ? kStages + 2 : i == 5 ? kStages + 3 : i + 1;
+            cudaEventElapsedTime(&ctx->stage_ms[i], ctx->ev[i], ctx->ev[end]);
+        }
         float ds = 0.f;
         for (int i = 0; i < ctx->info.sort_event_pairs; ++i) {
             float t = 0.f;
@@ -181,7 +185,7 @@ gd_status gd_create(gd_ctx** out, int device) {
     if (!ctx) return GD_ENOMEM;
     ctx->device = device;
     cudaError_t e = cudaSetDevice(device);
-    for (int i = 0; e == cudaSuccess && i <= kStages; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; e == cudaSuccess && i < kStageEvents; ++i) e = cudaEventCreate(&ctx->ev[i]);
     for (int i = 0; e == cudaSuccess && i < 2 * kSortEventPairs; ++i) e = cudaEventCreate(&ctx->sev[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -201,7 +205,7 @@ void gd_destroy(gd_ctx* ctx) {
     if (ctx->own_ev) cudaEventDestroy(ctx->own_ev);
     ctx->mem.release();
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
-    for (int i = 0; i <= kStages; ++i)
+    for (int i = 0; i < kStageEvents; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     for (int i = 0; i < 2 * kSortEventPairs; ++i)
         if (ctx->sev[i]) cudaEventDestroy(ctx->sev[i]);

@@ -387,7 +387,6 @@ gd_status Run::go() {
     long long tot;
 
     // --------------------------------------------- phase 1: bounds (sync 1)
-    mark(0);
     RUN_TRY(begin_desc());
     Flat pts_d[kMaxD];
     long long tot_d[kMaxD] = {};
@@ -399,8 +398,10 @@ gd_status Run::go() {
     }
     RUN_TRY(upload_desc());
     RUN_TRY(phase(0, [&]() -> gd_status {
+        mark(0);
         RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
         for (int d = 1; d <= kMaxD; ++d) RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
+        mark(kStages + 1);
         return GD_OK;
     }));
     RUN_TRY(readback());
@@ -511,6 +512,7 @@ gd_status Run::go() {
     RUN_TRY(scan(cseg, K, cseg_tiles));
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w, st), "compact write");
     RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
+    mark(kStages + 2);
     return GD_OK;
     }));
     RUN_TRY(readback());
@@ -592,6 +594,7 @@ gd_status Run::go() {
              "walk");
     RUN_TRY(scan(nseg, K, nseg_tiles));
     RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
+    mark(kStages + 3);
     return GD_OK;
     }));
     RUN_TRY(readback());

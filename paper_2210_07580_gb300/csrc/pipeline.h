@@ -32,9 +32,12 @@ struct MemProvider {
     virtual void note_nbr_per_grid(double) {}
 };
 
-// Stage timing: when non-null, events[s] is recorded before stage s and
-// events[kStages] at the end.
+// Stage timing: when non-null, events[s] is recorded when stage s starts and
+// events[kStages] at the end; stages that end at a read-back of sizes
+// (bounds, compact, walk) also record events[kStages + 1 + i], i = 0, 1, 2,
+// when their last kernel is issued, so that no stage includes host work.
 constexpr int kStages = 11;
+constexpr int kStageEvents = kStages + 4;
 extern const char* const kStageNames[kStages];
 
 // Kernel timing of the sort's downsweeps: when the driver is given sort
