@@ -197,8 +197,9 @@ gd_status gd_get_knob(const gd_ctx *ctx, int knob, int d, int64_t n, int32_t *va
  * graphs on, each phase's launches are captured from the call's stream into
  * a graph that the context keeps (one per phase): the next call updates it
  * in place when only launch parameters differ (re-instantiating it when the
- * launch sequence differs) and launches the phase as one graph.  Results are
- * identical either way.  Off by default for a new context; the stream must
+ * launch sequence differs) and launches the phase as one graph (calls of
+ * fewer than 2^18 points in all run without graphs: re-capturing would cost
+ * more than it saves).  Results are identical either way.  Off by default for a new context; the stream must
  * not be capturing already.  gd_graph_stats: out[0] = graph launches,
  * out[1] = in-place updates, out[2] = instantiations, since creation. */
 gd_status gd_set_graphs(gd_ctx *ctx, int enable);

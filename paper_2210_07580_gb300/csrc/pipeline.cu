@@ -153,13 +153,15 @@ struct Run {
     const Tuning* tune;
     PhaseGraphs* graphs;
     cudaEvent_t* sort_ev;  // kSortEventPairs pairs, or null
+    long long total_points = 0;
     int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
 
     // Runs the launches of phase `id` (body issues them on st): directly, or
     // captured into the phase's executable graph and launched as one graph.
     // A capture that fails is discarded and the launches are issued directly.
     template <typename F> gd_status phase(int id, F&& body) {
-        if (!graphs || !graphs->enabled) return body();
+        // small batches re-capture more than they save in launches
+        if (!graphs || !graphs->enabled || total_points < kGraphMinPoints) return body();
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             return body();
@@ -381,6 +383,7 @@ gd_status Run::go() {
     void* stp = nullptr;
     RUN_TRY(mem.device(kMemScanTmp, scan_tmp_ints * 4, &stp));
     scan_tmp = (int*)stp;
+    total_points = total_pts;
     for (int k = 0; k < K; ++k) members[k] = k;
     auto n_of = [&](int k) { return (long long)in[k].n; };
     auto C_of = [&](int k) { return hi[k].C; };

@@ -72,6 +72,9 @@ bool knob_in_range(int knob, int value);
 // captures a phase's launches from its stream and updates the executable
 // graph in place when only parameters changed (re-instantiating it when the
 // launch sequence changed), then launches it.
+// Calls with fewer points in all run without graphs.
+constexpr long long kGraphMinPoints = 1 << 18;
+
 struct PhaseGraphs {
     bool enabled = false;
     cudaGraphExec_t exec[4] = {};

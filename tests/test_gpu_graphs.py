@@ -17,7 +17,8 @@ def _np(res):
 def test_graph_phases_match_direct_launches():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    cases = [synth.workload("tiny", n=8000, seed=s) for s in (1, 2)] + [synth.workload("ss3d_2m", n=300_000, seed=3)]
+    # every case above the library's graph threshold (2^18 points)
+    cases = [synth.workload("tiny", n=300_000, seed=s) for s in (1, 2)] + [synth.workload("ss3d_2m", n=300_000, seed=3)]
     direct = Context(0)
     graphed = Context(0)
     graphed.set_graphs(True)
@@ -47,6 +48,12 @@ def test_graph_phases_match_direct_launches():
     times = graphed.stage_times()
     assert len(times) == 12 and all(v >= 0 for v in times.values()) and sum(times.values()) > 0
     assert 0 < times["sort_downsweep"] <= times["sort"]
+    # a small call runs without graphs
+    X, e, m = synth.workload("tiny", n=8000, seed=4)
+    before = graphed.graph_stats()
+    lab, core = graphed.dbscan(torch.from_numpy(X).cuda(), e, m)
+    assert graphed.graph_stats() == before
+    np.testing.assert_array_equal(lab.cpu().numpy(), oracle.grid(X, e, m)[0])
     direct.close()
     graphed.close()
 
@@ -54,7 +61,7 @@ def test_graph_phases_match_direct_launches():
 def test_graph_phases_batched():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    jobs = synth.batch_instances(16, seed=3, n_lo=300, n_hi=30000)
+    jobs = synth.batch_instances(16, seed=3, n_lo=20_000, n_hi=60_000)  # above the graph threshold in all
     dj = [(torch.from_numpy(X).cuda(), e, m) for X, e, m in jobs]
     ref = _np(Context(0).dbscan_batched(dj))
     ctx = Context(0)
@@ -64,4 +71,5 @@ def test_graph_phases_batched():
         for (a, ac), (b, bc) in zip(ref, got):
             np.testing.assert_array_equal(a, b)
             np.testing.assert_array_equal(ac, bc)
+    assert ctx.graph_stats()["launches"] == 8
     ctx.close()
