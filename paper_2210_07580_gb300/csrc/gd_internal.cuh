@@ -299,15 +299,6 @@ constexpr int kScanTile = 2048;
 // tmp: at least (total tiles + K) ints.
 cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st);
 
-// Zeroes int ranges: range k covers ptr[k][0 .. len[k]); off is the exclusive
-// prefix of len over the ranges (n_ranges + 1 entries).
-struct ZeroRange {
-    int* ptr;
-    long long len;
-    long long off;
-};
-cudaError_t zero_ranges(const ZeroRange* r, int n_ranges, long long total, cudaStream_t st);
-
 // Device-side flat offsets: off[0] = 0, off[k+1] = off[k] + small[slot] of
 // instance idx[k].
 cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st);

@@ -97,32 +97,6 @@ cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------- zero ranges
-
-__global__ void zero_ranges_kernel(const ZeroRange* __restrict__ r, int n_ranges, long long total) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_ranges - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (r[mid].off <= i)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        r[lo].ptr[i - r[lo].off] = 0;
-    }
-}
-
-cudaError_t zero_ranges(const ZeroRange* r, int n_ranges, long long total, cudaStream_t st) {
-    if (n_ranges <= 0 || total <= 0) return cudaSuccess;
-    long long b = (total + 255) / 256;
-    if (b > kPersistBlocks) b = kPersistBlocks;
-    zero_ranges_kernel<<<(int)b, 256, 0, st>>>(r, n_ranges, total);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------ flat offsets
 
 __global__ void count_flat_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int K, int slot,
