@@ -296,8 +296,12 @@ struct ScanSeg {
     long long blk0;
 };
 constexpr int kScanTile = 2048;
-// tmp: at least (total tiles + K) ints.
-cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st);
+// tmp: at least (total tiles + K) ints.  longest: the longest segment's
+// length if known (segments of at most kScanOneLaunch elements are scanned
+// by one block each in a single launch), else -1.
+constexpr long long kScanOneLaunch = 1 << 16;
+cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st,
+                          long long longest = -1);
 
 // Device-side flat offsets: off[0] = 0, off[k+1] = off[k] + small[slot] of
 // instance idx[k].

@@ -82,8 +82,42 @@ __global__ void __launch_bounds__(kScanBlock) seg_down_kernel(const ScanSeg* __r
     }
 }
 
-cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st) {
+// One block per segment scans it in chunks of 1024 x 8 elements, carrying the
+// running total (for short segments: one launch instead of three).
+constexpr int kScanOneItems = 8;
+__global__ void __launch_bounds__(1024) seg_single_kernel(const ScanSeg* __restrict__ segs) {
+    __shared__ int sm[33];
+    const ScanSeg sg = segs[blockIdx.x];
+    int carry = 0;
+    for (long long base = 0; base < sg.len; base += 1024 * kScanOneItems) {
+        const long long at = base + (long long)threadIdx.x * kScanOneItems;
+        int v[kScanOneItems];
+        int s = 0;
+#pragma unroll
+        for (int i = 0; i < kScanOneItems; ++i) {
+            v[i] = at + i < sg.len ? sg.in[at + i] : 0;
+            s += v[i];
+        }
+        int total;
+        int run = carry + block_exclusive_scan(s, sm, &total);
+#pragma unroll
+        for (int i = 0; i < kScanOneItems; ++i) {
+            if (at + i < sg.len) sg.out[at + i] = run;
+            run += v[i];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) sg.out[sg.len] = carry;
+}
+
+cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st,
+                          long long longest) {
     if (K <= 0) return cudaSuccess;
+    if (longest >= 0 && longest <= kScanOneLaunch) {
+        seg_single_kernel<<<K, 1024, 0, st>>>(segs);
+        GD_COUNT_LAUNCH();
+        return cudaGetLastError();
+    }
     if (total_tiles > 0) {
         seg_reduce_kernel<<<(unsigned)total_tiles, kScanBlock, 0, st>>>(segs, K, tmp);
         GD_COUNT_LAUNCH();

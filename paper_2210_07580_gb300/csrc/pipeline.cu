@@ -243,6 +243,7 @@ struct Run {
         b.overflow = false;
         // the Inst array always comes first
         dins = reinterpret_cast<Inst*>(b.dev + b.take(sizeof(Inst) * K));
+        seg_tabs = 0;
         all_idx = nullptr;
         return GD_OK;
     }
@@ -295,9 +296,14 @@ struct Run {
         return Flat{*off_dev, reinterpret_cast<const int*>(b.dev + at_idx), m};
     }
     // Segmented scans over one array per member instance.
+    // (longest segment of each table built since the descriptors were begun,
+    // so that scan() can pick the one-launch form for short segments)
+    const ScanSeg* seg_tab[64] = {};
+    long long seg_longest[64] = {};
+    int seg_tabs = 0;
     template <typename F> ScanSeg* segs(const int* members, int m, F arr, long long* tiles) {
         const size_t at = b.take(sizeof(ScanSeg) * (m > 0 ? m : 1));
-        long long blk = 0;
+        long long blk = 0, longest = 0;
         ScanSeg* h = reinterpret_cast<ScanSeg*>(b.host + at);
         for (int t = 0; t < m; ++t) {
             int* a = nullptr;
@@ -305,13 +311,22 @@ struct Run {
             arr(members[t], &a, &len);
             if (!b.overflow) h[t] = ScanSeg{a, a, len, blk};
             blk += (len + kScanTile - 1) / kScanTile;
+            if (len > longest) longest = len;
         }
         *tiles = blk;
-        return reinterpret_cast<ScanSeg*>(b.dev + at);
+        ScanSeg* dev = reinterpret_cast<ScanSeg*>(b.dev + at);
+        if (seg_tabs < 64) {
+            seg_tab[seg_tabs] = dev;
+            seg_longest[seg_tabs++] = longest;
+        }
+        return dev;
     }
     gd_status scan(const ScanSeg* sg, int m, long long tiles) {
         if (tiles + m > (long long)scan_tmp_ints) return fail(GD_ENOMEM, "scan scratch too small");
-        return cuda(scan_segments(sg, m, tiles, scan_tmp, st), "scan");
+        long long longest = -1;  // unknown: the three-launch form
+        for (int i = 0; i < seg_tabs; ++i)
+            if (seg_tab[i] == sg) longest = seg_longest[i];
+        return cuda(scan_segments(sg, m, tiles, scan_tmp, st, longest), "scan");
     }
     gd_status readback() {
         gd_status s = cuda(cudaMemcpyAsync(hsmall, dsmall, sizeof(int) * kSmallInts * K, cudaMemcpyDeviceToHost, st),
