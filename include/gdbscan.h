@@ -194,8 +194,10 @@ gd_status gd_get_knob(const gd_ctx *ctx, int knob, int d, int64_t n, int32_t *va
 
 /* CUDA graphs (no counterpart in the paper).  A call reads sizes back from
  * the device three times, which splits its launches into four phases.  With
- * graphs on, each phase's launches are captured from the call's stream into
- * a graph that the context keeps (one per phase): the next call updates it
+ * graphs on, the launches of the last three phases, after each phase's first
+ * long kernels (launched directly, so that the device works while the host
+ * captures), are captured from the call's stream into a graph that the
+ * context keeps (one per phase): the next call updates it
  * in place when only launch parameters differ (re-instantiating it when the
  * launch sequence differs) and launches the phase as one graph (calls of
  * fewer than 2^18 points in all run without graphs: re-capturing would cost

@@ -57,7 +57,7 @@ cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cuda
 // bounding box of each grid's core points by atomics: a warp whose 32 points
 // are all core points of one grid (the common case in dense data) reduces
 // them first and applies one atomic per bound.
-__global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+__global__ void __launch_bounds__(256, 6) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     const int lane = lane_id();
     const long long n_round = (total + 31) & ~31ll;
     FlatCursor cur;
@@ -73,10 +73,15 @@ __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__
             inst = f.idx[cur.k];
             I = ins + inst;
             const long long q = i - cur.lo;
+            const int dp = I->p.dp;
+            // the point's flag, grid and (padded-to-4) row are loaded together,
+            // before the loads that depend on the grid
             core = I->core_s[q] != 0;
+            c = I->pt_cell[q];
+            int4 v4 = make_int4(0, 0, 0, 0);
+            if (dp == 4) v4 = *reinterpret_cast<const int4*>(I->Xs + q * 4);
+            if (!core) c = -1;
             if (core) {
-                const int dp = I->p.dp;
-                c = I->pt_cell[q];
                 const int b = I->cell_start[c];
                 // a full grid's core rows are its rows in Xs (core_rows)
                 const bool full = I->cell_start[c + 1] - b >= I->p.minpts;
@@ -87,12 +92,11 @@ __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__
                     pos = I->core_start[c] + r;
                 }
                 if (dp == 4) {
-                    const int4 v = *reinterpret_cast<const int4*>(I->Xs + q * 4);
-                    if (!full) *reinterpret_cast<int4*>(I->Xc + pos * 4) = v;
-                    x[0] = v.x;
-                    x[1] = v.y;
-                    x[2] = v.z;
-                    x[3] = v.w;
+                    if (!full) *reinterpret_cast<int4*>(I->Xc + pos * 4) = v4;
+                    x[0] = v4.x;
+                    x[1] = v4.y;
+                    x[2] = v4.z;
+                    x[3] = v4.w;
                 } else {
 #pragma unroll
                     for (int j = 0; j < kMaxD; ++j)
@@ -117,7 +121,9 @@ __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__
             }
         } else if (core) {
             const int d = I->p.d;
-            for (int j = 0; j < d; ++j) {
+#pragma unroll
+            for (int j = 0; j < kMaxD; ++j) {
+                if (j >= d) break;
                 atomicMin(I->bbox + (long long)c * 2 * d + j, x[j]);
                 atomicMax(I->bbox + (long long)c * 2 * d + d + j, x[j]);
             }

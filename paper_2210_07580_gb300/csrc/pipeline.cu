@@ -143,6 +143,12 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
 }
 
 
+#define RUN_TRY_P(x)                  \
+    do {                              \
+        gd_status sp_ = (x);          \
+        if (sp_ != GD_OK) return sp_; \
+    } while (0)
+
 struct Run {
     MemProvider& mem;
     int K;
@@ -156,10 +162,13 @@ struct Run {
     long long total_points = 0;
     int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
 
-    // Runs the launches of phase `id` (body issues them on st): directly, or
-    // captured into the phase's executable graph and launched as one graph.
-    // A capture that fails is discarded and the launches are issued directly.
-    template <typename F> gd_status phase(int id, F&& body) {
+    // Runs the launches of phase `id`: head's directly, then body's either
+    // directly or captured into the phase's executable graph and launched as
+    // one graph.  The head (the phase's first long kernels) keeps the device
+    // busy while the host captures and updates the graph of the rest.  A
+    // capture that fails is discarded and the launches are issued directly.
+    template <typename H, typename F> gd_status phase(int id, H&& head, F&& body) {
+        RUN_TRY_P(head());
         // small batches re-capture more than they save in launches
         if (!graphs || !graphs->enabled || total_points < kGraphMinPoints) return body();
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -415,13 +424,11 @@ gd_status Run::go() {
         pts_d[d - 1] = flat(members2, m, n_of, &tot_d[d - 1]);
     }
     RUN_TRY(upload_desc());
-    RUN_TRY(phase(0, [&]() -> gd_status {
-        mark(0);
-        RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
-        for (int d = 1; d <= kMaxD; ++d) RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
-        mark(kStages + 1);
-        return GD_OK;
-    }));
+    // (one or a few launches: no graph)
+    mark(0);
+    RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
+    for (int d = 1; d <= kMaxD; ++d) RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
+    mark(kStages + 1);
     RUN_TRY(readback());
 
     // ------------------------- phase 2: keys, sort, compaction (sync 2)
@@ -512,6 +519,8 @@ gd_status Run::go() {
     RUN_TRY(phase(1, [&]() -> gd_status {
     mark(1);
     for (int w = 0; w < 3; ++w) RUN_CUDA(launch_quantise(dins, qflat[w], qtot[w], w, st), "quantise");
+    return GD_OK;
+    }, [&]() -> gd_status {
     mark(2);
     int pairs = 0;
     for (int w = 0; w < 3; ++w)
@@ -602,6 +611,8 @@ gd_status Run::go() {
     mark(4);
     RUN_CUDA(launch_point_boxes(dins, cells2, total_cells, st), "point boxes");
     RUN_CUDA(launch_level_diff(dins, cells2, total_cells, st), "levels");
+    return GD_OK;
+    }, [&]() -> gd_status {
     for (int j = 0; j + 1 < dmax; ++j) {
         RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
         RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
@@ -712,6 +723,8 @@ gd_status Run::go() {
         RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
     mark(6);
     RUN_CUDA(launch_core_full(dins, pts, total_pts, st), "core (full grids)");
+    return GD_OK;
+    }, [&]() -> gd_status {
     RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
     RUN_TRY(scan(nfseg.first, K, nfseg.second));
     RUN_CUDA(launch_totals(dins, idx, K, 2, st), "totals");

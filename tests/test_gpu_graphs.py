@@ -30,7 +30,7 @@ def test_graph_phases_match_direct_launches():
             np.testing.assert_array_equal(a[0], b[0])
             np.testing.assert_array_equal(a[1], b[1])
     st = graphed.graph_stats()
-    assert st["launches"] == 4 * 9 and st["instantiations"] >= 4 and st["updates"] > 0
+    assert st["launches"] == 3 * 9 and st["instantiations"] >= 3 and st["updates"] > 0
     # the same input again: every phase updates in place
     X, e, m = cases[0]
     Xd = torch.from_numpy(X).cuda()
@@ -39,7 +39,7 @@ def test_graph_phases_match_direct_launches():
     for _ in range(3):
         lab, core = graphed.dbscan(Xd, e, m)
     after = graphed.graph_stats()
-    assert after["updates"] - before["updates"] == 12 and after["instantiations"] == before["instantiations"]
+    assert after["updates"] - before["updates"] == 9 and after["instantiations"] == before["instantiations"]
     want = oracle.grid(X, e, m)
     np.testing.assert_array_equal(lab.cpu().numpy(), want[0])
     # stage timing still works inside graphs
@@ -71,5 +71,5 @@ def test_graph_phases_batched():
         for (a, ac), (b, bc) in zip(ref, got):
             np.testing.assert_array_equal(a, b)
             np.testing.assert_array_equal(ac, bc)
-    assert ctx.graph_stats()["launches"] == 8
+    assert ctx.graph_stats()["launches"] == 6
     ctx.close()
