@@ -381,7 +381,7 @@ cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limi
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
 cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Copies scan totals into the small blocks: nbr_start[C] -> kSmNnbr,

@@ -736,7 +736,8 @@ gd_status Run::go() {
     mark(7);
     RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
     RUN_TRY(scan(coreseg.first, K, coreseg.second));
-    RUN_CUDA(launch_core_pack(dins, pts, total_pts, st), "core pack");
+    for (int gi = 0; gi < ng; ++gi)
+        RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
     mark(8);
     RUN_CUDA(launch_pair_count(dins, cells, total_cells, st), "pair count");
     RUN_TRY(scan(ptseg.first, K, ptseg.second));
