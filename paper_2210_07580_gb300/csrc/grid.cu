@@ -158,7 +158,8 @@ cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long lo
 // instance and flushes with atomics when it moves to the next one (rare: only
 // at instance boundaries inside the chunk).  At the end, a warp whose lanes
 // all hold the same instance reduces with shuffles and applies one atomic per
-// dimension.  The small blocks' mnmx must hold INT_MAX / INT_MIN first.
+// dimension, and the block merges its warps' results before the atomics.
+// The small blocks' mnmx must hold INT_MAX / INT_MIN first.
 template <int D>
 __device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const int* mx) {
 #pragma unroll
@@ -169,8 +170,10 @@ __device__ __forceinline__ void bounds_flush(const Inst& I, const int* mn, const
 }
 
 // Over the instances of dimension D.
+constexpr int kBoundsWarps = 8;  // 256 threads
+
 template <int D>
-__global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+__global__ void __launch_bounds__(kBoundsWarps * 32) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     const long long per = (((total + nwarps - 1) / nwarps) + 31) & ~31ll;
@@ -219,17 +222,52 @@ __global__ void __launch_bounds__(256) bounds_kernel(const Inst* __restrict__ in
         }
         if (i >= stop && stop < end) i = stop + ((i - stop) & 31);
     }
+    // warp, then block: the atomics of a block's warps that hold one instance
+    // are merged, so that few atomics meet on the same addresses
+    __shared__ int s_k[kBoundsWarps], s_mn[kBoundsWarps][D], s_mx[kBoundsWarps][D];
+    const int w = threadIdx.x >> 5;
     const unsigned uniform = __match_any_sync(kFull, kk);
     if (uniform == kFull) {
-        if (kk < 0) return;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             mn[j] = __reduce_min_sync(kFull, mn[j]);
             mx[j] = __reduce_max_sync(kFull, mx[j]);
         }
-        if (lane_id() == 0) bounds_flush<D>(ins[kk], mn, mx);
-    } else if (kk >= 0) {
-        bounds_flush<D>(ins[kk], mn, mx);
+        if (lane_id() == 0) {
+            s_k[w] = kk;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                s_mn[w][j] = mn[j];
+                s_mx[w][j] = mx[j];
+            }
+        }
+    } else {
+        if (kk >= 0) bounds_flush<D>(ins[kk], mn, mx);
+        if (lane_id() == 0) s_k[w] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int k0 = -1;
+        for (int v = 0; v < kBoundsWarps; ++v) {
+            const int k = s_k[v];
+            if (k < 0) continue;
+            if (k != k0) {
+                if (k0 >= 0) bounds_flush<D>(ins[k0], mn, mx);
+                k0 = k;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    mn[j] = s_mn[v][j];
+                    mx[j] = s_mx[v][j];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    mn[j] = min(mn[j], s_mn[v][j]);
+                    mx[j] = max(mx[j], s_mx[v][j]);
+                }
+            }
+        }
+        if (k0 >= 0) bounds_flush<D>(ins[k0], mn, mx);
     }
 }
 
