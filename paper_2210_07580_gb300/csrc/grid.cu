@@ -372,6 +372,29 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
         fl[i] = q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb)));
         c += fl[i];
     }
+    // the items' source rows (random reads) are all requested before the
+    // block scan, so that their latency overlaps it
+    int src[kCompactItems];
+    int4 row4[kCompactItems];
+#pragma unroll
+    for (int i = 0; i < kCompactItems; ++i) {
+        const long long q = base + i;
+        src[i] = 0;
+        row4[i] = make_int4(0, 0, 0, 0);
+        if (q < n) {
+            if constexpr (PACKED)
+                src[i] = (int)(keys[q] & ((1ull << pb) - 1ull));
+            else
+                src[i] = vals[q];
+            if (dp == 4) {
+                const int* row = I.X + (long long)src[i] * d;
+                row4[i].x = __ldg(row);
+                if (d > 1) row4[i].y = __ldg(row + 1);
+                if (d > 2) row4[i].z = __ldg(row + 2);
+                if (d > 3) row4[i].w = __ldg(row + 3);
+            }
+        }
+    }
     int total;
     int cid = I.bcnt[tile] + block_exclusive_scan(c, sm, &total) - 1;
 #pragma unroll
@@ -386,22 +409,11 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
                 I.cell_coord[(long long)cid * d + j] = (int)key_field(key, I.p.shift[j], I.p.bits[j]);
         }
         I.pt_cell[q] = cid;
-        int src;
-        if constexpr (PACKED) {
-            src = (int)(keys[q] & ((1ull << pb) - 1ull));
-            vals[q] = src;
-        } else {
-            src = vals[q];
-        }
-        const int* row = I.X + (long long)src * d;
+        if constexpr (PACKED) vals[q] = src[i];
+        const int* row = I.X + (long long)src[i] * d;
         int* out = I.Xs + q * dp;
         if (dp == 4) {
-            int4 v;
-            v.x = __ldg(row);
-            v.y = d > 1 ? __ldg(row + 1) : 0;
-            v.z = d > 2 ? __ldg(row + 2) : 0;
-            v.w = d > 3 ? __ldg(row + 3) : 0;
-            *reinterpret_cast<int4*>(out) = v;
+            *reinterpret_cast<int4*>(out) = row4[i];
         } else {
             for (int j = 0; j < dp; ++j) out[j] = j < d ? __ldg(row + j) : 0;
         }
