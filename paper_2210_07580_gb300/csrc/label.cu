@@ -160,15 +160,33 @@ __global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ in
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     if (o[u] >= 0 && !core[u]) lab[u] = border_label<D>(I, i - cur.lo + 32 * u, c[u]);
+                // with core flags wanted: one packed word per point, split by
+                // label_split_kernel (half the scattered writes)
+                const bool packed = I.is_core != nullptr;
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (o[u] >= 0) {
-                        I.labels[o[u]] = lab[u];
-                        if (I.is_core) I.is_core[o[u]] = core[u];
-                    }
+                    if (o[u] >= 0)
+                        I.labels[o[u]] = packed ? (int)((unsigned)(lab[u] + 1) | ((unsigned)(core[u] != 0) << 31))
+                                                : lab[u];
             }
             if (i >= stop && stop < end) i = stop + ((i - stop) & 31);
         }
+    }
+}
+
+// Input order, instances that want core flags: the packed word (label + 1,
+// core flag in bit 31) in labels[] split into the label and the flag.
+// Coalesced reads and writes.
+__global__ void __launch_bounds__(256) label_split_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        if (!I.is_core) continue;
+        const long long q = i - cur.lo;
+        const unsigned v = (unsigned)I.labels[q];
+        I.labels[q] = (int)(v & 0x7fffffffu) - 1;
+        I.is_core[q] = (unsigned char)(v >> 31);
     }
 }
 
@@ -182,6 +200,8 @@ cudaError_t launch_labels(const Inst* ins, Flat pts, long long total, int d, cud
 #undef GD_LB
         default: return cudaErrorInvalidValue;
     }
+    GD_COUNT_LAUNCH();
+    label_split_kernel<<<nb, 256, 0, st>>>(ins, pts, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
