@@ -13,16 +13,35 @@ static int blocks_for(long long total) {
     return b < 1 ? 1 : (int)b;
 }
 
-__global__ void core_full_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+// Core flags of the points of full grids (1) and of the others (0, set by
+// core_point_kernel later).  Warps take chunks of 32 x kFullU consecutive
+// points, a lane's kFullU grid reads in flight together.
+constexpr int kFullU = 4;
+
+__global__ void __launch_bounds__(256) core_full_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     FlatCursor cur;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        cur.seek(f, i);
-        const int k = cur.k;
-        const Inst& I = ins[f.idx[k]];
-        const long long q = i - cur.lo;
-        const int c = I.pt_cell[q];
-        I.core_s[q] = (I.cell_start[c + 1] - I.cell_start[c]) >= I.p.minpts ? 1 : 0;
+    for (long long beg = wid * 32 * kFullU; beg < total; beg += nwarps * 32 * kFullU) {
+        int k[kFullU], c[kFullU];
+        long long q[kFullU];
+#pragma unroll
+        for (int u = 0; u < kFullU; ++u) {
+            const long long i = beg + 32 * u + lane_id();
+            k[u] = -1;
+            if (i < total) {
+                cur.seek(f, i);
+                k[u] = f.idx[cur.k];
+                q[u] = i - cur.lo;
+                c[u] = ins[k[u]].pt_cell[q[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kFullU; ++u)
+            if (k[u] >= 0) {
+                const Inst& I = ins[k[u]];
+                I.core_s[q[u]] = (I.cell_start[c[u] + 1] - I.cell_start[c[u]]) >= I.p.minpts ? 1 : 0;
+            }
     }
 }
 
@@ -42,7 +61,7 @@ __global__ void nonfull_count_kernel(const Inst* __restrict__ ins, Flat f, long 
 
 cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    core_full_kernel<<<blocks_for(total), 256, 0, st>>>(ins, pts, total);
+    core_full_kernel<<<blocks_for((total + kFullU - 1) / kFullU), 256, 0, st>>>(ins, pts, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

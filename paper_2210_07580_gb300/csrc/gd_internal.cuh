@@ -294,6 +294,7 @@ struct ScanSeg {
     int* out;
     long long len;
     long long blk0;
+    int* tot;  // also receives the segment's total (out[len]), if not null
 };
 constexpr int kScanTile = 2048;
 // tmp: at least (total tiles + K) ints.  longest: the longest segment's
@@ -384,11 +385,6 @@ cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cuda
 cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
 cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-// Copies scan totals into the small blocks: nbr_start[C] -> kSmNnbr,
-// nf_start[C] -> kSmNonfull, pair_start[C] / pair_start_f[C] -> kSmPairsT /
-// kSmPairsF (for the bits of `which`: 1, 2, 4) and, with 4, resets the hard
-// counters.
-cudaError_t launch_totals(const Inst* ins, const int* idx, int K, int which, cudaStream_t st);
 cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Warp-level test of the candidate pairs of one wave (0: touching, 1: others)

@@ -57,7 +57,10 @@ __global__ void __launch_bounds__(1024) seg_top_kernel(const ScanSeg* __restrict
         if (k < end) bsum[k] = carry + ex;
         carry += total;
     }
-    if (threadIdx.x == 0) sg.out[sg.len] = carry;
+    if (threadIdx.x == 0) {
+        sg.out[sg.len] = carry;
+        if (sg.tot) *sg.tot = carry;
+    }
 }
 
 __global__ void __launch_bounds__(kScanBlock) seg_down_kernel(const ScanSeg* __restrict__ segs, int K,
@@ -107,7 +110,10 @@ __global__ void __launch_bounds__(1024) seg_single_kernel(const ScanSeg* __restr
         }
         carry += total;
     }
-    if (threadIdx.x == 0) sg.out[sg.len] = carry;
+    if (threadIdx.x == 0) {
+        sg.out[sg.len] = carry;
+        if (sg.tot) *sg.tot = carry;
+    }
 }
 
 cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int* tmp, cudaStream_t st,
@@ -450,21 +456,31 @@ cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, i
 
 // Largest grid of each instance (bounds the merge's bitmaps).  The flat
 // space is the instances' points, an upper bound of their grids: a warp-sized
-// grid-stride loop visits only c < C (read on the device), reduces the sizes
-// in the warp and applies one atomic.  small[kSmMaxCell] must be 0 first.
+// grid-stride loop reads the sizes of grids c < C (C read on the device) and
+// steps over the rest of an instance, reduces the sizes in the warp and
+// applies one atomic.  small[kSmMaxCell] must be 0 first.
 __global__ void cell_max_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     FlatCursor cur;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;) {
         const long long i = base + lane_id();
         int kk = -1, size = 0;
+        long long past = -1;  // end of this lane's instance once its grids are behind
         if (i < total) {
             cur.seek(f, i);
             kk = f.idx[cur.k];
             const Inst& I = ins[kk];
             const long long c = i - cur.lo;
-            if (c < I.small[kSmCells]) size = I.cell_start[c + 1] - I.cell_start[c];
+            if (c < I.small[kSmCells])
+                size = I.cell_start[c + 1] - I.cell_start[c];
+            else
+                past = cur.hi;
         }
+        // the next position of this warp's stride, past the rest of lane 0's
+        // instance when lane 0 is already beyond that instance's grids
+        long long next = base + stride;
+        const long long hi0 = __shfl_sync(kFull, past, 0);
+        if (hi0 > next) next += (hi0 - next + stride - 1) / stride * stride;
         const int k0 = __shfl_sync(kFull, kk, 0);
         if (__all_sync(kFull, kk == k0)) {
             const int m = __reduce_max_sync(kFull, (unsigned)size);
@@ -472,6 +488,7 @@ __global__ void cell_max_kernel(const Inst* __restrict__ ins, Flat f, long long 
         } else if (kk >= 0 && size > 0) {
             atomicMax(ins[kk].small + kSmMaxCell, size);
         }
+        base = next;
     }
 }
 

@@ -263,28 +263,6 @@ cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaS
     return cudaGetLastError();
 }
 
-__global__ void totals_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int K, int which) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    const Inst& I = ins[idx[k]];
-    const int C = I.small[kSmCells];
-    if (which & 1) I.small[kSmNnbr] = I.nbr_start[C];
-    if (which & 2) I.small[kSmNonfull] = I.nf_start[C];
-    if (which & 4) {
-        I.small[kSmPairsT] = I.pair_start[C];
-        I.small[kSmPairsF] = I.pair_start_f[C];
-        I.small[kSmHard0] = 0;
-        I.small[kSmHard1] = 0;
-    }
-}
-
-cudaError_t launch_totals(const Inst* ins, const int* idx, int K, int which, cudaStream_t st) {
-    if (K <= 0) return cudaSuccess;
-    totals_kernel<<<(K + 127) / 128, 128, 0, st>>>(ins, idx, K, which);
-    GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------ union-find
 // Of two roots, the one with the lower priority is linked under the other
 // (atomicCAS on the root), and finds halve paths with plain stores: every

@@ -310,7 +310,9 @@ struct Run {
     const ScanSeg* seg_tab[64] = {};
     long long seg_longest[64] = {};
     int seg_tabs = 0;
-    template <typename F> ScanSeg* segs(const int* members, int m, F arr, long long* tiles) {
+    // tot_slot >= 0: each segment's total also goes to that slot of its
+    // instance's small block (read back with it).
+    template <typename F> ScanSeg* segs(const int* members, int m, F arr, long long* tiles, int tot_slot = -1) {
         const size_t at = b.take(sizeof(ScanSeg) * (m > 0 ? m : 1));
         long long blk = 0, longest = 0;
         ScanSeg* h = reinterpret_cast<ScanSeg*>(b.host + at);
@@ -318,7 +320,8 @@ struct Run {
             int* a = nullptr;
             long long len = 0;
             arr(members[t], &a, &len);
-            if (!b.overflow) h[t] = ScanSeg{a, a, len, blk};
+            int* tot = tot_slot >= 0 ? dsmall + (size_t)members[t] * kSmallInts + tot_slot : nullptr;
+            if (!b.overflow) h[t] = ScanSeg{a, a, len, blk, tot};
             blk += (len + kScanTile - 1) / kScanTile;
             if (len > longest) longest = len;
         }
@@ -588,7 +591,7 @@ gd_status Run::go() {
             *a = hi[k].dev.nbr_start;
             *len = hi[k].C;
         },
-        &nseg_tiles);
+        &nseg_tiles, kSmNnbr);
     idx = idx_all();
     RUN_TRY(upload_desc());
 
@@ -622,7 +625,6 @@ gd_status Run::go() {
     RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
              "walk");
     RUN_TRY(scan(nseg, K, nseg_tiles));
-    RUN_CUDA(launch_totals(dins, idx, K, 1, st), "totals");
     mark(kStages + 3);
     return GD_OK;
     }));
@@ -698,7 +700,7 @@ gd_status Run::go() {
             g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
         }
     }
-    auto arr_seg = [&](int* Inst::*field) {
+    auto arr_seg = [&](int* Inst::*field, int tot_slot) {
         long long tiles = 0;
         const ScanSeg* sgp = segs(
             members, K,
@@ -706,13 +708,13 @@ gd_status Run::go() {
                 *a = hi[k].dev.*field;
                 *len = hi[k].C;
             },
-            &tiles);
+            &tiles, tot_slot);
         return std::make_pair(sgp, tiles);
     };
-    const auto nfseg = arr_seg(&Inst::nf_start);
-    const auto coreseg = arr_seg(&Inst::core_start);
-    const auto ptseg = arr_seg(&Inst::pair_start);
-    const auto pfseg = arr_seg(&Inst::pair_start_f);
+    const auto nfseg = arr_seg(&Inst::nf_start, kSmNonfull);
+    const auto coreseg = arr_seg(&Inst::core_start, -1);
+    const auto ptseg = arr_seg(&Inst::pair_start, kSmPairsT);
+    const auto pfseg = arr_seg(&Inst::pair_start_f, kSmPairsF);
     idx = idx_all();
     RUN_TRY(upload_desc());
 
@@ -727,7 +729,6 @@ gd_status Run::go() {
     }, [&]() -> gd_status {
     RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
     RUN_TRY(scan(nfseg.first, K, nfseg.second));
-    RUN_CUDA(launch_totals(dins, idx, K, 2, st), "totals");
     for (int gi = 0; gi < ng; ++gi) {
         RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
         RUN_CUDA(launch_core_point(dins, g_nf[gi], dgroups[gi], knob(GD_KNOB_CORE_BANDS, dgroups[gi], gn[gi]), st),
@@ -743,7 +744,6 @@ gd_status Run::go() {
     RUN_TRY(scan(ptseg.first, K, ptseg.second));
     RUN_TRY(scan(pfseg.first, K, pfseg.second));
     RUN_CUDA(launch_pair_fill(dins, cells, total_cells, st), "pair fill");
-    RUN_CUDA(launch_totals(dins, idx, K, 4, st), "totals");
     mark(9);
     RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
     for (int w = 0; w < 2; ++w) {

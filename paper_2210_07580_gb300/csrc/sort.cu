@@ -181,9 +181,18 @@ __global__ void __launch_bounds__(kOsBlock) upsweep_kernel(const Inst* __restric
     const long long base = (long long)tile * kTile;
     const int count = (int)min((long long)kTile, (long long)I.p.n - base);
     const int lane = lane_id();
-    for (int t = threadIdx.x; t < kTile; t += kOsBlock) {
-        const bool valid = t < count;
-        const unsigned dg = valid ? SortKey<K>::digit(keys[base + t], shift, mask) : (unsigned)R + lane;
+    // all of the thread's digits first (their loads in flight together)
+    constexpr int kItems = kTile / kOsBlock;
+    unsigned dgs[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+        const int t = u * kOsBlock + threadIdx.x;
+        dgs[u] = t < count ? SortKey<K>::digit(keys[base + t], shift, mask) : (unsigned)R + lane;
+    }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+        const bool valid = u * kOsBlock + (int)threadIdx.x < count;
+        const unsigned dg = dgs[u];
         const unsigned prev = __shfl_up_sync(kFull, dg, 1);
         const bool start = lane == 0 || dg != prev;
         const unsigned starts = __ballot_sync(kFull, start);
