@@ -14,34 +14,47 @@ static int blocks_for(long long total) {
 }
 
 // Core flags of the points of full grids (1) and of the others (0, set by
-// core_point_kernel later).  Warps take chunks of 32 x kFullU consecutive
-// points, a lane's kFullU grid reads in flight together.
-constexpr int kFullU = 4;
+// core_point_kernel later).  A grid's points are contiguous in sorted order:
+// a lane takes a grid and fills the range of a small one itself, while the
+// warp fills the ranges of its lanes' large grids together, one after the
+// other, with 16-byte stores between the unaligned ends.
+constexpr int kFillLane = 64;  // largest grid a lane fills alone
 
 __global__ void __launch_bounds__(256) core_full_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
+    const int lane = lane_id();
+    const long long stride = (long long)gridDim.x * blockDim.x;
     FlatCursor cur;
-    for (long long beg = wid * 32 * kFullU; beg < total; beg += nwarps * 32 * kFullU) {
-        int k[kFullU], c[kFullU];
-        long long q[kFullU];
-#pragma unroll
-        for (int u = 0; u < kFullU; ++u) {
-            const long long i = beg + 32 * u + lane_id();
-            k[u] = -1;
-            if (i < total) {
-                cur.seek(f, i);
-                k[u] = f.idx[cur.k];
-                q[u] = i - cur.lo;
-                c[u] = ins[k[u]].pt_cell[q[u]];
-            }
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const long long w = base + lane;
+        long long b = 0, e = 0;
+        unsigned char v = 0;
+        const Inst* I = nullptr;
+        if (w < total) {
+            cur.seek(f, w);
+            I = ins + f.idx[cur.k];
+            const long long c = w - cur.lo;
+            b = I->cell_start[c];
+            e = I->cell_start[c + 1];
+            v = e - b >= I->p.minpts ? 1 : 0;
+            if (e - b <= kFillLane)
+                for (long long q = b; q < e; ++q) I->core_s[q] = v;
         }
-#pragma unroll
-        for (int u = 0; u < kFullU; ++u)
-            if (k[u] >= 0) {
-                const Inst& I = ins[k[u]];
-                I.core_s[q[u]] = (I.cell_start[c[u] + 1] - I.cell_start[c[u]]) >= I.p.minpts ? 1 : 0;
-            }
+        unsigned big = __ballot_sync(kFull, e - b > kFillLane);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const long long bb = __shfl_sync(kFull, b, src), ee = __shfl_sync(kFull, e, src);
+            const unsigned char vv = (unsigned char)__shfl_sync(kFull, (int)v, src);
+            unsigned char* p = reinterpret_cast<unsigned char*>(__shfl_sync(kFull, (unsigned long long)(size_t)(I ? I->core_s : nullptr), src));
+            const unsigned long long A = (unsigned long long)(size_t)p;
+            const long long a0 = min(ee, bb + (long long)((16 - (A + bb) % 16) % 16));
+            const long long a1 = max(a0, ee - (long long)((A + ee) % 16));
+            for (long long q = bb + lane; q < a0; q += 32) p[q] = vv;
+            const unsigned wv = vv ? 0x01010101u : 0u;
+            const uint4 word = make_uint4(wv, wv, wv, wv);
+            for (long long q = a0 + 16ll * lane; q < a1; q += 16 * 32) *reinterpret_cast<uint4*>(p + q) = word;
+            for (long long q = a1 + lane; q < ee; q += 32) p[q] = vv;
+        }
     }
 }
 
@@ -59,9 +72,9 @@ __global__ void nonfull_count_kernel(const Inst* __restrict__ ins, Flat f, long 
     }
 }
 
-cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st) {
+cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    core_full_kernel<<<blocks_for((total + kFullU - 1) / kFullU), 256, 0, st>>>(ins, pts, total);
+    core_full_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

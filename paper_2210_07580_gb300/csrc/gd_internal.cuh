@@ -375,7 +375,7 @@ cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, 
 cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st);
 
 // Core points (core.cu).
-cudaError_t launch_core_full(const Inst* ins, Flat pts, long long total, cudaStream_t st);
+cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Non-full points of instances with dimension d (flat offsets on the device).
 cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limit, cudaStream_t st);

@@ -724,7 +724,7 @@ gd_status Run::go() {
     else
         RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
     mark(6);
-    RUN_CUDA(launch_core_full(dins, pts, total_pts, st), "core (full grids)");
+    RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
     return GD_OK;
     }, [&]() -> gd_status {
     RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
