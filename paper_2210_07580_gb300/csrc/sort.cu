@@ -315,12 +315,23 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
             if constexpr (!PACKED) val[i] = vals_in[base + t];
         }
     }
+    const int bits = I.digit_bits;
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         const int t = wbase + i * 32 + lane;
         const bool valid = t < count;
         const unsigned dg = valid ? SortKey<K>::digit(key[i], shift, mask) : (unsigned)R + lane;
-        const unsigned peers = __match_any_sync(kFull, dg);
+        // lanes with the same digit: one ballot per digit bit (a constant
+        // cost, where a match instruction's grows with the distinct digits)
+        unsigned peers = __ballot_sync(kFull, valid);
+        if (!valid) peers = 1u << lane;
+#pragma unroll
+        for (int b = 0; b < kMaxDigitBits; ++b) {
+            if (b >= bits) break;
+            const bool on = (dg >> b) & 1u;
+            const unsigned bal = __ballot_sync(kFull, on);
+            peers &= on ? bal : ~bal;
+        }
         int before = 0;
         if (valid) before = wcount[warp * R + dg];
         __syncwarp();
