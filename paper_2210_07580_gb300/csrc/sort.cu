@@ -15,6 +15,7 @@
 // values): a pass then moves 8 bytes per point each way, not 12, and since
 // the passes are stable and look only at key digits, the order is the same.
 #include <atomic>
+#include <type_traits>
 
 #include "gd_internal.cuh"
 
@@ -301,106 +302,115 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
     const long long base = (long long)tile * kTile;
     const int count = (int)min((long long)kTile, (long long)n - base);
 
-    // Warp w owns items [w*32*kItems, (w+1)*32*kItems) of the tile in index
-    // order; item i of lane l is at w*32*kItems + i*32 + l.
-    K key[kItems];
-    int val[kItems];
-    int rk[kItems];  // rank within the warp (low 16 bits) | digit << 16
-    const int wbase = warp * 32 * kItems;
+    // Full tiles (all but an instance's last) run a copy of the body in which
+    // every bound check is known to hold.
+    auto run = [&](auto full) {
+        const int cnt = decltype(full)::value ? kTile : count;
+        // Warp w owns items [w*32*kItems, (w+1)*32*kItems) of the tile in index
+        // order; item i of lane l is at w*32*kItems + i*32 + l.
+        K key[kItems];
+        int val[kItems];
+        int rk[kItems];  // rank within the warp (low 16 bits) | digit << 16
+        const int wbase = warp * 32 * kItems;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        if (t < count) {
-            key[i] = keys_in[base + t];
-            if constexpr (!PACKED) val[i] = vals_in[base + t];
-        }
-    }
-    const int bits = I.digit_bits;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        const bool valid = t < count;
-        const unsigned dg = valid ? SortKey<K>::digit(key[i], shift, mask) : (unsigned)R + lane;
-        // lanes with the same digit: one ballot per digit bit (a constant
-        // cost, where a match instruction's grows with the distinct digits)
-        unsigned peers = __ballot_sync(kFull, valid);
-        if (!valid) peers = 1u << lane;
-#pragma unroll
-        for (int b = 0; b < kMaxDigitBits; ++b) {
-            if (b >= bits) break;
-            const bool on = (dg >> b) & 1u;
-            const unsigned bal = __ballot_sync(kFull, on);
-            peers &= on ? bal : ~bal;
-        }
-        int before = 0;
-        if (valid) before = wcount[warp * R + dg];
-        __syncwarp();
-        if (valid && lane == (int)(__ffs(peers) - 1)) wcount[warp * R + dg] = before + __popc(peers);
-        __syncwarp();
-        rk[i] = (before + __popc(peers & lanemask_lt())) | (int)(dg << 16);
-    }
-    __syncthreads();
-
-    // per digit: exclusive prefix over warps; then the exclusive prefix over
-    // digits (local start of each digit run).  Thread t owns the `per`
-    // consecutive digits starting at t * per.
-    {
-        const int per = (R + kOsBlock - 1) / kOsBlock;  // 1 or 2 (R <= 512)
-        constexpr int kPerMax = (kMaxBuckets + kOsBlock - 1) / kOsBlock;
-        int tots[kPerMax];
-        int sum = 0;
-#pragma unroll
-        for (int u = 0; u < kPerMax; ++u) {
-            tots[u] = 0;
-            const int b = threadIdx.x * per + u;
-            if (u < per && b < R) {
-                int tot = 0;
-#pragma unroll
-                for (int w = 0; w < kOsWarps; ++w) {
-                    const int c = wcount[w * R + b];
-                    wcount[w * R + b] = tot;
-                    tot += c;
-                }
-                tots[u] = tot;
-                sum += tot;
+        for (int i = 0; i < kItems; ++i) {
+            const int t = wbase + i * 32 + lane;
+            if (t < cnt) {
+                key[i] = keys_in[base + t];
+                if constexpr (!PACKED) val[i] = vals_in[base + t];
             }
         }
-        int all;
-        int ex = block_exclusive_scan(sum, sm, &all);
+        const int bits = I.digit_bits;
 #pragma unroll
-        for (int u = 0; u < kPerMax; ++u) {
-            const int b = threadIdx.x * per + u;
-            if (u < per && b < R) {
-                ldstart[b] = ex;
-                ex += tots[u];
+        for (int i = 0; i < kItems; ++i) {
+            const int t = wbase + i * 32 + lane;
+            const bool valid = t < cnt;
+            const unsigned dg = valid ? SortKey<K>::digit(key[i], shift, mask) : (unsigned)R + lane;
+            // lanes with the same digit: one ballot per digit bit (a constant
+            // cost, where a match instruction's grows with the distinct digits)
+            unsigned peers = cnt == kTile ? kFull : __ballot_sync(kFull, valid);
+            if (!valid) peers = 1u << lane;
+#pragma unroll
+            for (int b = 0; b < kMaxDigitBits; ++b) {
+                if (b >= bits) break;
+                const bool on = (dg >> b) & 1u;
+                const unsigned bal = __ballot_sync(kFull, on);
+                peers &= on ? bal : ~bal;
+            }
+            int before = 0;
+            if (valid) before = wcount[warp * R + dg];
+            __syncwarp();
+            if (valid && lane == (int)(__ffs(peers) - 1)) wcount[warp * R + dg] = before + __popc(peers);
+            __syncwarp();
+            rk[i] = (before + __popc(peers & lanemask_lt())) | (int)(dg << 16);
+        }
+        __syncthreads();
+
+        // per digit: exclusive prefix over warps; then the exclusive prefix over
+        // digits (local start of each digit run).  Thread t owns the `per`
+        // consecutive digits starting at t * per.
+        {
+            const int per = (R + kOsBlock - 1) / kOsBlock;  // 1 or 2 (R <= 512)
+            constexpr int kPerMax = (kMaxBuckets + kOsBlock - 1) / kOsBlock;
+            int tots[kPerMax];
+            int sum = 0;
+#pragma unroll
+            for (int u = 0; u < kPerMax; ++u) {
+                tots[u] = 0;
+                const int b = threadIdx.x * per + u;
+                if (u < per && b < R) {
+                    int tot = 0;
+#pragma unroll
+                    for (int w = 0; w < kOsWarps; ++w) {
+                        const int c = wcount[w * R + b];
+                        wcount[w * R + b] = tot;
+                        tot += c;
+                    }
+                    tots[u] = tot;
+                    sum += tot;
+                }
+            }
+            int all;
+            int ex = block_exclusive_scan(sum, sm, &all);
+#pragma unroll
+            for (int u = 0; u < kPerMax; ++u) {
+                const int b = threadIdx.x * per + u;
+                if (u < per && b < R) {
+                    ldstart[b] = ex;
+                    ex += tots[u];
+                }
+            }
+            __syncthreads();
+        }
+
+        // keys and values into tile-local digit order through shared memory
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int t = wbase + i * 32 + lane;
+            if (t < cnt) {
+                const int dg = rk[i] >> 16;
+                const int pos = ldstart[dg] + wcount[warp * R + dg] + (rk[i] & 0xffff);
+                skeys[pos] = key[i];
+                if constexpr (!PACKED) svals[pos] = val[i];
             }
         }
         __syncthreads();
-    }
-
-    // keys and values into tile-local digit order through shared memory
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = wbase + i * 32 + lane;
-        if (t < count) {
-            const int dg = rk[i] >> 16;
-            const int pos = ldstart[dg] + wcount[warp * R + dg] + (rk[i] & 0xffff);
-            skeys[pos] = key[i];
-            if constexpr (!PACKED) svals[pos] = val[i];
+        for (int i = 0; i < kItems; ++i) {
+            const int t = i * kOsBlock + threadIdx.x;
+            if (t < cnt) {
+                const K k2 = skeys[t];
+                const unsigned dg = SortKey<K>::digit(k2, shift, mask);
+                const int dst = goff[dg] + (t - ldstart[dg]);
+                keys_out[dst] = k2;
+                if constexpr (!PACKED) vals_out[dst] = svals[t];
+            }
         }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int t = i * kOsBlock + threadIdx.x;
-        if (t < count) {
-            const K k2 = skeys[t];
-            const unsigned dg = SortKey<K>::digit(k2, shift, mask);
-            const int dst = goff[dg] + (t - ldstart[dg]);
-            keys_out[dst] = k2;
-            if constexpr (!PACKED) vals_out[dst] = svals[t];
-        }
-    }
+    };
+    if (count == kTile)
+        run(std::true_type{});
+    else
+        run(std::false_type{});
 }
 
 template <typename K, bool PACKED> static size_t downsweep_smem(int R) {

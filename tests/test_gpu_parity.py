@@ -361,3 +361,43 @@ def test_batched_mixed_key_widths_and_tiny(ctx):
     torch.cuda.synchronize()
     for i, ((X, e, m), (lab, core)) in enumerate(zip(jobs, res)):
         assert_same((lab.cpu().numpy(), core.cpu().numpy()), oracle.grid(X, e, m), f"mixed instance {i}")
+
+
+def test_labels_without_core_flags(ctx):
+    """is_core may be NULL: labels only, alone and in a batch that mixes
+    instances with and without core flags (labels are then written directly,
+    with flags as one packed word split afterwards)."""
+    rng = np.random.default_rng(12)
+    jobs = [
+        (rand_points(rng, 6000, 3, 4000), 90 ** 2, 6),
+        (rand_points(rng, 3000, 2, 2000), 60 ** 2, 4),
+        (rand_points(rng, 5000, 5, 3000), 400 ** 2, 5),
+    ]
+    want = [oracle.grid(X, e, m) for X, e, m in jobs]
+    # single instance through the raw entry point
+    X, e, m = jobs[0]
+    Xd = torch.from_numpy(X).cuda()
+    lab = torch.full((len(X),), -7, dtype=torch.int32, device="cuda")
+    ctx._check(ctx._lib.gd_dbscan(ctx._h, Xd.data_ptr(), len(X), X.shape[1], e, m, lab.data_ptr(), None,
+                                  binding._stream_handle(None)))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lab.cpu().numpy(), want[0][0])
+    # batch: core flags for the middle instance only
+    arr = (binding.GdInstance * len(jobs))()
+    keep, outs = [], []
+    for i, (X, e, m) in enumerate(jobs):
+        Xd = torch.from_numpy(X).cuda()
+        lab = torch.full((len(X),), -7, dtype=torch.int32, device="cuda")
+        core = torch.full((len(X),), 7, dtype=torch.uint8, device="cuda") if i == 1 else None
+        keep.append(Xd)
+        outs.append((lab, core))
+        arr[i] = binding.GdInstance(Xd.data_ptr(), len(X), X.shape[1], e, m, lab.data_ptr(),
+                                    core.data_ptr() if core is not None else None)
+    ctx._check(ctx._lib.gd_dbscan_batched(ctx._h, len(jobs), binding.ctypes.cast(arr, binding.ctypes.c_void_p),
+                                          binding._stream_handle(None)))
+    torch.cuda.synchronize()
+    for i, ((lab, core), (wl, wc)) in enumerate(zip(outs, want)):
+        np.testing.assert_array_equal(lab.cpu().numpy(), wl, err_msg=f"instance {i}")
+        if core is not None:
+            np.testing.assert_array_equal(core.cpu().numpy().astype(bool), wc.astype(bool),
+                                          err_msg=f"instance {i} core")
