@@ -326,8 +326,8 @@ struct SortPlan {
     int tiles;
 };
 SortPlan sort_plan(int n, int key_words, int key_bits);
-// ints of workspace for one instance's sort (histograms, tile counters,
-// look-back status); layout in sort.cu.
+// ints of workspace for one instance's sort (tile histograms, digit totals
+// and starts); layout in sort.cu.
 size_t sort_tmp_ints(int n, int key_words, int key_bits);
 void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** dtot, int** dstart);
 constexpr int kQuantTile = 4096;  // points per quantise block

@@ -67,11 +67,12 @@ struct Tuning {
 int knob_default(int knob);
 bool knob_in_range(int knob, int value);
 
-// Executable graphs of the driver's four launch phases (the work between two
-// reads of sizes), one per phase, kept by a context between calls.  Each call
-// captures a phase's launches from its stream and updates the executable
-// graph in place when only parameters changed (re-instantiating it when the
-// launch sequence changed), then launches it.
+// Executable graphs of the driver's launch phases (the work between two reads
+// of sizes), one per phase, kept by a context between calls.  The first phase
+// (bounds) is not captured; each later call launches a phase's first long
+// kernels directly, captures the rest from its stream and updates the
+// executable graph in place when only parameters changed (re-instantiating
+// it when the launch sequence changed), then launches it.
 // Calls with fewer points in all run without graphs.
 constexpr long long kGraphMinPoints = 1 << 18;
 
