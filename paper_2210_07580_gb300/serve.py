@@ -60,6 +60,31 @@ def estimate_footprint(n: int, d: int, workspace_bytes) -> int:
     return int(workspace_bytes(n, d)) + n * (4 * d + 5) + n * 64 * 20 // 4
 
 
+def stage_in(hin, jobs, offsets) -> None:
+    """Copy the jobs' points (int32 rows) into the byte tensor `hin` at the
+    given byte offsets.  torch copies release the GIL, so the staging of
+    several slots' threads overlaps."""
+    import torch
+    for j, o in zip(jobs, offsets):
+        src = torch.from_numpy(np.ascontiguousarray(j.X, dtype=np.int32).reshape(-1).view(np.uint8))
+        hin[o:o + src.numel()].copy_(src)
+
+
+def stage_out(hout, jobs, offsets, align: int) -> list:
+    """Each job's (labels int32 [n], core flags bool [n]) from the byte tensor
+    `hout`: labels at the job's offset, flags at the next multiple of `align`
+    after them.  Copies out of `hout` (torch, GIL released)."""
+    import torch
+    res = []
+    for j, oo in zip(jobs, offsets):
+        n = j.n
+        fo = oo + (4 * n + align - 1) // align * align
+        lab = hout[oo:oo + 4 * n].view(torch.int32).clone().numpy()
+        core = hout[fo:fo + n].to(torch.bool).numpy()
+        res.append((lab, core))
+    return res
+
+
 class GpuBackend:
     """Runs jobs through the C ABI: one Context and one CUDA stream per slot.
     Each slot keeps grow-only staging buffers: pinned host memory for the
@@ -112,9 +137,7 @@ class GpuBackend:
             hout = self._buf(slot, "hout", tout, True)
             din = self._buf(slot, "din", tin, False)
             dout = self._buf(slot, "dout", tout, False)
-            hin_np = hin.numpy()
-            for j, o in zip(jobs, in_off):
-                hin_np[o:o + j.X.nbytes] = j.X.reshape(-1).view(np.uint8)
+            stage_in(hin, jobs, in_off)
             din[:tin].copy_(hin[:tin], non_blocking=True)
             dev, outs = [], []
             for j, oi, oo in zip(jobs, in_off, out_off):
@@ -138,14 +161,7 @@ class GpuBackend:
                     gate.release()
             hout[:tout].copy_(dout[:tout], non_blocking=True)
             stream.synchronize()
-        hout_np = hout.numpy()
-        res = []
-        for j, oo in zip(jobs, out_off):
-            n = j.n
-            lab = hout_np[oo:oo + 4 * n].view(np.int32).copy()
-            core = hout_np[oo + up(4 * n):oo + up(4 * n) + n].astype(bool)
-            res.append((lab, core))
-        return res
+        return stage_out(hout, jobs, out_off, al)
 
     def close(self):
         for c in self.ctxs:

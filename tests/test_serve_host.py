@@ -124,3 +124,40 @@ def test_large_jobs_never_overlap_and_small_ones_keep_flowing():
         big_done_at = time.perf_counter()
     assert fb.max_large_now == 1
     assert small_done_at < big_done_at, "small jobs waited behind the large ones"
+
+
+def test_staging_round_trip():
+    """GpuBackend's host staging: rows in at aligned byte offsets, labels and
+    core flags out of the result buffer."""
+    torch = pytest.importorskip("torch")
+    from paper_2210_07580_gb300.serve import Job, stage_in, stage_out
+    rng = np.random.default_rng(3)
+    jobs = [Job(rng.integers(-10**6, 10**6, size=(n, d)).astype(np.int32), 1, 1, 0, 0.0)
+            for n, d in ((1, 3), (257, 5), (1000, 2))]
+    al = 256
+    up = lambda v: (v + al - 1) // al * al  # noqa: E731
+    in_off, out_off, tin, tout = [], [], 0, 0
+    for j in jobs:
+        in_off.append(tin)
+        tin += up(j.X.nbytes)
+        out_off.append(tout)
+        tout += up(4 * j.n) + up(j.n)
+    hin = torch.zeros(tin, dtype=torch.uint8)
+    stage_in(hin, jobs, in_off)
+    for j, o in zip(jobs, in_off):
+        got = hin[o:o + j.X.nbytes].numpy().view(np.int32).reshape(j.X.shape)
+        np.testing.assert_array_equal(got, j.X)
+    hout = torch.zeros(tout, dtype=torch.uint8)
+    want = []
+    for j, o in zip(jobs, out_off):
+        lab = rng.integers(-1, j.n, size=j.n).astype(np.int32)
+        core = rng.integers(0, 2, size=j.n).astype(np.uint8)
+        hout[o:o + 4 * j.n] = torch.from_numpy(lab.view(np.uint8))
+        hout[o + up(4 * j.n):o + up(4 * j.n) + j.n] = torch.from_numpy(core)
+        want.append((lab, core.astype(bool)))
+    got = stage_out(hout, jobs, out_off, al)
+    hout.fill_(0)  # the results are copies
+    for (gl, gc), (wl, wc) in zip(got, want):
+        assert gl.dtype == np.int32 and gc.dtype == bool
+        np.testing.assert_array_equal(gl, wl)
+        np.testing.assert_array_equal(gc, wc)
