@@ -74,7 +74,9 @@ void gd_destroy(gd_ctx *ctx);
 size_t gd_workspace_bytes(int64_t n, int d);
 
 /* Exact DBSCAN of the device-resident points X (Section 4.4, Alg. 6).
- * X, labels and is_core are device pointers (is_core may be NULL).  Work is
+ * X, labels and is_core are device pointers (is_core may be NULL); labels and
+ * is_core must not overlap each other or X (labels also serves as scratch
+ * during the call; its contents are final when the call returns).  Work is
  * issued on `stream`; the call returns after the result is complete on that
  * stream (it synchronises with it to size data-dependent buffers).  n == 0 is
  * a no-op returning GD_OK. */
