@@ -242,22 +242,27 @@ int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
  * exhausted.  gd_dbscan_noalloc serves them for small inputs.  It needs no
  * gd_ctx and calls no cudaMalloc, cudaFree, cudaMallocHost or other
  * allocating routine: every scratch buffer is carved from one file-scope
- * device array of GD_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads
- * this library holds until the process exits.  The caller still provides X,
- * labels and is_core (device pointers, as for gd_dbscan), and the result is
- * bit-identical to gd_dbscan's.
+ * device array of GD_NOALLOC_SCRATCH_BYTES bytes.  The caller still provides
+ * X, labels and is_core (device pointers, as for gd_dbscan), and the result
+ * is bit-identical to gd_dbscan's.
  *
+ *   - The array is backed on a GPU when the library's module is loaded there
+ *     and is held until the process exits.  CUDA loads modules lazily by
+ *     default, so that happens inside the first call on each device (with
+ *     that device current; the call looks up the array's device address with
+ *     cudaGetSymbolAddress).  Make one warm-up call per device at start-up,
+ *     before the device's memory is committed elsewhere and before any
+ *     stream capture.  If the device cannot back the array, the call returns
+ *     GD_ENOMEM.
  *   - n above GD_NOALLOC_MAX_POINTS, or data whose neighbour lists do not fit
  *     in what the array has left, returns GD_ENOMEM (nothing is written);
  *     malformed arguments return GD_EINVAL as for gd_dbscan.
- *   - The first call on a device (with that device current) looks up the
- *     array's device address with cudaGetSymbolAddress; make that first call
- *     before any stream capture on the device.
  *   - All calls share the one array and it keeps the previous call's
  *     contents; the pipeline clears whatever must start at zero.  Calls that
  *     overlapped on the GPU would race on the array: this function takes a
  *     process-wide lock and returns only after its work on `stream` has
- *     finished, so calls made through it do not overlap.
+ *     finished (on success and on failure), so calls made through it do not
+ *     overlap.
  * --------------------------------------------------------------------- */
 #define GD_NOALLOC_MAX_POINTS 65536
 #define GD_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -217,7 +217,7 @@ size_t gd_workspace_bytes(int64_t n, int d) {
     // the per-instance arrays (upper bound: 128-bit keys, the most digit
     // passes) plus the batch's small blocks, descriptors and scan scratch
     const size_t N = (size_t)n, dp = d == 1 ? 1 : d == 2 ? 2 : d <= 4 ? 4 : 8;
-    size_t b = N * (2 * 16 + 2 * 4 + 2 * dp * 4 + 4 + 1 + 4 * 10 + (size_t)d * 4 * 4 + 4 * (2 * d + 2)) ;
+    size_t b = N * (2 * 16 + 2 * 4 + 2 * dp * 4 + 4 + 1 + 4 * 12 + (size_t)d * 4 * 4 + 4 * (2 * d + 2));
     b += sort_tmp_ints((int)n, 2, 128) * 4 + ((size_t)1 << 20);
     return b;
 }

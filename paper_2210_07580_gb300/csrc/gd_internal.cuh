@@ -109,8 +109,14 @@ struct Inst {
     int* lv_cb[kMaxD];
     int* lv_E;  // [d][C+1] level scratch
     int* lv_L;  // [C]
+    // Neighbour lists: list(c) holds the grids g' >= c the walk found from c
+    // (forward part, nbr_fwd[c] entries) followed by the grids g < c whose
+    // walks found c (backward part); nbr_bwd counts the backward entries,
+    // then serves as the cursor that places them.
     int* nbr_start;
     int* nbr;
+    int* nbr_fwd;
+    int* nbr_bwd;
     int* nf_start;
     int* core_start;
     int* bbox;
@@ -373,6 +379,9 @@ enum WalkMode { kWalkCount = 0, kWalkFill = 1, kWalkPool = 2 };
 cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
                         cudaStream_t st);
 cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st);
+// After a counting or pooled walk: nbr_start[c] = forward + backward entries
+// (scanned next), backward counts reset to serve as placement cursors.
+cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 
 // Core points (core.cu).
 cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st);

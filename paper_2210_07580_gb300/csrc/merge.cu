@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256) pair_kernel(const Inst* __restrict__ ins,
                 out_f = I.pairs + I.pair_start[C] + I.pair_start_f[c];
             }
             const int gl = lane < d ? coord[c * d + lane] : 0;
-            const int t_end = I.nbr_start[c + 1];
+            // the grids j2 > c are the forward part of the list
+            const int t_end = I.nbr_start[c] + I.nbr_fwd[c];
             for (int t0 = I.nbr_start[c]; t0 < t_end; t0 += 32) {
                 const int t = t0 + lane;
                 const int j2 = t < t_end ? I.nbr[t] : -1;

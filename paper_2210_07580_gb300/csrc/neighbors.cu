@@ -19,8 +19,15 @@
 // Nei(g) that still holds every grid with a point within eps of a point of g
 // (in sparse, high-dimensional data, where grids hold about one point, it is
 // an order of magnitude smaller).  Grids of more than kBoxPoints points use
-// their identifier range as their box, and their own lists skip the leaf
-// test: dense grids fill their range, so it would only cost loads.
+// their identifier range as their box (dense grids fill their range).
+//
+// The relation "boxes within eps" is symmetric, so each pair is found once:
+// the walk from grid c enumerates only the grids g' >= c (lexicographic
+// order, the order of the grid list): while the path it descends equals c's
+// own identifier prefix, a level's key window is [g_j, g_j + r] instead of
+// [g_j - r, g_j + r].  Each pair (c, g'), g' > c, then also enters g''s list
+// (its backward part), placed by an atomic cursor per grid.  The walk does
+// about half the work of a full one, and the lists are the same sets.
 #include "gd_internal.cuh"
 
 namespace gd {
@@ -124,6 +131,7 @@ __global__ void level_diff_kernel(const Inst* __restrict__ ins, Flat f, long lon
                 }
         }
         I.lv_L[c] = l;
+        I.nbr_bwd[c] = 0;  // backward-entry counts of the walk that follows
     }
 }
 
@@ -192,15 +200,18 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
 // Walk of the levels for one grid (Alg. 3), one warp per query grid.
 //
 // The warp keeps a stack of key ranges in shared memory: (level j, nodes
-// [lo, hi) of level j, partial offset of the path above them).  Each step
-// takes the entries of the top level -- up to 32 nodes across several
-// ranges, the last range possibly split -- and the lanes test one node each:
-// key within +-r, offset within eps (and, at a leaf, the point-box test);
-// surviving inner nodes push their child range narrowed to keys within +-r
-// (so no pushed node fails its key test), surviving leaves are counted into
-// nbr_start[c] and written: at nbr + nbr_start[c] once the counts are
+// [lo, hi) of level j, partial offset of the path above them, whether the
+// path equals the query's own prefix).  Each step takes the entries of the
+// top level -- up to 32 nodes across several ranges, the last range possibly
+// split -- and the lanes test one node each: key within the window, offset
+// within eps (and, at a leaf, the point-box test); surviving inner nodes push
+// their child range narrowed to the child window (so no pushed node fails
+// its key test), surviving leaves are the forward neighbours g' >= c: counted
+// into nbr_fwd[c] and written -- at nbr + nbr_start[c] once the counts are
 // scanned (kWalkFill), or to the pool in runs of up to 32 (kWalkPool, see
-// WalkPool).  Every mode visits the nodes in the same order.
+// WalkPool) -- while each g' > c also counts (count and pool modes) or
+// receives (fill mode) the backward entry c.  Every mode visits the nodes in
+// the same order.
 //
 // Stack bound: levels never decrease from the bottom of the stack to its top
 // (a step pops the top level j and pushes level j + 1), so a level receives
@@ -208,6 +219,9 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
 // entries.  Hence at most 32 entries per level below the root: 1 + 32 (d - 1).
 constexpr int kWalkWarps = 4;
 constexpr int kWalkStack = 1 + 32 * (kMaxD - 1);
+// stack entry level byte: the level in the low bits, kTight when the path to
+// the range equals the query's identifier prefix
+constexpr int kTight = 0x10;
 
 // Narrow the key-sorted range [*lo, *hi) to keys in [vlo, vhi]: the two
 // bisections run side by side, so their loads overlap.
@@ -261,6 +275,13 @@ __device__ __forceinline__ void pool_flush(const WalkPool& pool, const int* buf,
     }
 }
 
+// The backward entry c in the list of grid u > c (fill mode and the pool
+// scatter): after the forward part, at the next free slot.
+__device__ __forceinline__ void put_backward(const Inst& I, int u, int c) {
+    const int at = I.nbr_start[u] + I.nbr_fwd[u] + atomicAdd(I.nbr_bwd + u, 1);
+    I.nbr[at] = c;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(32 * kWalkWarps)
     walk_kernel(const Inst* __restrict__ ins, Flat f, long long total, WalkPool pool) {
@@ -301,7 +322,6 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             }
         }
         __syncwarp();
-        const bool refine = I.cell_start[c + 1] - I.cell_start[c] <= kBoxPoints;
         const int* pbox = I.pbox;
         int* out = FILL ? I.nbr + I.nbr_start[c] : nullptr;
         int found = 0;
@@ -310,14 +330,15 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         int* const buf = sh.buf[w];
         int top = 0;
         {
+            // the root range: level-0 keys in [g_0, g_0 + r], on the query's path
             int a0 = 0, b0 = I.small[kSmLevelCount];
-            narrow_range(I.lv_key[0], &a0, &b0, sh.klo[w][0], sh.khi[w][0]);
+            narrow_range(I.lv_key[0], &a0, &b0, sh.g[w][0], sh.khi[w][0]);
             if (b0 > a0) {
                 if (lane == 0) {
                     slo[0] = a0;
                     shi[0] = b0;
                     spart[0] = 0;
-                    slvl[0] = 0;
+                    slvl[0] = (signed char)kTight;
                 }
                 top = 1;
             }
@@ -325,15 +346,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         __syncwarp();
         while (top > 0) {
             // the group: the entries of the top level, lane i holding entry top-1-i
-            const int J = slvl[top - 1];
+            const int J = slvl[top - 1] & (kTight - 1);
             const int e = top - 1 - lane;
-            const bool in_group = e >= 0 && slvl[e] == J;
-            int elo = 0, sz = 0;
+            const int ev = e >= 0 ? slvl[e] : -1;
+            const bool in_group = e >= 0 && (ev & (kTight - 1)) == J;
+            int elo = 0, sz = 0, etight = 0;
             long long epart = 0;
             if (in_group) {
                 elo = slo[e];
                 sz = min(shi[e] - elo, 64);
                 epart = spart[e];
+                etight = ev & kTight;
             }
             const int P = warp_inclusive_scan(sz);
             const int start = P - sz;
@@ -345,15 +368,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             // each lane's node: entry index = number of segment starts at or
             // below the lane, minus one
             const int ei = __popc(starts & ((2u << lane) - 1u)) - 1;
-            const int my_lo = __shfl_sync(kFull, elo, ei < 0 ? 0 : ei);
-            const int my_start = __shfl_sync(kFull, start, ei < 0 ? 0 : ei);
-            const long long my_part = __shfl_sync(kFull, epart, ei < 0 ? 0 : ei);
+            const int src = ei < 0 ? 0 : ei;
+            const int my_lo = __shfl_sync(kFull, elo, src);
+            const int my_start = __shfl_sync(kFull, start, src);
+            const long long my_part = __shfl_sync(kFull, epart, src);
+            const int my_tight = __shfl_sync(kFull, etight, src);
             top -= consumed;
             __syncwarp();
 
             const bool act = lane < taken;
             const int u = my_lo + (lane - my_start);
-            bool ok = false;
+            bool ok = false, tight = false;
             long long off = 0;
             // the node's child range is loaded with its key (one round trip)
             int clo = 0, chi = 0;
@@ -367,11 +392,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 if (dl >= -r && dl <= r) {
                     off = my_part + sh.gap2[w][J][dl + kMaxR];
                     ok = off <= eps2;
+                    tight = my_tight && dl == 0;
                 }
             }
             if (J == d - 1) {
-                // leaf: the two grids' point boxes
-                if (ok && refine) {
+                // leaf: the two grids' boxes (a forward neighbour u >= c)
+                if (ok) {
                     const int* ub = pbox + (long long)u * 2 * d;
                     long long g2 = 0;
                     for (int t = 0; t < d; ++t) {
@@ -385,6 +411,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     ok = g2 <= eps2;
                 }
                 const unsigned m = __ballot_sync(kFull, ok);
+                if (ok && u != (int)c) {
+                    if (FILL)
+                        put_backward(I, u, (int)c);
+                    else
+                        atomicAdd(I.nbr_bwd + u, 1);
+                }
                 if (FILL && ok) out[found + __popc(m & lt)] = u;
                 found += __popc(m);
                 if (POOL) {
@@ -402,7 +434,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 }
             } else {
                 if (ok) {
-                    narrow_range(I.lv_key[J + 1], &clo, &chi, sh.klo[w][J + 1], sh.khi[w][J + 1]);
+                    // a child window: [g - r, g + r], or [g, g + r] below a node
+                    // on the query's own path
+                    const long long wlo = tight ? (long long)sh.g[w][J + 1] : sh.klo[w][J + 1];
+                    narrow_range(I.lv_key[J + 1], &clo, &chi, wlo, sh.khi[w][J + 1]);
                     ok = chi > clo;
                 }
                 const unsigned m = __ballot_sync(kFull, ok);
@@ -411,14 +446,14 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     slo[at] = clo;
                     shi[at] = chi;
                     spart[at] = off;
-                    slvl[at] = (signed char)(J + 1);
+                    slvl[at] = (signed char)((J + 1) | (tight ? kTight : 0));
                 }
                 top += __popc(m);
             }
             __syncwarp();
         }
         if (POOL && nbuf > 0) pool_flush(pool, buf, nbuf, kin, (int)c, flushed, lane);
-        if (!FILL && lane == 0) I.nbr_start[c] = found;
+        if (!FILL && lane == 0) I.nbr_fwd[c] = found;
         __syncwarp();
     }
 }
@@ -438,7 +473,9 @@ cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, 
     return cudaGetLastError();
 }
 
-// The pool's segments into the scanned lists: one warp per segment.
+// The pool's segments into the scanned lists, one warp per segment: each
+// run of forward neighbours of query c goes to its place in c's list, and
+// every neighbour u > c receives the backward entry c.
 __global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restrict__ ins, WalkPool pool,
                                                            long long nseg) {
     const int lane = lane_id();
@@ -447,8 +484,32 @@ __global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restric
          sgi += warps) {
         const PoolSeg sg = pool.seg[sgi];
         const Inst& I = ins[sg.inst];
-        if (lane < sg.len) I.nbr[(long long)I.nbr_start[sg.c] + sg.off + lane] = pool.data[sg.pos + lane];
+        if (lane < sg.len) {
+            const int u = pool.data[sg.pos + lane];
+            I.nbr[(long long)I.nbr_start[sg.c] + sg.off + lane] = u;
+            if (u != sg.c) put_backward(I, u, sg.c);
+        }
     }
+}
+
+// List lengths before the scan: forward + backward entries of each grid; the
+// backward counts restart at zero as the cursors that place the entries.
+__global__ void nbr_total_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = i - cur.lo;
+        I.nbr_start[c] = I.nbr_fwd[c] + I.nbr_bwd[c];
+        I.nbr_bwd[c] = 0;
+    }
+}
+
+cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    nbr_total_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st) {

@@ -10,9 +10,13 @@
 // routine.  It runs the same driver and kernels as gd_dbscan, so its labels
 // equal gd_dbscan's bit for bit.
 //
-// The device array below (GD_NOALLOC_SCRATCH_BYTES) exists on every GPU that
-// loads this library, for as long as the library stays loaded; the host-side
-// staging it needs is a static host array.
+// The device array below (GD_NOALLOC_SCRATCH_BYTES) is backed on a GPU once
+// the module holding it is loaded there and stays until the process exits.
+// CUDA loads modules lazily by default (CUDA_MODULE_LOADING=LAZY), so that
+// happens inside the first call on each device: callers should make one
+// warm-up call per device at start-up, before any allocation budget is
+// spent and before any stream capture.  The host-side staging it needs is a
+// static host array.
 #include <cstring>
 #include <mutex>
 
@@ -25,10 +29,8 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GD_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
 constexpr size_t kHostStaging = 1 << 20;
-std::mutex g_mutex;                 // serialises host callers (they share both arrays)
-void* g_scratch_addr[kMaxDevices];  // device address of the array, per device
+std::mutex g_mutex;  // serialises host callers (they share both arrays)
 alignas(256) unsigned char g_host[kHostSlots][kHostStaging];
 
 // Memory from the static arrays: each slot is carved once per call, in the
@@ -82,21 +84,28 @@ extern "C" gd_status gd_dbscan_noalloc(const int32_t* X, int64_t n, int d, int64
     if (n == 0) return GD_OK;
 
     std::lock_guard<std::mutex> lock(g_mutex);
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GD_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return GD_EINVAL;
-    if (!g_scratch_addr[dev]) {
-        // First call on this device (which is current): look up the device
-        // address of the static array.  The host-side symbol is only a
-        // stand-in and must never be handed to a kernel.
-        void* addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return GD_ECUDA;
-        g_scratch_addr[dev] = addr;
+    // The device address of the static array on the current device.  The
+    // host-side symbol is only a stand-in and must never be handed to a
+    // kernel.  It is looked up on every call (cheap once the module is
+    // loaded), so nothing stale survives a device reset.  The first lookup on
+    // a device loads the module and backs the array; if the device cannot
+    // back it, that is an out-of-memory condition, not a CUDA fault.
+    void* addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || !addr) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? GD_ENOMEM : GD_ECUDA;
     }
     StaticMem mem;
-    mem.base = (char*)g_scratch_addr[dev];
+    mem.base = (char*)addr;
     // The driver clears every piece of device state it reads before it reads
     // it, so nothing left in the array by an earlier call leaks into this one.
     const gd_instance g{X, n, d, eps2, minpts, labels, is_core};
-    return run_batch(mem, 1, &g, (cudaStream_t)stream, nullptr, nullptr, &noalloc_tuning());
+    const cudaStream_t st = (cudaStream_t)stream;
+    const gd_status s = run_batch(mem, 1, &g, st, nullptr, nullptr, &noalloc_tuning());
+    // A failed run may return with kernels still queued on the stream; they
+    // use the shared array, so they must finish before the next caller gets
+    // the lock.
+    if (s != GD_OK) cudaStreamSynchronize(st);
+    return s;
 }

@@ -128,6 +128,8 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     I.lv_E = (int*)take((size_t)d * (N + 1) * 4);
     I.lv_L = (int*)take(N * 4);
     I.nbr_start = (int*)take((N + 1) * 4);
+    I.nbr_fwd = (int*)take(N * 4);
+    I.nbr_bwd = (int*)take(N * 4);
     I.nf_start = (int*)take((N + 1) * 4);
     I.core_start = (int*)take((N + 1) * 4);
     I.bbox = (int*)take(N * 2 * d * 4);
@@ -624,6 +626,7 @@ gd_status Run::go() {
     mark(5);
     RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
              "walk");
+    RUN_CUDA(launch_nbr_total(dins, cells2, total_cells, st), "list lengths");
     RUN_TRY(scan(nseg, K, nseg_tiles));
     mark(kStages + 3);
     return GD_OK;

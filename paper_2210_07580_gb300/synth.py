@@ -106,6 +106,7 @@ def workload(name: str, seed: int = 1, n: int | None = None):
     ss3d_2m    d=3, n=2,000,000 seed spreader + 0.01% noise, eps=500, MinPts=20
     ss3d_10m   d=3, n=10,000,000 seed spreader + 0.01% noise, eps=500, MinPts=20
     skew5d_10m d=5, n=10,000,000 skewed mix, eps=1000, MinPts=100
+    skew3d_10m d=3, n=10,000,000 skewed mix, eps=500, MinPts=20
     ``n`` overrides the size.  For the seed spreader the restart probability
     stays that of the full workload, so a smaller ``n`` is the same walk
     process stopped early (same local density, fewer points).
@@ -122,6 +123,9 @@ def workload(name: str, seed: int = 1, n: int | None = None):
     if name == "skew5d_10m":
         nn = n or 10_000_000
         return skewed_mix(nn, 5, eps=1000.0, seed=seed), 1000 ** 2, 100
+    if name == "skew3d_10m":
+        nn = n or 10_000_000
+        return skewed_mix(nn, 3, eps=500.0, seed=seed), 500 ** 2, 20
     raise KeyError(name)
 
 
