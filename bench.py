@@ -30,8 +30,15 @@ WORKLOADS = {
     "ss3d_10m": "seed-spreader d=3 n=10,000,000 eps=500 MinPts=20 (+0.01% uniform noise)",
     "ss3d_2m": "seed-spreader d=3 n=2,000,000 eps=500 MinPts=20 (+0.01% uniform noise)",
     "skew5d_10m": "skewed mix d=5 n=10,000,000 eps=1000 MinPts=100 (50% in one eps-ball + 20 blobs)",
+    "skew3d_10m": "skewed mix d=3 n=10,000,000 eps=500 MinPts=20 (50% in one eps-ball + 20 blobs)",
     "tiny": "blobs d=2 n=20,000 eps=800 MinPts=10 (10 blobs sigma=1500 + 5% noise)",
 }
+# The plain-method configurations measured beside the headline: label,
+# workload, timed steps.  L3 is the headline itself (seed spreader) and its
+# skewed-mix variant.
+CONFIGS = [("T", "tiny", 20), ("S", "ss3d_2m", 10), ("L3", "ss3d_10m", 10), ("L3_skew", "skew3d_10m", 10),
+           ("L5", "skew5d_10m", 5)]
+HBM_STAGES = ("bounds", "quantise", "sort", "compact", "core")
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) per downsweep launch, from one `ncu --set full`
@@ -55,9 +62,13 @@ def sort_source_digest() -> str:
     return hashlib.sha256(text[a:b].encode()).hexdigest()[:16] if 0 <= a < b else ""
 
 
-def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float) -> dict:
-    """Achieved bandwidth of the grid-build stages: algorithmic bytes (each
-    array the stage must read or write, once) over the stage's device time."""
+def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float, stats: dict | None = None) -> dict:
+    """Achieved bandwidth of the grid-build stages and (with run statistics)
+    of the count stage: algorithmic bytes (each array the stage must read or
+    write, once) over the stage's device time.  The count stage must write
+    every core flag (1 B/point) and read each non-full point's row and, once
+    per non-full grid, the rows of its neighbour grids (the statistic
+    count_rows)."""
     dp = 1 if d == 1 else 2 if d == 2 else 4 if d <= 4 else 8
     kc = sizes["key_class"]
     key_b = 16 if kc == 2 else 8
@@ -70,6 +81,8 @@ def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float) -> d
         "sort": (P * 2 * (key_b + val_b) + (P - (1 if first_hist else 0)) * key_b) * n,
         "compact": (2 * key_b + val_b + 4 + 4 + 4 * d + 4 * dp) * n,
     }
+    if stats:
+        bytes_["core"] = n + (stats["nonfull_points"] + stats["count_rows"]) * 4 * dp
     out = {}
     for st, b in bytes_.items():
         ms = stages.get(st, 0.0)
@@ -230,6 +243,132 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def alu_utilisation(stages: dict, stats: dict, peak_per_s: float) -> dict:
+    """Exact squared distances per second of the distance-heavy stages (the
+    statistics' counts over the timed stage's time) against the register-only
+    ceiling of the same instruction mix (gd_distance_peak)."""
+    out = {"peak_dist_per_s": round(peak_per_s / 1e9, 2), "unit": "Gdist/s"}
+    for stage, keys in (("core", ("dist_core",)), ("merge", ("dist_merge", "dist_fastmerging")),
+                        ("labels", ("dist_labels",))):
+        ms = stages.get(stage, 0.0)
+        cnt = sum(stats.get(k, 0) for k in keys)
+        if ms > 0 and cnt > 0:
+            rate = cnt / (ms / 1e3)
+            out[stage] = {"distances": int(cnt), "ms": round(ms, 4), "gdist_per_s": round(rate / 1e9, 2),
+                          "frac": round(rate / peak_per_s, 4)}
+    return out
+
+
+def merge_summary(stats: dict) -> dict:
+    """Candidate-pair outcomes, the rate of pairs skipped because their grids
+    were already joined (the LDF skip of Section 5.2), and the FastMerging
+    round histogram (kappa, Section 4.3.3)."""
+    pairs = stats.get("pairs", 0)
+    kappa = [stats.get(f"kappa_{i}", 0) for i in range(1, 16)] + [stats.get("kappa_16_or_more", 0)]
+    kmax = max((i + 1 for i, v in enumerate(kappa) if v), default=0)
+    return {"pairs": pairs, "skipped_rate": round(stats.get("pairs_skipped", 0) / pairs, 4) if pairs else None,
+            "outcomes": {k: stats.get(k, 0) for k in ("pairs_skipped", "pairs_box_no", "pairs_box_yes",
+                                                      "pairs_lane", "pairs_warp", "pairs_fastmerging",
+                                                      "fm_yes", "fm_no", "fm_pruned_triangle",
+                                                      "fm_pruned_angle")},
+            "kappa_hist": kappa, "kappa_max": kmax}
+
+
+def measure_workload(ctx, dev, workload: str, steps: int, warmup: int, flush, stream, X=None, eps2=None,
+                     minpts=None):
+    """Device-timed runs of one workload (L2 flushed before each, outside the
+    events), the library's stage times, and one untimed run with statistics."""
+    import torch
+    from paper_2210_07580_gb300 import synth
+    if X is None:
+        X, eps2, minpts = synth.workload(workload, seed=1)
+    n = len(X)
+    Xd = torch.from_numpy(X).to(dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    core = torch.empty(n, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream)
+
+    for _ in range(warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    acc, times = {}, []
+    for k in range(steps):
+        flush.fill_(k + 2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        for name, ms in ctx.stage_times().items():
+            acc[name] = acc.get(name, 0.0) + ms / steps
+    ctx.set_timing(False)
+    sizes = ctx.last_sizes()
+    ctx.set_stats(True)
+    step()
+    torch.cuda.synchronize()
+    stats = ctx.run_stats()
+    ctx.set_stats(False)
+    return {"X": X, "eps2": eps2, "minpts": minpts, "labels": labels.cpu().numpy(),
+            "core": core.cpu().numpy().astype(bool), "ms": sum(times) / len(times),
+            "stages": {k: round(v, 4) for k, v in acc.items()}, "sizes": sizes, "stats": stats}
+
+
+def oracle_check(m: dict, fastmerging: bool = True) -> dict:
+    """The oracle on the same input, outside the timed region: label and core
+    flag parity, and its host time (plain merge, and FastMerging as the
+    GriT-DBSCAN-LDF CPU baseline with its kappa)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    wl, wc = oracle.grid(m["X"], m["eps2"], m["minpts"])
+    t_plain = time.perf_counter() - t0
+    n = len(m["X"])
+    out = {"parity": bool(np.array_equal(wl, m["labels"]) and np.array_equal(wc, m["core"])),
+           "cpu_baseline": {"value": round(n / t_plain / 1e6, 3), "unit": "Mpts/s", "cores": oracle.num_threads(),
+                            "kind": "oracle", "cpu": cpu_info(), "s": round(t_plain, 3),
+                            "sample": "full input, merge by Def. 7"}}
+    if fastmerging:
+        t0 = time.perf_counter()
+        _, _, st = oracle.grid(m["X"], m["eps2"], m["minpts"], merge="fastmerging", return_stats=True)
+        t_fm = time.perf_counter() - t0
+        out["cpu_baseline_fastmerging"] = {"value": round(n / t_fm / 1e6, 3), "unit": "Mpts/s", "s": round(t_fm, 3),
+                                           "kind": "oracle (GriT-DBSCAN-LDF with FastMerging)",
+                                           "kappa_max": st["max_rounds"], "kappa_hist": st["kappa_hist"],
+                                           "merge_tests": st["merge_tests"]}
+    return out
+
+
+def config_line(label: str, workload: str, m: dict, peak: float, dist_peak: float, check: dict | None) -> dict:
+    n, d = m["X"].shape
+    stages = m["stages"]
+    sb = stage_bandwidth(stages, n, d, m["sizes"], peak, m["stats"])
+    main = {k: v for k, v in stages.items() if k != "sort_downsweep"}
+    dom = max(main, key=main.get)
+    total = sum(main.values())
+    line = {"label": label, "workload": WORKLOADS[workload], "n": n, "d": d, "eps2": m["eps2"],
+            "minpts": m["minpts"], "ms_per_step": round(m["ms"], 4), "value": round(n / (m["ms"] / 1e3) / 1e6, 3),
+            "unit": "Mpts/s", "grids": m["sizes"]["grids"], "neighbour_entries": m["sizes"]["nnbr"],
+            "stages_ms": stages,
+            "dominant_stage": {"name": dom, "ms": round(main[dom], 4), "share": round(main[dom] / total, 3)},
+            "stage_bandwidth": sb,
+            "alu": alu_utilisation(stages, m["stats"], dist_peak),
+            "merge": merge_summary(m["stats"])}
+    # roofline of the config's dominant HBM-bound stage (grid build or count)
+    hb = {k: v for k, v in sb.items() if k in HBM_STAGES}
+    if hb:
+        k = max(hb, key=lambda s: hb[s]["ms"])
+        line["roofline"] = {"bound": "hbm", "stage": k, "achieved": hb[k]["gbs"], "peak": peak, "unit": "GB/s",
+                            "frac": hb[k]["frac"], "bytes": hb[k]["bytes"]}
+    if check:
+        line.update(check)
+    return line
 
 
 def bench_batched(ctx, dev, args):
@@ -448,17 +587,46 @@ def run_gpu(args):
             "wall_s_timed": round(t_wall, 3),
             "stage_bandwidth": stage_bandwidth(stages, n, d, sizes, peak),
         }
+        headline_check = None
+        if not args.no_configs and ws == 1:
+            # every plain-method configuration: device time, stages, HBM and
+            # ALU fractions, merge statistics, and (outside the timed region)
+            # the oracle's labels and host time on the same input
+            from paper_2210_07580_gb300 import binding
+            dist_peak = {}
+            configs = {}
+            for label, wl, steps in CONFIGS:
+                m = measure_workload(ctx, dev, wl, steps, args.warmup, flush, stream)
+                dd = m["X"].shape[1]
+                if dd not in dist_peak:
+                    dist_peak[dd] = binding.distance_peak(dd, local)
+                check = None if args.no_cpu_baseline else oracle_check(m, fastmerging=not args.no_oracle_fm)
+                configs[label] = config_line(label, wl, m, peak, dist_peak[dd], check)
+                if wl == args.workload:
+                    headline_check = check
+                del m
+            line["configs"] = configs
+            line["parity_all_configs"] = all(c.get("parity", False) for c in configs.values()) \
+                if not args.no_cpu_baseline else None
         if not args.no_batch:
             line["batched"] = bench_batched(ctx, dev, args)
         if not args.no_serve:
             line["serve"] = bench_serve(dev, args)
         if not args.no_cpu_baseline and ws == 1:
-            t, ns, thr = time_oracle(args.workload, 1, args.cpu_sample)
-            line["cpu_baseline"] = {"value": round(ns / t / 1e6, 3), "unit": "Mpts/s", "cores": thr,
-                                    "kind": "oracle", "cpu": cpu_info(),
-                                    "sample": f"{WORKLOADS[args.workload]}, "
-                                              + (f"first {ns} points of the walk" if args.cpu_sample else "full size")
-                                              + f", one run, {t:.1f} s"}
+            if headline_check and not args.cpu_sample:
+                cb = dict(headline_check["cpu_baseline"])
+                cb["sample"] = f"{WORKLOADS[args.workload]}, full size, one run, {cb.pop('s'):.1f} s"
+                line["cpu_baseline"] = cb
+                if "cpu_baseline_fastmerging" in headline_check:
+                    line["cpu_baseline_fastmerging"] = headline_check["cpu_baseline_fastmerging"]
+            else:
+                t, ns, thr = time_oracle(args.workload, 1, args.cpu_sample)
+                line["cpu_baseline"] = {"value": round(ns / t / 1e6, 3), "unit": "Mpts/s", "cores": thr,
+                                        "kind": "oracle", "cpu": cpu_info(),
+                                        "sample": f"{WORKLOADS[args.workload]}, "
+                                                  + (f"first {ns} points of the walk" if args.cpu_sample
+                                                     else "full size")
+                                                  + f", one run, {t:.1f} s"}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -477,6 +645,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="points of the workload the CPU oracle times (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-configuration measurements (T, S, L3, L3_skew, L5)")
+    ap.add_argument("--no-oracle-fm", action="store_true",
+                    help="skip timing the oracle's FastMerging variant beside its plain merge")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched vs looped measurement")
     ap.add_argument("--batch-k", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")

@@ -164,6 +164,17 @@ typedef enum {
  *                         largest dimension and instance).
  *   GD_KNOB_WALK_BLOCKS   blocks of the neighbour walk (4 warps each);
  *                         152..19456, default 4864 (per batch, likewise).
+ *   GD_KNOB_MERGE_ORDER   order in which candidate pairs of core grids are
+ *                         tested: 0 = touching grids first, then the rest
+ *                         (two waves); 1 = low density first (the LDF
+ *                         variant of Section 5.2: one queue, pairs of grids
+ *                         with fewer core points first); default 1
+ *                         (per instance).
+ *   GD_KNOB_CORE_MODE     how points of grids with fewer than minpts points
+ *                         count their neighbours: 0 = a warp per point; 1 =
+ *                         a warp per grid, which reads the grid's neighbour
+ *                         list once for all its points; default 1 for d <= 4,
+ *                         0 above (per group).
  *
  * Groups: instances of one dimension whose sizes fall in one bucket (at most
  * 2^12, 2^15, 2^18, 2^21 points, or more) are launched together and share
@@ -175,7 +186,9 @@ typedef enum {
     GD_KNOB_MERGE_SMALL = 3,
     GD_KNOB_CORE_BANDS = 4,
     GD_KNOB_FM_BLOCKS = 5,
-    GD_KNOB_WALK_BLOCKS = 6
+    GD_KNOB_WALK_BLOCKS = 6,
+    GD_KNOB_MERGE_ORDER = 7,
+    GD_KNOB_CORE_MODE = 8
 } gd_knob;
 
 typedef struct {
@@ -225,12 +238,53 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
 /* Per-stage device timing (CUDA events around each stage of gd_dbscan).
  * Off by default; when on, gd_stage_times fills up to max entries of
  * milliseconds and names for the last run and returns the count: the 11
- * stages in order (device time from a stage's first launch to its last; the
- * host's work between the call's phases is in none of them), then
+ * stages in order -- bounds, quantise, sort, compact, levels, walk, core,
+ * core_pack, merge_order, merge, labels -- (device time from a stage's first
+ * launch to its last; the host's work between the call's phases is in none
+ * of them), then
  * "sort_downsweep", the summed time of the radix sort's downsweep kernels
  * (part of the "sort" stage). */
 gd_status gd_set_timing(gd_ctx *ctx, int enable);
 int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
+
+/* Run statistics (no counterpart in the paper; the quantities are the ones
+ * Section 4.3.3 and Section 5.2 discuss).  Off by default; when on, each call
+ * counts, summed over its instances, and gd_run_stats fills up to max values
+ * and names for the last call and returns the count (0 if the last call kept
+ * none).  The counters, in order:
+ *   pairs                candidate pairs of neighbouring core grids
+ *   pairs_skipped        ... already in one union-find set (the LDF skip)
+ *   pairs_box_no         ... decided "no" by the gap of the core boxes
+ *   pairs_box_yes        ... decided "yes" by the core boxes' farthest corners
+ *   pairs_lane           ... decided by one lane's exact loop
+ *   pairs_warp           ... decided by a warp's exact tiles
+ *   pairs_fastmerging    ... handed to FastMerging (Alg. 5); each of these ends
+ *                        as fm_yes, fm_no or a later skip
+ *   fm_yes, fm_no        FastMerging answers
+ *   fm_pruned_triangle   points removed by Alg. 4's triangle test
+ *   fm_pruned_angle      points removed by Alg. 4's angle test (Def. 8)
+ *   nonfull_points       points of grids with fewer than minpts points
+ *   count_rows           rows of their neighbour grids, once per such grid
+ *   dist_core, dist_merge, dist_fastmerging, dist_labels
+ *                        exact squared distances evaluated by core
+ *                        counting, the warp-level merge, FastMerging and
+ *                        border labelling
+ *   kappa_1 .. kappa_15, kappa_16_or_more
+ *                        FastMerging calls by number of rounds (kappa of
+ *                        Section 4.3.3)
+ * Counting costs atomics: do not time calls that keep statistics. */
+gd_status gd_set_stats(gd_ctx *ctx, int enable);
+int gd_run_stats(const gd_ctx *ctx, int64_t *values, const char **names, int max);
+
+/* Throughput ceiling of the exact squared-distance test in d dimensions on
+ * CUDA device `device` (no counterpart in the paper; for measurement).  Runs
+ * the instruction mix of the merge's warp tiles -- a point broadcast by
+ * shuffle, d int32 differences, d 64-bit squares summed, one compare -- from
+ * registers only for a few tens of milliseconds and writes the best rate in
+ * distances per second to *per_s.  The dist_* statistics over a stage's time
+ * give that stage's ALU utilisation against this figure.  Allocates 4 bytes
+ * of device memory for the duration of the call. */
+gd_status gd_distance_peak(int device, int d, double *per_s);
 
 /* ---------------------------------------------------------------------
  * Clustering without any device allocation (no counterpart in the paper).

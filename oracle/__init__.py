@@ -14,7 +14,8 @@ Functions (all inputs are numpy arrays; coordinates int32 [n, d], row-major):
                      G13 core rule, LDF union-find merging, border step).
 ``grid_structure``   non-empty grids and Nei(g) of every grid (Alg. 1, Alg. 3).
 ``neighbor_counts``  |N_eps(p)| for a list of query points, by brute force.
-``mindist_le``       MinDist(A, B) <= eps by Def. 7 or by FastMerging (Alg. 5).
+``mindist_le``       MinDist(A, B) <= eps by Def. 7 or by FastMerging (Alg. 5, with
+                     both pruning tests of Alg. 4).
 ``cell_side``        the integer cell side of Eq. 1 (largest s, d(s-1)^2 <= eps2).
 """
 from __future__ import annotations
@@ -44,7 +45,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-Wall", "-Wextra",
-           "-Wno-unused-parameter", _SRC, "-o", tmp]
+           "-Wno-unused-parameter", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -99,7 +100,7 @@ def restore_library(lib):
 def compile_source(src_path: str, out_path: str):
     """Compile a gd_oracle.c variant with the same flags as build()."""
     subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", src_path, "-o",
-                    out_path], check=True)
+                    out_path, "-lm"], check=True)
 
 
 def _ptr(a: np.ndarray, ctype):
@@ -136,14 +137,15 @@ def grid(X, eps2: int, minpts: int, merge: str = "plain", return_stats: bool = F
     n, d = X.shape
     labels = np.empty(n, np.int32)
     core = np.empty(n, np.uint8)
-    stats = np.zeros(4, np.int64)
+    stats = np.zeros(20, np.int64)
     mode = {"plain": 0, "fastmerging": 1}[merge]
     _check(_load().oracle_grid(_ptr(X, ctypes.c_int32), n, d, int(eps2), int(minpts),
                                _ptr(labels, ctypes.c_int32), _ptr(core, ctypes.c_uint8), mode,
                                _ptr(stats, ctypes.c_longlong)))
     if return_stats:
         return labels, core.astype(bool), dict(grids=int(stats[0]), merge_tests=int(stats[1]),
-                                               max_rounds=int(stats[2]), core_grids=int(stats[3]))
+                                               max_rounds=int(stats[2]), core_grids=int(stats[3]),
+                                               kappa_hist=[int(v) for v in stats[4:20]])
     return labels, core.astype(bool)
 
 

@@ -43,6 +43,7 @@
  * All distances are exact int64 squared distances.  The caller must ensure
  * d * (max_j range_j)^2 < 2^62 (checked: returns ORACLE_ERANGE).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -257,15 +258,61 @@ static int triangle_trivial(i64 A, i64 B, i64 eps2)
     return lhs < rhs;
 }
 
-/* Alg. 4 on a set held as an index list: drop every x with the triangle test
- * against pivot p and its nearest point's squared distance B. */
-static i64 prune_set(const int32_t *S, i64 *idx, i64 cnt, const int32_t *p, i64 B, int d, i64 eps2)
+/* Alg. 4, angle part (Def. 8, Thm. 1): lambda is the largest
+ *   lambda_y = arcsin(eps / dist(p,y)) + arccos(pq.py / (dist(p,q) dist(p,y)))
+ * over the points y of the other set O (index list oidx, ocnt points); a
+ * point x whose angle between pq and px exceeds lambda is trivial.  The
+ * paper's reals are doubles here.  arcsin and arccos are 1/2-Hoelder
+ * continuous (|acos a - acos b| <= pi * sqrt(|a - b| / 2)) and their
+ * arguments are a few correctly rounded operations on exact integers
+ * (relative error a few units of 2^-53), so the computed angles are within
+ * 1e-7 of the exact ones: x is removed only when its angle exceeds lambda by
+ * ANGLE_MARGIN, which keeps every removal one the exact test makes. */
+#define ANGLE_MARGIN 1e-6
+
+static i64 dot_from(const int32_t *o, const int32_t *u, const int32_t *v, int d)
+{
+    i64 s = 0;
+    for (int j = 0; j < d; ++j)
+        s += ((i64)u[j] - o[j]) * ((i64)v[j] - o[j]);
+    return s;
+}
+
+static double clamp1(double v) { return v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v); }
+
+static double angle_lambda(const int32_t *O, const i64 *oidx, i64 ocnt, const int32_t *p, const int32_t *q,
+                           int d, i64 eps2)
+{
+    const double a = sqrt((double)sqdist(p, q, d)), eps = sqrt((double)eps2);
+    double lambda = 0.0;
+    for (i64 k = 0; k < ocnt; ++k) {
+        const int32_t *y = O + oidx[k] * d;
+        const double b = sqrt((double)sqdist(p, y, d));
+        const double ly = asin(clamp1(eps / b)) + acos(clamp1((double)dot_from(p, q, y, d) / (a * b)));
+        if (ly > lambda) lambda = ly;
+    }
+    return lambda;
+}
+
+/* Alg. 4 on a set held as an index list: drop every x that the triangle test
+ * (pivot p, nearest partner q at squared distance B) or the angle test
+ * (bound lambda) shows to be trivial. */
+static i64 prune_set(const int32_t *S, i64 *idx, i64 cnt, const int32_t *p, const int32_t *q, i64 B,
+                     double lambda, int d, i64 eps2)
 {
     i64 kept = 0;
+    const double a = sqrt((double)B);
     for (i64 k = 0; k < cnt; ++k) {
-        i64 A = sqdist(S + idx[k] * d, p, d);
-        if (!triangle_trivial(A, B, eps2))
-            idx[kept++] = idx[k];
+        const int32_t *x = S + idx[k] * d;
+        i64 A = sqdist(x, p, d);
+        if (triangle_trivial(A, B, eps2))
+            continue;
+        if (A > 0) {
+            const double theta = acos(clamp1((double)dot_from(p, q, x, d) / (a * sqrt((double)A))));
+            if (lambda + ANGLE_MARGIN < theta)
+                continue;
+        }
+        idx[kept++] = idx[k];
     }
     return kept;
 }
@@ -301,12 +348,12 @@ static int fastmerging(const int32_t *A, i64 na, const int32_t *B, i64 nb, int d
         i64 kq = nearest(B, ib, cb, p, d, &dpq);
         const int32_t *q = B + ib[kq] * d;
         if (dpq <= eps2) { ans = 1; break; }
-        ca = prune_set(A, ia, ca, p, dpq, d, eps2);
+        ca = prune_set(A, ia, ca, p, q, dpq, angle_lambda(B, ib, cb, p, q, d, eps2), d, eps2);
         if (ca == 0) break;
         i64 kp = nearest(A, ia, ca, q, d, &dpq);
         p = A + ia[kp] * d;
         if (dpq <= eps2) { ans = 1; break; }
-        cb = prune_set(B, ib, cb, q, dpq, d, eps2);
+        cb = prune_set(B, ib, cb, q, p, dpq, angle_lambda(A, ia, ca, q, p, d, eps2), d, eps2);
     }
     if (iters) *iters = rounds;
     return ans;
@@ -543,8 +590,9 @@ static int cmp_by_m(const void *pa, const void *pb)
 }
 
 /* GriT-DBSCAN(-LDF) on the CPU.  merge_mode 0 decides each merge by Def. 7
- * directly, merge_mode 1 by FastMerging (Alg. 5).  stats (may be NULL)
- * receives {C, merge tests run, max FastMerging rounds, core grids}. */
+ * directly, merge_mode 1 by FastMerging (Alg. 5).  stats (may be NULL, else
+ * 20 entries) receives {C, merge tests run, max FastMerging rounds, core
+ * grids}, then FastMerging calls by rounds 1..15 and >= 16. */
 int oracle_grid(const int32_t *X, long long n, int d, long long eps2, int minpts,
                 int32_t *labels, uint8_t *is_core, int merge_mode, long long *stats)
 {
@@ -620,6 +668,8 @@ int oracle_grid(const int32_t *X, long long n, int d, long long eps2, int minpts
      * the pair is skipped when union-find already joins them, else merged
      * when MinDist(s_i, s_j) <= eps (Def. 6). */
     i64 ncore = 0, tests = 0, max_rounds = 0;
+    if (stats)
+        for (int t = 4; t < 20; ++t) stats[t] = 0;
     for (i64 c = 0; c < C; ++c) {
         parent[c] = c;
         if (m[c] > 0) ord[ncore++] = c;
@@ -638,6 +688,7 @@ int oracle_grid(const int32_t *X, long long n, int d, long long eps2, int minpts
                                       : fastmerging(A, na, B, nb, d, eps2, ia, ib, &rounds);
             tests++;
             if (rounds > max_rounds) max_rounds = rounds;
+            if (stats && merge_mode == 1) stats[4 + (rounds < 16 ? rounds : 16) - 1]++;
             if (yes) uf_union(parent, ci, cj);
         }
     }

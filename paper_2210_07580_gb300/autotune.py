@@ -29,13 +29,23 @@ PER_GROUP = {
     "merge_lane": ([1, 4, 16, 64], ["merge"]),
     "merge_small": ([64, 128, 256], ["merge"]),
     "core_bands": ([0, 128, 4096], ["core"]),
+    "merge_order": ([0, 1], ["merge_order", "merge"]),
+    "core_mode": ([0, 1], ["core"]),
 }
 PER_BATCH = {
     "fm_blocks": ([152 * 2, 152 * 8, 152 * 32], ["merge"]),
     "walk_blocks": ([152 * 8, 152 * 32, 152 * 64], ["walk"]),
 }
 DEFAULTS = {"merge_budget": 2, "merge_lane": 16, "merge_small": 128, "core_bands": 128, "fm_blocks": 152 * 8,
-            "walk_blocks": 152 * 32}
+            "walk_blocks": 152 * 32, "merge_order": 1}
+
+
+def default_value(knob: str, d: int) -> int:
+    """The library's built-in value of a knob for dimension d (the core
+    counting form depends on the dimension: a warp per grid up to d = 4)."""
+    if knob == "core_mode":
+        return 1 if 1 <= d <= 4 else 0
+    return DEFAULTS[knob]
 
 
 def bucket_of(n: int) -> int:
@@ -108,7 +118,7 @@ def tune(instances, device: int = 0, reps: int = 3, log=print) -> dict:
     descend(_Runner(ctx, instances), 0, BUCKET_MAX[-1], PER_BATCH)
     ctx.close()
     # drop entries equal to the built-in default
-    entries = [e for e in ordered(table) if e[3] != DEFAULTS[e[0]] or e[0] in PER_BATCH]
+    entries = [e for e in ordered(table) if e[3] != default_value(e[0], e[1]) or e[0] in PER_BATCH]
     return {"entries": [{"knob": k, "d": d, "n_max": n, "value": v} for k, d, n, v in entries], "log": records}
 
 

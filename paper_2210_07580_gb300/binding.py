@@ -32,7 +32,8 @@ class GdTuning(ctypes.Structure):
 
 
 # gd_knob of include/gdbscan.h
-KNOBS = {"merge_budget": 1, "merge_lane": 2, "merge_small": 3, "core_bands": 4, "fm_blocks": 5, "walk_blocks": 6}
+KNOBS = {"merge_budget": 1, "merge_lane": 2, "merge_small": 3, "core_bands": 4, "fm_blocks": 5, "walk_blocks": 6,
+         "merge_order": 7, "core_mode": 8}
 # tuning table shipped with the package (written by autotune.py on a GB300)
 DEFAULT_TUNING = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
@@ -83,6 +84,12 @@ def load_library(path: str | None = None):
         lib.gd_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.c_int]
         lib.gd_stage_times.restype = ctypes.c_int
+        lib.gd_set_stats.argtypes = [vp, ctypes.c_int]
+        lib.gd_set_stats.restype = ctypes.c_int
+        lib.gd_run_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
+        lib.gd_run_stats.restype = ctypes.c_int
+        lib.gd_distance_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        lib.gd_distance_peak.restype = ctypes.c_int
         lib.gd_ctx_bytes.argtypes = [vp]
         lib.gd_ctx_bytes.restype = ctypes.c_size_t
         lib.gd_ctx_trim.argtypes = [vp]
@@ -283,6 +290,18 @@ class Context:
     def set_timing(self, enable: bool):
         self._check(self._lib.gd_set_timing(self._h, 1 if enable else 0))
 
+    def set_stats(self, enable: bool):
+        """Keep run statistics (merge outcomes, FastMerging rounds, count
+        rows) for each following call; such calls are slower."""
+        self._check(self._lib.gd_set_stats(self._h, 1 if enable else 0))
+
+    def run_stats(self) -> dict:
+        """The statistics of the last call (empty if it kept none)."""
+        vals = (ctypes.c_int64 * 64)()
+        names = (ctypes.c_char_p * 64)()
+        k = self._lib.gd_run_stats(self._h, vals, names, 64)
+        return {names[i].decode(): int(vals[i]) for i in range(k)}
+
     def stage_times(self) -> dict:
         ms = (ctypes.c_float * 32)()
         names = (ctypes.c_char_p * 32)()
@@ -314,6 +333,18 @@ def dbscan_noalloc(X, eps2: int, minpts: int, labels=None, is_core=None, stream=
     if st != GD_OK:
         raise GdError(st, lib.gd_status_str(st).decode())
     return labels, is_core
+
+
+def distance_peak(d: int, device: int = 0) -> float:
+    """gd_distance_peak: squared distances per second the GPU can evaluate
+    in d dimensions from registers alone (the ALU ceiling of the distance
+    loops)."""
+    lib = load_library()
+    v = ctypes.c_double()
+    st = lib.gd_distance_peak(int(device), int(d), ctypes.byref(v))
+    if st != GD_OK:
+        raise GdError(st, lib.gd_status_str(st).decode())
+    return float(v.value)
 
 
 def workspace_bytes(n: int, d: int) -> int:

@@ -101,6 +101,7 @@ struct gd_ctx {
     DevBuf io;  // device copies for gd_dbscan_host
     cudaEvent_t ev[kStageEvents] = {};
     bool timing = false;
+    bool stats = false;
     float stage_ms[kStages + 1] = {};   // the stages, then the sort's downsweeps
     cudaEvent_t sev[2 * kSortEventPairs] = {};
     int nstages = 0;
@@ -147,6 +148,7 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     ctx->mem.st = st;
     ctx->mem.err = &ctx->err;
     ctx->info = RunInfo();
+    ctx->info.want_stats = ctx->stats;
     const long long l0 = t_launches;
     gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning,
                             &ctx->graphs, ctx->timing ? ctx->sev : nullptr);
@@ -331,7 +333,7 @@ gd_status gd_set_tuning(gd_ctx* ctx, const gd_tuning* entries, int count) {
 }
 
 gd_status gd_get_knob(const gd_ctx* ctx, int knob, int d, int64_t n, int32_t* value) {
-    if (!ctx || !value || knob_default(knob) == 0) return GD_EINVAL;
+    if (!ctx || !value || knob_default(knob, d) < 0) return GD_EINVAL;
     *value = ctx->tuning.value(knob, d, n);
     return GD_OK;
 }
@@ -372,6 +374,29 @@ gd_status gd_set_timing(gd_ctx* ctx, int enable) {
     ctx->timing = enable != 0;
     ctx->nstages = 0;
     return GD_OK;
+}
+
+gd_status gd_set_stats(gd_ctx* ctx, int enable) {
+    if (!ctx) return GD_EINVAL;
+    ctx->stats = enable != 0;
+    return GD_OK;
+}
+
+static const char* const kStatNames[kStatCount] = {
+    "pairs", "pairs_skipped", "pairs_box_no", "pairs_box_yes", "pairs_lane", "pairs_warp", "pairs_fastmerging",
+    "fm_yes", "fm_no", "fm_pruned_triangle", "fm_pruned_angle", "nonfull_points", "count_rows",
+    "dist_core", "dist_merge", "dist_fastmerging", "dist_labels",
+    "kappa_1", "kappa_2", "kappa_3", "kappa_4", "kappa_5", "kappa_6", "kappa_7", "kappa_8", "kappa_9",
+    "kappa_10", "kappa_11", "kappa_12", "kappa_13", "kappa_14", "kappa_15", "kappa_16_or_more"};
+
+int gd_run_stats(const gd_ctx* ctx, int64_t* values, const char** names, int max) {
+    if (!ctx || !ctx->have_run || !ctx->info.have_stats) return 0;
+    const int k = kStatCount < max ? kStatCount : max;
+    for (int i = 0; i < k; ++i) {
+        if (values) values[i] = (int64_t)ctx->info.stats[i];
+        if (names) names[i] = kStatNames[i];
+    }
+    return k;
 }
 
 int gd_stage_times(const gd_ctx* ctx, float* ms, const char** names, int max) {

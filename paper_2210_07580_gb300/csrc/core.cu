@@ -72,6 +72,35 @@ __global__ void nonfull_count_kernel(const Inst* __restrict__ ins, Flat f, long 
     }
 }
 
+// Statistics (not timed): for each non-full grid, its points and the rows of
+// its neighbour grids -- the points a count that stages every neighbour grid
+// once per non-full grid reads.
+__global__ void core_stats_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    FlatCursor cur;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = i - cur.lo;
+        const int m = I.cell_start[c + 1] - I.cell_start[c];
+        if (m >= I.p.minpts) continue;
+        unsigned long long rows = 0;
+        for (int t = I.nbr_start[c]; t < I.nbr_start[c + 1]; ++t) {
+            const int cc = I.nbr[t];
+            rows += (unsigned long long)(I.cell_start[cc + 1] - I.cell_start[cc]);
+        }
+        stat_add(I.stats, kStNonfull, (unsigned long long)m);
+        stat_add(I.stats, kStCountRows, rows);
+    }
+}
+
+cudaError_t launch_core_stats(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    core_stats_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     core_full_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
@@ -154,6 +183,7 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
 #pragma unroll
         for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];
         int cnt = 0;
+        unsigned ndist = 0;  // statistics: distances this warp evaluated
         const int t_begin = I.nbr_start[c], t_end = I.nbr_start[c + 1];
         const int* nbr = I.nbr;
         // whole grids
@@ -211,12 +241,188 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
                         hit = dd <= eps2;
                     }
                     cnt += __popc(__ballot_sync(kFull, hit));
+                    ndist += (unsigned)min(32, flat - k0);
                     if (cnt >= minpts) break;
                 }
             }
         }
-        if (lane == 0) I.core_s[i] = cnt >= minpts ? 1 : 0;
+        if (lane == 0) {
+            I.core_s[i] = cnt >= minpts ? 1 : 0;
+            stat_add(I.stats, kStDistCore, ndist);
+        }
     }
+}
+
+// One warp per grid g that is not full (per-grid form of core_point_kernel).
+// The grid's points -- 32 at a time -- are staged in shared memory; the warp
+// reads g's neighbour list and the neighbours' point boxes once per 32 list
+// entries (lane t loading entry t into shared memory) and applies them to
+// every point of g in turn, so a grid of m points reads its list once
+// instead of m times.  For each point p:
+//   pass 1, over the whole list: grids entirely within eps of p count whole;
+//   pass 2, while p is short of MinPts: the straddling grids' points are
+//     streamed as one flat sequence (lane k taking the k-th) -- for short
+//     lists nearest band first, as in core_point_kernel.
+// A point stops as soon as its count reaches MinPts.
+constexpr int kCoreWarps = 8;
+
+template <int D>
+__global__ void __launch_bounds__(32 * kCoreWarps)
+    core_grid_kernel(const Inst* __restrict__ ins, Flat f, long long total, int band_limit) {
+    constexpr int DP = Padded<D>::value;
+    __shared__ int sx[kCoreWarps][32][D];      // the grid's points (32 at a time)
+    __shared__ int sbox[kCoreWarps][2 * D][32];  // the entries' boxes: lo then hi, lane-major
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    FlatCursor cur;
+    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + wib; w < total; w += warps) {
+        cur.seek(f, w);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = w - cur.lo;
+        const int* cell_start = I.cell_start;
+        const int b = cell_start[c], m = cell_start[c + 1] - b;
+        const int minpts = I.p.minpts;
+        if (m >= minpts) continue;  // full: core_full_kernel set its flags
+        const long long eps2 = I.p.eps2;
+        const int* Xs = I.Xs;
+        const int* pbox = I.pbox;
+        const int* nbr = I.nbr;
+        const int t_begin = I.nbr_start[c], t_end = I.nbr_start[c + 1];
+        const int nbands = (t_end - t_begin) <= band_limit ? 3 : 1;
+        unsigned ndist = 0;  // statistics: distances this warp evaluated
+        // the entries t0 .. t0+31 into shared memory; returns the lane's
+        // entry's first point and size (0 past the list)
+        auto load_entries = [&](int t0, int* st_out) {
+            int sz = 0, st = 0;
+            if (t0 + lane < t_end) {
+                const int cc = nbr[t0 + lane];
+#pragma unroll
+                for (int j = 0; j < 2 * D; ++j) sbox[wib][j][lane] = pbox[(long long)cc * 2 * D + j];
+                st = cell_start[cc];
+                sz = cell_start[cc + 1] - st;
+            }
+            *st_out = st;
+            __syncwarp();
+            return sz;
+        };
+        for (int own0 = 0; own0 < m; own0 += 32) {
+            const int mo = min(32, m - own0);
+            if (lane < mo) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) sx[wib][lane][j] = Xs[(long long)(b + own0 + lane) * DP + j];
+            }
+            __syncwarp();
+            int cnt = 0;  // lane p < mo: the count of own point p
+            const unsigned own = mo == 32 ? kFull : ((1u << mo) - 1u);
+            // pass 1: whole grids
+            for (int t0 = t_begin; t0 < t_end; t0 += 32) {
+                int st0;
+                const int sz0 = load_entries(t0, &st0);
+                for (int p = 0; p < mo; ++p) {
+                    int whole = 0;
+                    if (sz0 > 0) {
+                        long long maxd = 0;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const long long x = sx[wib][p][j];
+                            const long long a = x - sbox[wib][j][lane], bb = sbox[wib][D + j][lane] - x;
+                            const long long fm = a > bb ? a : bb;
+                            maxd += fm * fm;
+                        }
+                        if (maxd <= eps2) whole = sz0;
+                    }
+                    whole = __reduce_add_sync(kFull, whole);
+                    if (lane == p) cnt += whole;
+                }
+                __syncwarp();
+                if (__ballot_sync(kFull, cnt >= minpts) == own) break;
+            }
+            // pass 2: straddling grids, per point still short of MinPts
+            for (int band = 0; band < nbands; ++band) {
+                unsigned pend = own & ~__ballot_sync(kFull, cnt >= minpts);
+                if (!pend) break;
+                const long long blo = band == 0 ? -1 : (band == 1 ? eps2 / 16 : eps2 / 4);
+                const long long bhi = nbands == 1 ? eps2 : (band == 0 ? eps2 / 16 : (band == 1 ? eps2 / 4 : eps2));
+                for (int t0 = t_begin; t0 < t_end && pend; t0 += 32) {
+                    int st0;
+                    const int sz0 = load_entries(t0, &st0);
+                    for (unsigned pp = pend; pp; pp &= pp - 1) {
+                        const int p = __ffs(pp) - 1;
+                        long long x[D];
+#pragma unroll
+                        for (int j = 0; j < D; ++j) x[j] = sx[wib][p][j];
+                        int cp = __shfl_sync(kFull, cnt, p);
+                        int sz = 0;
+                        if (sz0 > 0) {
+                            long long mind = 0, maxd = 0;
+#pragma unroll
+                            for (int j = 0; j < D; ++j) {
+                                const long long l = sbox[wib][j][lane], h = sbox[wib][D + j][lane];
+                                long long g = 0;
+                                if (l > x[j]) g = l - x[j];
+                                else if (x[j] > h) g = x[j] - h;
+                                mind += g * g;
+                                const long long a = x[j] - l, bb = h - x[j];
+                                const long long fm = a > bb ? a : bb;
+                                maxd += fm * fm;
+                            }
+                            if (maxd > eps2 && mind > blo && mind <= bhi) sz = sz0;
+                        }
+                        const int incl = warp_inclusive_scan(sz);
+                        const int flat = __shfl_sync(kFull, incl, 31);
+                        for (int k0 = 0; k0 < flat && cp < minpts; k0 += 32) {
+                            const int k = k0 + lane;
+                            int lo2 = 0, hi2 = 31;
+#pragma unroll
+                            for (int step = 0; step < 5; ++step) {
+                                const int mid = (lo2 + hi2) >> 1;
+                                if (__shfl_sync(kFull, incl, mid) > k)
+                                    hi2 = mid;
+                                else
+                                    lo2 = mid + 1;
+                            }
+                            const int gst = __shfl_sync(kFull, st0, lo2);
+                            const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
+                            bool hit = false;
+                            if (k < flat) {
+                                const long long qi = (long long)gst + (k - gex);
+                                long long dd = 0;
+#pragma unroll
+                                for (int j = 0; j < D; ++j) {
+                                    const long long t = (long long)Xs[qi * DP + j] - x[j];
+                                    dd += t * t;
+                                }
+                                hit = dd <= eps2;
+                            }
+                            cp += __popc(__ballot_sync(kFull, hit));
+                            ndist += (unsigned)min(32, flat - k0);
+                        }
+                        if (lane == p) cnt = cp;
+                        if (cp >= minpts) pend &= ~(1u << p);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (lane < mo) I.core_s[b + own0 + lane] = cnt >= minpts ? 1 : 0;
+            __syncwarp();
+        }
+        if (lane == 0) stat_add(I.stats, kStDistCore, ndist);
+    }
+}
+
+cudaError_t launch_core_grid(const Inst* ins, Flat cells, long long total, int d, int band_limit, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    long long nb = (total + kCoreWarps - 1) / kCoreWarps;
+    if (nb > kPersistBlocks) nb = kPersistBlocks;
+    switch (d) {
+#define GD_CG(DD) \
+    case DD: core_grid_kernel<DD><<<(int)nb, 32 * kCoreWarps, 0, st>>>(ins, cells, total, band_limit); break;
+        GD_CG(1) GD_CG(2) GD_CG(3) GD_CG(4) GD_CG(5) GD_CG(6) GD_CG(7) GD_CG(8)
+#undef GD_CG
+        default: return cudaErrorInvalidValue;
+    }
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limit, cudaStream_t st) {

@@ -59,6 +59,7 @@ struct Params {
     // index values, 2 = 128-bit key plus index values.
     int key_class;
     int pack_bits;
+    int ldf;          // merge order: 0 = touching pairs first, 1 = low density first (Section 5.2)
     int mn[kMaxD];    // per-dimension minimum coordinate
     int bits[kMaxD];  // bits of each identifier in the key
     int shift[kMaxD]; // bit offset of identifier j (dimension 0 most significant)
@@ -77,8 +78,7 @@ enum SmallSlot {
     kSmMaxCell = 18,    // largest grid
     kSmNnbr = 19,       // neighbour-list length
     kSmNonfull = 20,    // points of non-full grids
-    kSmPairsT = 21,     // touching candidate pairs
-    kSmPairsF = 22,     // other candidate pairs
+    kSmPairsT = 21,     // candidate pairs taken by the merge
     kSmHard0 = 23,      // pairs handed to FastMerging, wave 0
     kSmHard1 = 24,      // ... wave 1
     kSmPool = 26,       // [2] instance 0 only: 64-bit neighbour-pool counter
@@ -86,10 +86,41 @@ enum SmallSlot {
     kSmallInts = 64
 };
 
+// Run statistics (gd_set_stats): 64-bit counters per instance, kept only when
+// the context asks for them (Inst::stats non-null).  Slot names are in
+// kStatNames (api.cu); kStKappa is a histogram of FastMerging rounds.
+enum StatSlot {
+    kStPairs = 0,      // candidate pairs of neighbouring core grids
+    kStSkipped,        // ... skipped: the two grids were already in one set
+    kStBoxNo,          // ... decided "no" by the gap between the core boxes
+    kStBoxYes,         // ... decided "yes" by the core boxes' farthest corners
+    kStLane,           // ... decided by one lane's exact loop
+    kStWarp,           // ... decided by the warp's exact tiles
+    kStHanded,         // ... handed to FastMerging (Alg. 5)
+    kStFmYes,          // FastMerging answers
+    kStFmNo,
+    kStFmTriangle,     // points FastMerging removed by the triangle test (Alg. 4)
+    kStFmAngle,        // points it removed by the angle test (Alg. 4, Def. 8)
+    kStNonfull,        // points of non-full grids (their core flag is counted)
+    kStCountRows,      // rows of neighbour grids a count would stage once per non-full grid
+    kStDistCore,       // exact squared distances evaluated: core counting,
+    kStDistMerge,      // ... merging (lane loops and warp tiles),
+    kStDistFm,         // ... FastMerging (every pass, the angle bound included),
+    kStDistLabels,     // ... border labels
+    kStKappa,          // [kKappaBins] FastMerging rounds 1, 2, ..., then >= kKappaBins
+    kKappaBins = 16,
+    kStatCount = kStKappa + kKappaBins
+};
+
+__device__ __forceinline__ void stat_add(unsigned long long* stats, int slot, unsigned long long v) {
+    if (stats && v) atomicAdd(stats + slot, v);
+}
+
 // One instance: parameters and workspace, in device memory.
 struct Inst {
     Params p;
     int passes, digit_bits, tiles;  // radix-sort plan
+    unsigned long long* stats;      // [kStatCount] or null (statistics off)
     const int* X;
     int* labels;
     unsigned char* is_core;
@@ -120,10 +151,9 @@ struct Inst {
     int* nf_start;
     int* core_start;
     int* bbox;
-    int* pair_start;
-    int* pair_start_f;
-    int2* pairs;
-    int2* hard;
+    int* ldf_grid;  // low-density-first order: the grid at each slot (core grids by core count first)
+    int* ldf_ctr;  // [kLdfBuckets] bucket counts, then cursors
+    int2* hard;  // pairs handed to FastMerging: wave 0's, then wave 1's
     int* parent;
     int* cid_root;
     int* cell_cid;
@@ -386,20 +416,31 @@ cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaS
 // Core points (core.cu).
 cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+// Statistics only: non-full points and the rows a per-grid count would stage.
+cudaError_t launch_core_stats(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Non-full points of instances with dimension d (flat offsets on the device).
 cudaError_t launch_core_point(const Inst* ins, Flat nf_pts, int d, int band_limit, cudaStream_t st);
+// Non-full grids of instances with dimension d, one warp per grid (the grids
+// of `cells`; full grids are skipped).
+cudaError_t launch_core_grid(const Inst* ins, Flat cells, long long total, int d, int band_limit, cudaStream_t st);
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
-cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+// Low-density-first order of the grids (instances with p.ldf set): core
+// grids by ascending core-point count (buckets: exact counts below 64, then
+// powers of two), non-core grids last.
+constexpr int kLdfBuckets = 128;
+cudaError_t launch_ldf_order(const Inst* ins, const int* idx, int K, Flat cells, long long total, cudaStream_t st);
+
 cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-// Warp-level test of the candidate pairs of one wave (0: touching, 1: others)
-// of instances with dimension d; undecided pairs go to the instance's hard list.
-cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, int lane_limit,
-                              int small_set, cudaStream_t st);
+// Warp-level test of the candidate pairs of one wave (touching order: 0 =
+// touching pairs, 1 = the others; LDF order: wave 0 only), taken from the
+// neighbour lists of the grids of `cells` (instances of dimension d);
+// undecided pairs go to the instance's hard list.
+cudaError_t launch_merge_list(const Inst* ins, Flat cells, long long total, int wave, int d, int budget,
+                              int lane_limit, int small_set, cudaStream_t st);
 // FastMerging (Alg. 5) of the hard pairs of one wave: `blocks` blocks, block b
 // using the 2 * wpb bitmap words at scratch + 2 * wpb * b (wpb >= the largest
 // grid of the batch / 32 + 1).

@@ -85,7 +85,7 @@ cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cud
 // skipping grids whose cluster id cannot improve the best found so far or
 // whose core box is farther than eps; -1 (noise) if there is none.
 template <int D>
-__device__ __forceinline__ int border_label(const Inst& I, long long q, int c) {
+__device__ __forceinline__ int border_label(const Inst& I, long long q, int c, unsigned& ndist) {
     constexpr int DP = Padded<D>::value;
     int x[D];
 #pragma unroll
@@ -112,6 +112,7 @@ __device__ __forceinline__ int border_label(const Inst& I, long long q, int c) {
             int y[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) y[j] = Y[(long long)u * DP + j];
+            ++ndist;
             if (sqdist<D>(x, y) <= eps2) {
                 best = id;
                 break;
@@ -157,9 +158,11 @@ __global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ in
                 int lab[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) lab[u] = (o[u] >= 0 && core[u]) ? I.cell_cid[c[u]] : -1;
+                unsigned ndist = 0;  // statistics: distances evaluated
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (o[u] >= 0 && !core[u]) lab[u] = border_label<D>(I, i - cur.lo + 32 * u, c[u]);
+                    if (o[u] >= 0 && !core[u]) lab[u] = border_label<D>(I, i - cur.lo + 32 * u, c[u], ndist);
+                stat_add(I.stats, kStDistLabels, ndist);
                 // with core flags wanted: one packed word per point, split by
                 // label_split_kernel (half the scattered writes)
                 const bool packed = I.is_core != nullptr;

@@ -36,6 +36,8 @@ __global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long lon
             for (int q = b; q < e; ++q) m += I.core_s[q];
         }
         I.core_start[c] = m;
+        if (c == 0)
+            for (int b = 0; b < kLdfBuckets; ++b) I.ldf_ctr[b] = 0;
         for (int j = 0; j < d; ++j) {
             I.bbox[c * 2 * d + j] = 0x7fffffff;
             I.bbox[c * 2 * d + d + j] = (int)0x80000000;
@@ -180,86 +182,80 @@ cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, 
 
 
 
-// -------------------------------------------------------- candidate pairs
-// Pairs (i, j) of core grids with j in Nei(i) and j > i, in two waves:
-// touching grids (identifiers differ by at most 1 in every dimension) first,
-// all others after them.  Touching core grids are nearly always merged, so
-// once the first wave has joined them the union-find precheck skips most of
-// the second wave (the LDF idea of Section 5.2: establish clusters early so
-// that later checks can be skipped).
+// ------------------------------------------------ candidate pair orders
+// The merge takes every unordered pair of neighbouring core grids once,
+// straight from the neighbour lists (no pair array), in one of two orders
+// (Params::ldf):
+//   - touching first: grid i takes the pairs (i, j), j > i, of its forward
+//     list, in two waves -- touching grids (identifiers differ by at most 1
+//     in every dimension) first, all others after them.  Touching core grids
+//     are nearly always merged, so once the first wave has joined them the
+//     union-find precheck skips most of the second.
+//   - low density first (GriT-DBSCAN-LDF, Section 5.2): one wave in which the
+//     core grids are visited in ascending order of core-point count
+//     (launch_ldf_order), each taking the pairs it owns from its whole list
+//     (forward and backward parts): a pair belongs to its grid with fewer core
+//     points (ties: the lower index).  Clusters form among cheap pairs first
+//     and the precheck skips the costly ones.
 
-template <bool FILL>
-__global__ void __launch_bounds__(256) pair_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
-    // one warp per grid; the lanes take 32 list entries at a time
-    const int lane = lane_id();
-    const unsigned lt = lanemask_lt();
-    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+__device__ __forceinline__ int ldf_bucket(int m) {
+    if (m <= 0) return kLdfBuckets - 1;  // not a core grid: last
+    if (m < 64) return m - 1;
+    return 63 + (31 - __clz(m)) - 5;  // 64..127 -> 64, 128..255 -> 65, ...
+}
+
+__device__ __forceinline__ int core_m(const Inst& I, int c) { return I.core_start[c + 1] - I.core_start[c]; }
+
+// Pass 1: bucket counts (ldf_ctr zeroed by core_count_kernel).
+// Pass 2 (RANK): each grid's slot in the order, after the counts became
+// starts: ldf_grid[slot] = grid.
+template <bool RANK>
+__global__ void __launch_bounds__(256) ldf_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     FlatCursor cur;
-    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
-        cur.seek(f, w);
-        const Inst& I = ins[f.idx[cur.k]];
-        const long long c = w - cur.lo;
-        const int d = I.p.d, C = I.small[kSmCells];
-        const int* core_start = I.core_start;
-        const int* coord = I.cell_coord;
-        int kt = 0, kf = 0;
-        if (core_start[c + 1] > core_start[c]) {
-            int2* out_t = nullptr;
-            int2* out_f = nullptr;
-            if (FILL) {
-                out_t = I.pairs + I.pair_start[c];
-                out_f = I.pairs + I.pair_start[C] + I.pair_start_f[c];
-            }
-            const int gl = lane < d ? coord[c * d + lane] : 0;
-            // the grids j2 > c are the forward part of the list
-            const int t_end = I.nbr_start[c] + I.nbr_fwd[c];
-            for (int t0 = I.nbr_start[c]; t0 < t_end; t0 += 32) {
-                const int t = t0 + lane;
-                const int j2 = t < t_end ? I.nbr[t] : -1;
-                const bool keep = j2 > c && core_start[j2 + 1] > core_start[j2];
-                bool touching = true;
-                for (int j = 0; j < d; ++j) {
-                    const int gj = __shfl_sync(kFull, gl, j);
-                    if (keep) {
-                        const int dl = coord[(long long)j2 * d + j] - gj;
-                        if (dl > 1 || dl < -1) touching = false;
-                    }
-                }
-                const unsigned mt = __ballot_sync(kFull, keep && touching);
-                const unsigned mf = __ballot_sync(kFull, keep && !touching);
-                if (FILL && keep) {
-                    if (touching)
-                        out_t[kt + __popc(mt & lt)] = make_int2((int)c, j2);
-                    else
-                        out_f[kf + __popc(mf & lt)] = make_int2((int)c, j2);
-                }
-                kt += __popc(mt);
-                kf += __popc(mf);
-            }
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + lane_id();
+        const bool valid = i < total;
+        const Inst* I = nullptr;
+        long long c = 0;
+        int b = 0;
+        if (valid) {
+            cur.seek(f, i);
+            I = ins + f.idx[cur.k];
+            c = i - cur.lo;
+            if (!I->p.ldf) I = nullptr;
+            else b = ldf_bucket(core_m(*I, (int)c));
         }
-        if (!FILL && lane == 0) {
-            I.pair_start[c] = kt;
-            I.pair_start_f[c] = kf;
-        }
+        // lanes of different instances never share a counter: aggregate per instance
+        const unsigned long long key = I ? ((unsigned long long)(size_t)I << 8) | (unsigned)b : 0ull;
+        const unsigned peers = __match_any_sync(kFull, key);
+        const int leader = __ffs(peers) - 1;
+        int at = 0;
+        if (I && (int)lane_id() == leader) at = atomicAdd(I->ldf_ctr + b, __popc(peers));
+        at = __shfl_sync(kFull, at, leader) + __popc(peers & lanemask_lt());
+        if (RANK && I) I->ldf_grid[at] = (int)c;
     }
 }
 
-static int warp_blocks_for(long long warps) {
-    long long b = (warps * 32 + 255) / 256;
-    if (b > kPersistBlocks) b = kPersistBlocks;
-    return b < 1 ? 1 : (int)b;
+// Exclusive scan of each LDF instance's bucket counts (one block each).
+__global__ void __launch_bounds__(kLdfBuckets) ldf_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx) {
+    __shared__ int sm[33];
+    const Inst& I = ins[idx[blockIdx.x]];
+    if (!I.p.ldf) return;
+    const int v = I.ldf_ctr[threadIdx.x];
+    int total;
+    const int ex = block_exclusive_scan(v, sm, &total);
+    I.ldf_ctr[threadIdx.x] = ex;
 }
 
-cudaError_t launch_pair_count(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
-    if (total <= 0) return cudaSuccess;
-    pair_kernel<false><<<warp_blocks_for(total), 256, 0, st>>>(ins, cells, total);
+cudaError_t launch_ldf_order(const Inst* ins, const int* idx, int K, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0 || K <= 0) return cudaSuccess;
+    const int nb = blocks_for(total);
+    ldf_kernel<false><<<nb, 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pair_fill(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
-    if (total <= 0) return cudaSuccess;
-    pair_kernel<true><<<warp_blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    ldf_scan_kernel<<<K, kLdfBuckets, 0, st>>>(ins, idx);
+    GD_COUNT_LAUNCH();
+    ldf_kernel<true><<<nb, 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -355,7 +351,9 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 }
 
 // ----------------------------------------------------- the warp-level test
-// A warp takes 32 consecutive candidate pairs of a wave, one per lane:
+// One warp per core grid i (slot order: grid order, or the LDF order), over
+// the pairs (i, j) it takes from its list (see above), 32 at a time, one per
+// lane:
 //   1. skip if the grids are already in one set;
 //   2. the two box tests (they alone decide pairs of one-point grids);
 //   3. pairs of at most `lane_limit` point pairs are decided by the lane
@@ -363,136 +361,186 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 // The pairs still open are then taken one at a time by the whole warp: the
 // exact test over core points in 32 x 32 tiles (lane l holds a point of s_j,
 // points of s_i are broadcast), stopping at the first pair within eps.  Pairs
-// of two small sets (both at most `small_set` points) are decided in full; any other pair gets `budget` diagonal tiles (distinct chunks
-// of both sets), which finds a witness for nearly every pair that has many,
-// and is otherwise handed to the block-level FastMerging kernel -- in
-// particular a few points against thousands, where one scan of the large set
-// usually decides.
+// of two small sets (both at most `small_set` points) are decided in full;
+// any other pair gets `budget` diagonal tiles (distinct chunks of both sets),
+// which finds a witness for nearly every pair that has many, and is otherwise
+// handed to the block-level FastMerging kernel -- in particular a few points
+// against thousands, where one scan of the large set usually decides.  Hard
+// pairs of wave 1 are stored after wave 0's.
 template <int D>
 __global__ void __launch_bounds__(256)
-    merge_warp_kernel(const Inst* __restrict__ ins, Flat f, int wave, int budget, int lane_limit, int small_set) {
+    merge_list_kernel(const Inst* __restrict__ ins, Flat f, long long total, int wave, int budget, int lane_limit,
+                      int small_set) {
     constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long total = flat_total(f);
-    for (long long w0 = ((((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5)) * 32; w0 < total;
-         w0 += warps * 32) {
-        // ---- one pair per lane
-        const long long i = w0 + lane;
-        int inst = 0;
-        int2 pr = make_int2(0, 0);
-        bool open = false;
-        if (i < total) {
-            const int kk = flat_find(f, i);
-            inst = f.idx[kk];
-            const Inst& I = ins[inst];
-            const long long eps2 = I.p.eps2;
-            const int base = wave == 0 ? 0 : I.small[kSmPairsT];
-            pr = I.pairs[base + (i - f.off[kk])];
-            int* parent = I.parent;
-            const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
-            if (ra < 0 || rb < 0) {
-                set_status(I, kDevTimeout);
-            } else if (ra != rb) {
-                const int dec =
-                    box_decision<D>(I.bbox + (long long)pr.x * 2 * D, I.bbox + (long long)pr.y * 2 * D, eps2);
-                bool yes = dec == 1;
-                if (dec < 0) {
-                    const int mi = I.core_start[pr.x + 1] - I.core_start[pr.x];
-                    const int mj = I.core_start[pr.y + 1] - I.core_start[pr.y];
-                    if ((long long)mi * mj <= lane_limit) {
-                        const int* A = core_rows(I, pr.x, DP);
-                        const int* B = core_rows(I, pr.y, DP);
-                        for (int u = 0; u < mi && !yes; ++u) {
-                            int P[D];
+    FlatCursor cur;
+    int acc_inst = -1;
+    unsigned acc_pairs = 0;  // candidate pairs taken, flushed per instance
+    for (long long w = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
+        cur.seek(f, w);
+        const int inst = f.idx[cur.k];
+        const Inst& I = ins[inst];
+        if (inst != acc_inst) {
+            if (acc_inst >= 0 && lane == 0 && acc_pairs) atomicAdd(ins[acc_inst].small + kSmPairsT, (int)acc_pairs);
+            acc_inst = inst;
+            acc_pairs = 0;
+        }
+        const bool ldf = I.p.ldf != 0;
+        if (ldf && wave == 1) continue;
+        const long long slot = w - cur.lo;
+        const int c = ldf ? I.ldf_grid[slot] : (int)slot;
+        const int* core_start = I.core_start;
+        const int mc = core_start[c + 1] - core_start[c];
+        if (mc == 0) continue;
+        const int d = I.p.d;
+        const long long eps2 = I.p.eps2;
+        int* parent = I.parent;
+        unsigned long long* const stv = I.stats;
+        const int gl = lane < d ? I.cell_coord[(long long)c * d + lane] : 0;
+        const int t_begin = I.nbr_start[c];
+        const int t_end = ldf ? I.nbr_start[c + 1] : t_begin + I.nbr_fwd[c];
+        const int hard_base = wave == 0 ? 0 : I.small[kSmHard0];
+        for (int t0 = t_begin; t0 < t_end; t0 += 32) {
+            // ---- the lane's candidate pair (c, j2)
+            const int t = t0 + lane;
+            const int j2 = t < t_end ? I.nbr[t] : c;
+            const int mj = j2 != c ? core_start[j2 + 1] - core_start[j2] : 0;
+            bool keep;
+            if (ldf) {
+                keep = mj > 0 && (mc < mj || (mc == mj && c < j2));
+            } else {
+                bool touching = true;
+                for (int j = 0; j < d; ++j) {
+                    const int gj = __shfl_sync(kFull, gl, j);
+                    const int dl = I.cell_coord[(long long)j2 * d + j] - gj;
+                    if (dl > 1 || dl < -1) touching = false;
+                }
+                keep = j2 > c && mj > 0 && touching == (wave == 0);
+            }
+            bool open = false;
+            int outcome = -1;    // statistics: the slot that decided the lane's pair
+            unsigned ndist = 0;  // statistics: distances this lane evaluated
+            if (keep) {
+                const int ra = uf_find(parent, c), rb = uf_find(parent, j2);
+                if (ra < 0 || rb < 0) {
+                    set_status(I, kDevTimeout);
+                } else if (ra == rb) {
+                    outcome = kStSkipped;
+                } else {
+                    const int dec =
+                        box_decision<D>(I.bbox + (long long)c * 2 * D, I.bbox + (long long)j2 * 2 * D, eps2);
+                    bool yes = dec == 1;
+                    outcome = dec == 1 ? kStBoxYes : dec == 0 ? kStBoxNo : kStLane;
+                    if (dec < 0) {
+                        if ((long long)mc * mj <= lane_limit) {
+                            const int* A = core_rows(I, c, DP);
+                            const int* B = core_rows(I, j2, DP);
+                            for (int u = 0; u < mc && !yes; ++u) {
+                                int P[D];
 #pragma unroll
-                            for (int j = 0; j < D; ++j) P[j] = A[(long long)u * DP + j];
-                            for (int v = 0; v < mj; ++v) {
-                                int Q[D];
+                                for (int j = 0; j < D; ++j) P[j] = A[(long long)u * DP + j];
+                                for (int v = 0; v < mj; ++v) {
+                                    int Q[D];
 #pragma unroll
-                                for (int j = 0; j < D; ++j) Q[j] = B[(long long)v * DP + j];
-                                if (sqdist<D>(P, Q) <= eps2) {
-                                    yes = true;
-                                    break;
+                                    for (int j = 0; j < D; ++j) Q[j] = B[(long long)v * DP + j];
+                                    ++ndist;
+                                    if (sqdist<D>(P, Q) <= eps2) {
+                                        yes = true;
+                                        break;
+                                    }
                                 }
                             }
+                        } else {
+                            open = true;
+                            outcome = -1;
                         }
-                    } else {
-                        open = true;
+                    }
+                    if (yes && !uf_union(parent, c, j2)) set_status(I, kDevTimeout);
+                }
+            }
+            acc_pairs += __popc(__ballot_sync(kFull, keep));
+            if (stv) {
+                stat_add(stv, kStPairs, keep ? 1 : 0);
+                if (outcome >= 0) stat_add(stv, outcome, 1);
+                stat_add(stv, kStDistMerge, ndist);
+            }
+            // ---- the open pairs, one at a time, by the whole warp
+            unsigned pend = __ballot_sync(kFull, open);
+            while (pend) {
+                const int src = __ffs(pend) - 1;
+                pend &= pend - 1;
+                const int py = __shfl_sync(kFull, j2, src);
+                int same = 0;
+                if (lane == 0) {
+                    const int ra = uf_find(parent, c), rb = uf_find(parent, py);
+                    if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
+                    same = ra == rb;
+                }
+                if (__shfl_sync(kFull, same, 0)) {
+                    if (lane == 0) stat_add(stv, kStSkipped, 1);
+                    continue;
+                }
+                const int* A = core_rows(I, c, DP);
+                const int* B = core_rows(I, py, DP);
+                const int mi = mc;
+                const int mjj = core_start[py + 1] - core_start[py];
+                const int na = (mi + 31) >> 5, nb = (mjj + 31) >> 5;
+                const long long tiles = (long long)na * nb;
+                const bool exhaustive = mi <= small_set && mjj <= small_set;
+                const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
+                bool yes = false;
+                unsigned long long tile_dist = 0;
+                for (long long tt = 0; tt < limit; ++tt) {
+                    const int ta = exhaustive ? (int)(tt / nb) : (int)(tt % na);
+                    const int tb = (int)(tt % nb);
+                    const int a0 = ta << 5, b0 = tb << 5;
+                    const int ca = min(32, mi - a0);
+                    int P[D], Q[D];
+                    const bool vq = b0 + lane < mjj;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        P[j] = lane < ca ? A[(long long)(a0 + lane) * DP + j] : 0;
+                        Q[j] = vq ? B[(long long)(b0 + lane) * DP + j] : 0;
+                    }
+                    bool hit = false;
+                    tile_dist += (unsigned long long)ca * (unsigned long long)min(32, mjj - b0);
+                    for (int u = 0; u < ca; ++u) {
+                        int pt[D];
+#pragma unroll
+                        for (int j = 0; j < D; ++j) pt[j] = __shfl_sync(kFull, P[j], u);
+                        hit |= vq && sqdist<D>(pt, Q) <= eps2;
+                    }
+                    if (__any_sync(kFull, hit)) {
+                        yes = true;
+                        break;
                     }
                 }
-                if (yes && !uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
-            }
-        }
-        // ---- the open pairs, one at a time, by the whole warp
-        unsigned pend = __ballot_sync(kFull, open);
-        while (pend) {
-            const int src = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int oi = __shfl_sync(kFull, inst, src);
-            const int px = __shfl_sync(kFull, pr.x, src), py = __shfl_sync(kFull, pr.y, src);
-            const Inst& I = ins[oi];
-            const long long eps2 = I.p.eps2;
-            const int base = wave == 0 ? 0 : I.small[kSmPairsT];
-            int* parent = I.parent;
-            int same = 0;
-            if (lane == 0) {
-                const int ra = uf_find(parent, px), rb = uf_find(parent, py);
-                if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
-                same = ra == rb;
-            }
-            if (__shfl_sync(kFull, same, 0)) continue;
-            const int* A = core_rows(I, px, DP);
-            const int* B = core_rows(I, py, DP);
-            const int mi = I.core_start[px + 1] - I.core_start[px];
-            const int mj = I.core_start[py + 1] - I.core_start[py];
-            const int na = (mi + 31) >> 5, nb = (mj + 31) >> 5;
-            const long long tiles = (long long)na * nb;
-            const bool exhaustive = mi <= small_set && mj <= small_set;
-            const long long limit = exhaustive ? tiles : (tiles < budget ? tiles : budget);
-            bool yes = false;
-            for (long long t = 0; t < limit; ++t) {
-                const int ta = exhaustive ? (int)(t / nb) : (int)(t % na);
-                const int tb = (int)(t % nb);
-                const int a0 = ta << 5, b0 = tb << 5;
-                const int ca = min(32, mi - a0);
-                int P[D], Q[D];
-                const bool vq = b0 + lane < mj;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    P[j] = lane < ca ? A[(long long)(a0 + lane) * DP + j] : 0;
-                    Q[j] = vq ? B[(long long)(b0 + lane) * DP + j] : 0;
-                }
-                bool hit = false;
-                for (int u = 0; u < ca; ++u) {
-                    int pt[D];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) pt[j] = __shfl_sync(kFull, P[j], u);
-                    hit |= vq && sqdist<D>(pt, Q) <= eps2;
-                }
-                if (__any_sync(kFull, hit)) {
-                    yes = true;
-                    break;
-                }
-            }
-            const bool handed = !yes && limit < tiles;
-            if (lane == 0) {
-                if (yes) {
-                    if (!uf_union(parent, px, py)) set_status(I, kDevTimeout);
-                } else if (handed) {
-                    I.hard[base + atomicAdd(I.small + kSmHard0 + wave, 1)] = make_int2(px, py);
+                const bool handed = !yes && limit < tiles;
+                if (lane == 0) {
+                    stat_add(stv, handed ? kStHanded : kStWarp, 1);
+                    stat_add(stv, kStDistMerge, tile_dist);
+                    if (yes) {
+                        if (!uf_union(parent, c, py)) set_status(I, kDevTimeout);
+                    } else if (handed) {
+                        I.hard[hard_base + atomicAdd(I.small + kSmHard0 + wave, 1)] = make_int2(c, py);
+                    }
                 }
             }
         }
     }
+    if (acc_inst >= 0 && lane == 0 && acc_pairs) atomicAdd(ins[acc_inst].small + kSmPairsT, (int)acc_pairs);
 }
 
-cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int budget, int lane_limit,
-                              int small_set, cudaStream_t st) {
+cudaError_t launch_merge_list(const Inst* ins, Flat cells, long long total, int wave, int d, int budget,
+                              int lane_limit, int small_set, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    long long b = (total * 32 + 255) / 256;
+    if (b > kPersistBlocks) b = kPersistBlocks;
     switch (d) {
-#define GD_MW(DD)                                                                                          \
-    case DD:                                                                                               \
-        merge_warp_kernel<DD><<<kPersistBlocks, 256, 0, st>>>(ins, pairs, wave, budget, lane_limit, small_set); \
+#define GD_MW(DD)                                                                                             \
+    case DD:                                                                                                  \
+        merge_list_kernel<DD><<<(int)b, 256, 0, st>>>(ins, cells, total, wave, budget, lane_limit, small_set); \
         break;
         GD_MW(1) GD_MW(2) GD_MW(3) GD_MW(4) GD_MW(5) GD_MW(6) GD_MW(7) GD_MW(8)
 #undef GD_MW
@@ -506,17 +554,34 @@ cudaError_t launch_merge_warp(const Inst* ins, Flat pairs, int wave, int d, int 
 // Alg. 5 for one pair per block, exact:
 //   p starts at the point of s_i nearest to the centre of s_j's box;
 //   q = argmin over s_j of dist(p, .); yes if dist(p, q) <= eps;
-//   otherwise prune s_i around p (Alg. 4, triangle part: x goes when
-//   dist(x, p) < dist(p, q) - eps, decided in integers), take p = argmin over
-//   the rest of s_i of dist(., q), test, prune s_j around q, and repeat;
+//   otherwise prune s_i around p (Alg. 4), take p = argmin over the rest of
+//   s_i of dist(., q), test, prune s_j around q, and repeat;
 //   no as soon as a pruning empties a set (Thm. 2: only points with no
 //   partner within eps are ever removed).
+// Alg. 4 removes x from the set pruned around pivot p (nearest partner q,
+// dist(p, q) > eps) when
+//   - triangle: dist(x, p) < dist(p, q) - eps, decided in exact integers;
+//   - angle (Def. 8, Thm. 1): the angle between pq and px exceeds
+//     lambda = max over the other set's live points y of
+//     arcsin(eps / |py|) + angle(pq, py).
+// The angle test runs in double precision on exact int64 inputs (squared
+// lengths and dot products) and prunes only with a margin: cos(angle(pq, px))
+// < cos(lambda) - kAngleMargin, and never when some lambda_y may reach pi
+// (cos is decreasing only on [0, pi]).  Every quantity is a handful of
+// correctly rounded IEEE operations (+, -, *, /, sqrt: relative error at
+// most 2^-53 each; Higham, "Accuracy and Stability of Numerical
+// Algorithms", 2nd ed., Sec. 2.2 and Lemma 3.1), so the computed cosines are
+// within 1e-14 of the exact ones; the margin of 1e-9 makes every angle
+// prune one the exact test would also make.  Pruning less never changes the
+// answer (Thm. 2), only the number of rounds.
 // s_i is the smaller set.  Each pruning is fused with the next argmin, so a
-// round is two passes over the live points.  Every round removes p from s_i
-// and q from s_j, so the loop ends after at most min(m_i, m_j) rounds.  The
-// live sets are bitmaps (one word per 32 points) in the block's slice of the
-// scratch.  The angle-based part of Alg. 4 is not used: it needs arcsin and
-// arccos, and only saves work.
+// round is three passes over live points (the angle bound, then the pruning
+// with the argmin).  Every round removes p from s_i and q from s_j, so the
+// loop ends after at most min(m_i, m_j) rounds.  The live sets are bitmaps
+// (one word per 32 points) in the block's slice of the scratch.
+
+constexpr double kAngleMargin = 1e-9;
+constexpr double kNoAngle = -4.0;  // cos(lambda) sentinel: no angle pruning
 
 __device__ __forceinline__ bool triangle_trivial(long long A, long long B, long long eps2) {
     // x is trivial iff sqrt(A) + sqrt(eps2) < sqrt(B)
@@ -569,6 +634,20 @@ __device__ __forceinline__ BestPt block_best(BestPt v, int cnt, BestPt* sb, int*
     return r;
 }
 
+// Block-wide minimum of a double; every thread gets it.
+__device__ __forceinline__ double block_min(double v, double* sd) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(kFull, v, o));
+    if (lane == 0) sd[warp] = v;
+    __syncthreads();
+    double r = sd[0];
+#pragma unroll
+    for (int w = 1; w < kFmWarps; ++w) r = fmin(r, sd[w]);
+    __syncthreads();
+    return r;
+}
+
 template <int D, int DP>
 __device__ __forceinline__ void load_pt(const int* __restrict__ S, int k, int* x) {
 #pragma unroll
@@ -586,15 +665,67 @@ __device__ __forceinline__ long long sqdist_ll(const int* a, const long long* b)
     return s;
 }
 
+// (u - o) . (v - o) for integer points; |result| < 2^62 (Cauchy-Schwarz and
+// the coordinate range check d * R^2 < 2^62).
+template <int D>
+__device__ __forceinline__ long long dot_from(const long long* o, const long long* u, const int* v) {
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) s += (u[j] - o[j]) * ((long long)v[j] - o[j]);
+    return s;
+}
+
+// cos(lambda) of the angle test for pruning around pivot p with nearest
+// partner q (|pq|^2 = a2 > eps2): the minimum over the live points y of the
+// other set S of cos(arcsin(eps / |py|) + angle(pq, py)), or kNoAngle when
+// some lambda_y may reach pi.
+template <int D, int DP>
+__device__ double fm_cos_lambda(const int* __restrict__ S, int m, const unsigned* live, const long long* p,
+                                const long long* q, long long a2, long long eps2, double* sd,
+                                unsigned long long* ndist) {
+    const int lane = lane_id();
+    const double a = sqrt((double)a2), eps = sqrt((double)eps2);
+    double best = 2.0;
+    int nlive = 0;
+    for (int base = 0; base < m; base += kFmBlock) {
+        const int k = base + threadIdx.x;
+        const unsigned word = k < m ? live[k >> 5] : 0u;
+        if ((word >> lane) & 1u) {
+            int y[D];
+            load_pt<D, DP>(S, k, y);
+            const long long b2 = sqdist_ll<D>(y, p);  // >= a2 > eps2 (q is p's nearest)
+            const long long dt = dot_from<D>(p, q, y);
+            const double b = sqrt((double)b2);
+            const double sin_a = eps / b, cos_a = sqrt((double)(b2 - eps2)) / b;
+            double cos_t = (double)dt / (a * b);
+            cos_t = fmin(1.0, fmax(-1.0, cos_t));
+            const double sin_t = sqrt(fmax(0.0, 1.0 - cos_t * cos_t));
+            // lambda_y < pi  <=>  cos(theta) + cos(alpha) > 0
+            const double v = (cos_t + cos_a > kAngleMargin) ? cos_a * cos_t - sin_a * sin_t : kNoAngle;
+            best = fmin(best, v);
+            ++nlive;
+        }
+    }
+    if (ndist) {
+        nlive = __reduce_add_sync(kFull, nlive);
+        if (lane == 0) atomicAdd(ndist, (unsigned long long)nlive);
+    }
+    return block_min(best, sd);
+}
+
 // One pass over a live set S (bitmap `live`, m points): optionally prune
-// around pivot `piv` with nearest-distance B, and return the argmin of the
-// distance to `tgt` over the points kept, plus their count.
+// around pivot `piv` (nearest partner `near` of the other set at squared
+// distance B, cos(lambda) = cl), and return the argmin of the distance to
+// `near` over the points kept, plus their count.  Without pruning, `near` is
+// only the target of the argmin.
 template <int D, int DP, bool PRUNE>
 __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, const long long* piv, long long B,
-                          const long long* tgt, long long eps2, BestPt* sb, int* sc, int* count) {
+                          const long long* near, double cl, long long eps2, BestPt* sb, int* sc, int* count,
+                          int* pruned_tri, int* pruned_ang, unsigned long long* ndist) {
     const int lane = lane_id();
     BestPt best{0x7fffffffffffffffll, 0x7fffffff};
-    int cnt = 0;
+    int cnt = 0, ntri = 0, nang = 0;
+    const double sqB = PRUNE ? sqrt((double)B) : 0.0;
     for (int base = 0; base < m; base += kFmBlock) {
         const int k = base + threadIdx.x;
         // the 32 lanes of a warp hold one bitmap word's 32 points; lane 0 has
@@ -604,7 +735,19 @@ __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, cons
         int x[D];
         if (alive) {
             load_pt<D, DP>(S, k, x);
-            if (PRUNE && triangle_trivial(sqdist_ll<D>(x, piv), B, eps2)) alive = false;
+            if (PRUNE) {
+                const long long A = sqdist_ll<D>(x, piv);
+                if (triangle_trivial(A, B, eps2)) {
+                    alive = false;
+                    ++ntri;
+                } else if (cl > kNoAngle && A > 0) {
+                    const double cg = (double)dot_from<D>(piv, near, x) / (sqB * sqrt((double)A));
+                    if (cg < cl - kAngleMargin) {
+                        alive = false;
+                        ++nang;
+                    }
+                }
+            }
         }
         if (PRUNE) {
             const unsigned nw = __ballot_sync(kFull, alive);
@@ -612,7 +755,20 @@ __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, cons
         }
         if (alive) {
             cnt++;
-            best = better(best, BestPt{sqdist_ll<D>(x, tgt), k});
+            best = better(best, BestPt{sqdist_ll<D>(x, near), k});
+        }
+    }
+    if (pruned_tri) {
+        // statistics: a pruning pass evaluates the distance to the pivot for
+        // every live point and to the target for every kept one
+        const int nlive = __reduce_add_sync(kFull, cnt + ntri + nang);
+        const int nkept = __reduce_add_sync(kFull, cnt);
+        ntri = __reduce_add_sync(kFull, ntri);
+        nang = __reduce_add_sync(kFull, nang);
+        if (lane == 0) {
+            atomicAdd(pruned_tri, ntri);
+            atomicAdd(pruned_ang, nang);
+            atomicAdd(ndist, (unsigned long long)(PRUNE ? nlive + nkept : nkept));
         }
     }
     return block_best(best, cnt, sb, sc, count);
@@ -624,7 +780,10 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
     constexpr int DP = Padded<D>::value;
     __shared__ BestPt sb[kFmWarps];
     __shared__ int sc[kFmWarps];
+    __shared__ double sd[kFmWarps];
     __shared__ int s_same;
+    __shared__ int s_tri, s_ang;  // statistics: points pruned by each test
+    __shared__ unsigned long long s_dist;  // statistics: distances evaluated
     unsigned* live_a = scratch + (long long)blockIdx.x * 2 * wpb;
     unsigned* live_b = live_a + wpb;
     const long long total = flat_total(f);
@@ -632,18 +791,28 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
         const int kk = flat_find(f, h);
         const Inst& I = ins[f.idx[kk]];
         const long long eps2 = I.p.eps2;
-        const int base = wave == 0 ? 0 : I.small[kSmPairsT];
+        const int base = wave == 0 ? 0 : I.small[kSmHard0];
         const int2 pr = I.hard[base + (h - f.off[kk])];
         int* parent = I.parent;
+        unsigned long long* const stv = I.stats;
         if (threadIdx.x == 0) {
             const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
             if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
             s_same = ra == rb;
+            s_tri = 0;
+            s_ang = 0;
+            s_dist = 0;
         }
         __syncthreads();
         const bool same = s_same;
         __syncthreads();
-        if (same) continue;
+        if (same) {
+            if (threadIdx.x == 0) stat_add(stv, kStSkipped, 1);
+            continue;
+        }
+        int* const ptri = stv ? &s_tri : nullptr;
+        int* const pang = stv ? &s_ang : nullptr;
+        unsigned long long* const pdist = stv ? &s_dist : nullptr;
 
         // s_i is the smaller set: each round removes at least its pivot, and
         // a small set is usually emptied by the first pruning
@@ -669,25 +838,27 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
 #pragma unroll
         for (int j = 0; j < D; ++j) tgt[j] = ((long long)bj[j] + bj[D + j]) / 2;
         int cnt;
-        BestPt bp = fm_pass<D, DP, false>(A, ma, live_a, nullptr, 0, tgt, eps2, sb, sc, &cnt);
+        BestPt bp = fm_pass<D, DP, false>(A, ma, live_a, nullptr, 0, tgt, 0.0, eps2, sb, sc, &cnt, ptri, pang, pdist);
         int px[D];
         load_pt<D, DP>(A, bp.i, px);
 #pragma unroll
         for (int j = 0; j < D; ++j) piv[j] = px[j];
-        BestPt bq = fm_pass<D, DP, false>(B, mb, live_b, nullptr, 0, piv, eps2, sb, sc, &cnt);
+        BestPt bq = fm_pass<D, DP, false>(B, mb, live_b, nullptr, 0, piv, 0.0, eps2, sb, sc, &cnt, ptri, pang, pdist);
         bool yes = false;
+        int kappa = 1;  // rounds: one per nearest point q found in s_j
         for (int round = 0; round <= ma + mb; ++round) {
             if (bq.d <= eps2) {
                 yes = true;
                 break;
             }
-            // prune s_i around p (nearest in s_j at distance^2 bq.d), then p' = argmin over s_i of dist(., q)
+            // prune s_i around p (nearest partner q at distance^2 bq.d), then p' = argmin over s_i of dist(., q)
             int qx[D];
             load_pt<D, DP>(B, bq.i, qx);
             long long qv[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) qv[j] = qx[j];
-            bp = fm_pass<D, DP, true>(A, ma, live_a, piv, bq.d, qv, eps2, sb, sc, &cnt);
+            double cl = fm_cos_lambda<D, DP>(B, mb, live_b, piv, qv, bq.d, eps2, sd, pdist);
+            bp = fm_pass<D, DP, true>(A, ma, live_a, piv, bq.d, qv, cl, eps2, sb, sc, &cnt, ptri, pang, pdist);
             if (cnt == 0) break;
             if (bp.d <= eps2) {
                 yes = true;
@@ -696,12 +867,21 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
             load_pt<D, DP>(A, bp.i, px);
 #pragma unroll
             for (int j = 0; j < D; ++j) piv[j] = px[j];
-            // prune s_j around q (nearest in s_i at distance^2 bp.d), then q' = argmin over s_j of dist(p', .)
-            bq = fm_pass<D, DP, true>(B, mb, live_b, qv, bp.d, piv, eps2, sb, sc, &cnt);
+            // prune s_j around q (nearest partner p' at distance^2 bp.d), then q' = argmin over s_j of dist(p', .)
+            cl = fm_cos_lambda<D, DP>(A, ma, live_a, qv, piv, bp.d, eps2, sd, pdist);
+            bq = fm_pass<D, DP, true>(B, mb, live_b, qv, bp.d, piv, cl, eps2, sb, sc, &cnt, ptri, pang, pdist);
             if (cnt == 0) break;
+            ++kappa;
         }
-        if (yes && threadIdx.x == 0) {
-            if (!uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
+        if (threadIdx.x == 0) {
+            if (yes && !uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
+            if (stv) {
+                stat_add(stv, yes ? kStFmYes : kStFmNo, 1);
+                stat_add(stv, kStKappa + min(kappa, (int)kKappaBins) - 1, 1);
+                stat_add(stv, kStFmTriangle, (unsigned long long)s_tri);
+                stat_add(stv, kStFmAngle, (unsigned long long)s_ang);
+                stat_add(stv, kStDistFm, s_dist);
+            }
         }
         __syncthreads();
     }

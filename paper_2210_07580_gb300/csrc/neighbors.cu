@@ -246,13 +246,31 @@ __device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* l
     *hi = l2;
 }
 
+// The key offsets delta in [lo, hi] of one level whose squared gap (table
+// gap2, index delta + kMaxR, non-decreasing in |delta| on each side, 0 at
+// delta = 0) is within `rem`; lo >= 0 when `fwd` (a range on the query's own
+// path).  rem >= 0, so delta = 0 always qualifies.
+__device__ __forceinline__ void budget_window(const long long* gap2, long long rem, long long r, bool fwd, int* lo,
+                                              int* hi) {
+    int h = 0, l = 0;
+#pragma unroll
+    for (int t = 1; t <= kMaxR; ++t)
+        if (t <= r && gap2[kMaxR + t] <= rem) h = t;
+    if (!fwd) {
+#pragma unroll
+        for (int t = 1; t <= kMaxR; ++t)
+            if (t <= r && gap2[kMaxR - t] <= rem) l = -t;
+    }
+    *lo = l;
+    *hi = h;
+}
+
 struct WalkShared {
     int lo[kWalkWarps][kWalkStack];
     int hi[kWalkWarps][kWalkStack];
     long long part[kWalkWarps][kWalkStack];
     signed char lvl[kWalkWarps][kWalkStack];
     long long qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];    // query point box
-    long long klo[kWalkWarps][kMaxD], khi[kWalkWarps][kMaxD];    // key window g_j -+ r
     int g[kWalkWarps][kMaxD];                                    // query identifier
     // squared gap in dimension j between the query's point box and the cell
     // at key offset delta = key - g_j, index delta + kMaxR (saturated at 2^62,
@@ -307,8 +325,6 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const long long g = gi, ql = I.pbox[c * 2 * d + lane], qh = I.pbox[c * 2 * d + d + lane];
             sh.qlo[w][lane] = ql;
             sh.qhi[w][lane] = qh;
-            sh.klo[w][lane] = g - r;
-            sh.khi[w][lane] = g + r;
             sh.g[w][lane] = gi;
             // the cell at offset delta spans [cl + delta s, cl + delta s + s - 1]
             const long long cl = (long long)I.p.mn[lane] + g * s;
@@ -330,9 +346,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         int* const buf = sh.buf[w];
         int top = 0;
         {
-            // the root range: level-0 keys in [g_0, g_0 + r], on the query's path
+            // the root range: level-0 keys in [g_0, g_0 + r] (on the query's
+            // path), narrowed to the offsets whose gap alone is within eps
             int a0 = 0, b0 = I.small[kSmLevelCount];
-            narrow_range(I.lv_key[0], &a0, &b0, sh.g[w][0], sh.khi[w][0]);
+            int dlo, dhi;
+            budget_window(sh.gap2[w][0], eps2, r, true, &dlo, &dhi);
+            narrow_range(I.lv_key[0], &a0, &b0, (long long)sh.g[w][0] + dlo, (long long)sh.g[w][0] + dhi);
             if (b0 > a0) {
                 if (lane == 0) {
                     slo[0] = a0;
@@ -435,9 +454,12 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             } else {
                 if (ok) {
                     // a child window: [g - r, g + r], or [g, g + r] below a node
-                    // on the query's own path
-                    const long long wlo = tight ? (long long)sh.g[w][J + 1] : sh.klo[w][J + 1];
-                    narrow_range(I.lv_key[J + 1], &clo, &chi, wlo, sh.khi[w][J + 1]);
+                    // on the query's own path, narrowed to the key offsets whose
+                    // gap still fits in what the path leaves of eps^2
+                    int dlo, dhi;
+                    budget_window(sh.gap2[w][J + 1], eps2 - off, r, tight, &dlo, &dhi);
+                    const long long g1 = sh.g[w][J + 1];
+                    narrow_range(I.lv_key[J + 1], &clo, &chi, g1 + dlo, g1 + dhi);
                     ok = chi > clo;
                 }
                 const unsigned m = __ballot_sync(kFull, ok);

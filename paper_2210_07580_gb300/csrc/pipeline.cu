@@ -19,8 +19,8 @@
 
 namespace gd {
 
-const char* const kStageNames[kStages] = {"bounds", "quantise", "sort",  "compact", "levels", "walk",
-                                          "core",   "core_pack", "pairs", "merge",   "labels"};
+const char* const kStageNames[kStages] = {"bounds", "quantise", "sort",        "compact", "levels", "walk",
+                                          "core",   "core_pack", "merge_order", "merge",   "labels"};
 
 namespace {
 
@@ -133,8 +133,8 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     I.nf_start = (int*)take((N + 1) * 4);
     I.core_start = (int*)take((N + 1) * 4);
     I.bbox = (int*)take(N * 2 * d * 4);
-    I.pair_start = (int*)take((N + 1) * 4);
-    I.pair_start_f = (int*)take((N + 1) * 4);
+    I.ldf_grid = (int*)take(N * 4);
+    I.ldf_ctr = (int*)take(kLdfBuckets * 4);
     I.parent = (int*)take(N * 4);
     I.cid_root = (int*)take(N * 4);
     I.cell_cid = (int*)take(N * 4);
@@ -162,7 +162,7 @@ struct Run {
     PhaseGraphs* graphs;
     cudaEvent_t* sort_ev;  // kSortEventPairs pairs, or null
     long long total_points = 0;
-    int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn); }
+    int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn, d); }
 
     // Runs the launches of phase `id`: head's directly, then body's either
     // directly or captured into the phase's executable graph and launched as
@@ -373,9 +373,17 @@ gd_status Run::go() {
     void* dsm = nullptr;
     RUN_TRY(mem.device(kMemSmall, sizeof(int) * kSmallInts * K, &dsm));
     dsmall = (int*)dsm;
+    unsigned long long* dstats = nullptr;
+    if (info && info->want_stats) {
+        void* sp = nullptr;
+        RUN_TRY(mem.device(kMemStats, sizeof(unsigned long long) * kStatCount * K, &sp));
+        dstats = (unsigned long long*)sp;
+        RUN_CUDA(cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * kStatCount * K, st), "statistics");
+    }
 
     long long total_pts = 0;
     int dmax = 1;
+    bool any_ldf = false, all_ldf = true;
     for (int k = 0; k < K; ++k) {
         const gd_instance& g = in[k];
         HI& h = hi[k];
@@ -389,6 +397,7 @@ gd_status Run::go() {
         const long long cap = (1ll << 62) - 1;
         p.eps2 = g.eps2 > cap ? cap : g.eps2;
         p.minpts = g.minpts;
+        p.ldf = knob(GD_KNOB_MERGE_ORDER, g.d, g.n);
         p.s = 1 + (long long)isqrt_u64((unsigned long long)p.eps2 / (unsigned long long)g.d);
         p.s_mul = p.s >= 2 ? ~0ull / (unsigned long long)p.s + 1 : 0;
         p.r = p.eps2 == 0 ? 0 : 1 + ((long long)isqrt_u64((unsigned long long)p.eps2) - 1) / p.s;
@@ -397,6 +406,7 @@ gd_status Run::go() {
         h.dev.labels = g.labels;
         h.dev.is_core = g.is_core;
         h.dev.small = dsmall + (size_t)k * kSmallInts;
+        h.dev.stats = dstats ? dstats + (size_t)k * kStatCount : nullptr;
         int* s = sm(k);
         memset(s, 0, sizeof(int) * kSmallInts);
         for (int j = 0; j < kMaxD; ++j) {
@@ -405,6 +415,8 @@ gd_status Run::go() {
         }
         total_pts += g.n;
         if (g.d > dmax) dmax = g.d;
+        if (p.ldf) any_ldf = true;
+        else all_ldf = false;
     }
     // scan scratch: enough for any segmented scan of the batch
     scan_tmp_ints = (size_t)K + 64;
@@ -648,15 +660,15 @@ gd_status Run::go() {
         total_nbr += hi[k].nnbr;
     }
     if (total_cells > 0) mem.note_nbr_per_grid((double)total_nbr / (double)total_cells);
-    void *nbp = nullptr, *pp = nullptr, *hp = nullptr;
+    void *nbp = nullptr, *hp = nullptr;
+    // hard pairs: each candidate pair at most once, at most one per forward
+    // list entry
     RUN_TRY(mem.device(kMemNbr, (size_t)total_nbr * 4 + 256 * (size_t)K + 256, &nbp));
-    RUN_TRY(mem.device(kMemPairs, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &pp));
     RUN_TRY(mem.device(kMemHard, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &hp));
     {
         size_t o4 = 0, o8 = 0;
         for (int k = 0; k < K; ++k) {
             hi[k].dev.nbr = (int*)((char*)nbp + o4);
-            hi[k].dev.pairs = (int2*)((char*)pp + o8);
             hi[k].dev.hard = (int2*)((char*)hp + o8);
             o4 += align256((size_t)hi[k].nnbr * 4);
             o8 += align256((size_t)hi[k].nnbr * 8);
@@ -683,11 +695,10 @@ gd_status Run::go() {
                 gn[ng++] = nmax;
             }
         }
-    Flat g_pts[kGroups], g_nf[kGroups], g_pair[2][kGroups], g_hard[2][kGroups];
+    Flat g_pts[kGroups], g_cells[kGroups], g_nf[kGroups], g_hard[2][kGroups];
     long long* g_nf_off[kGroups];
-    long long* g_pair_off[2][kGroups];
     long long* g_hard_off[2][kGroups];
-    long long g_pts_tot[kGroups];
+    long long g_pts_tot[kGroups], g_cells_tot[kGroups];
     int g_m[kGroups];
     const int* g_idx[kGroups];
     for (int gi = 0; gi < ng; ++gi) {
@@ -696,12 +707,10 @@ gd_status Run::go() {
             if (hi[k].dev.p.d == dgroups[gi] && size_bucket(in[k].n) == gbucket[gi]) members2[m++] = k;
         g_m[gi] = m;
         g_pts[gi] = flat(members2, m, n_of, &g_pts_tot[gi]);
+        g_cells[gi] = flat(members2, m, C_of, &g_cells_tot[gi]);
         g_idx[gi] = g_pts[gi].idx;
         g_nf[gi] = dflat(members2, m, &g_nf_off[gi]);
-        for (int w = 0; w < 2; ++w) {
-            g_pair[w][gi] = dflat(members2, m, &g_pair_off[w][gi]);
-            g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
-        }
+        for (int w = 0; w < 2; ++w) g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
     }
     auto arr_seg = [&](int* Inst::*field, int tot_slot) {
         long long tiles = 0;
@@ -716,8 +725,6 @@ gd_status Run::go() {
     };
     const auto nfseg = arr_seg(&Inst::nf_start, kSmNonfull);
     const auto coreseg = arr_seg(&Inst::core_start, -1);
-    const auto ptseg = arr_seg(&Inst::pair_start, kSmPairsT);
-    const auto pfseg = arr_seg(&Inst::pair_start_f, kSmPairsF);
     idx = idx_all();
     RUN_TRY(upload_desc());
 
@@ -730,31 +737,39 @@ gd_status Run::go() {
     RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
     return GD_OK;
     }, [&]() -> gd_status {
-    RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
-    RUN_TRY(scan(nfseg.first, K, nfseg.second));
-    for (int gi = 0; gi < ng; ++gi) {
-        RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
-        RUN_CUDA(launch_core_point(dins, g_nf[gi], dgroups[gi], knob(GD_KNOB_CORE_BANDS, dgroups[gi], gn[gi]), st),
-                 "core (counting)");
+    // a warp per point (the non-full points as a flat space, scanned on the
+    // device) or a warp per grid, per group
+    bool any_point_mode = false;
+    for (int gi = 0; gi < ng; ++gi)
+        if (!knob(GD_KNOB_CORE_MODE, dgroups[gi], gn[gi])) any_point_mode = true;
+    if (any_point_mode) {
+        RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
+        RUN_TRY(scan(nfseg.first, K, nfseg.second));
     }
+    for (int gi = 0; gi < ng; ++gi) {
+        const int d = dgroups[gi], bands = knob(GD_KNOB_CORE_BANDS, d, gn[gi]);
+        if (knob(GD_KNOB_CORE_MODE, d, gn[gi])) {
+            RUN_CUDA(launch_core_grid(dins, g_cells[gi], g_cells_tot[gi], d, bands, st), "core (counting)");
+        } else {
+            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
+            RUN_CUDA(launch_core_point(dins, g_nf[gi], d, bands, st), "core (counting)");
+        }
+    }
+    if (dstats) RUN_CUDA(launch_core_stats(dins, cells, total_cells, st), "core statistics");
     mark(7);
     RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
     RUN_TRY(scan(coreseg.first, K, coreseg.second));
     for (int gi = 0; gi < ng; ++gi)
         RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
     mark(8);
-    RUN_CUDA(launch_pair_count(dins, cells, total_cells, st), "pair count");
-    RUN_TRY(scan(ptseg.first, K, ptseg.second));
-    RUN_TRY(scan(pfseg.first, K, pfseg.second));
-    RUN_CUDA(launch_pair_fill(dins, cells, total_cells, st), "pair fill");
-    mark(9);
+    if (any_ldf) RUN_CUDA(launch_ldf_order(dins, idx, K, cells, total_cells, st), "low-density-first order");
     RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
+    mark(9);
     for (int w = 0; w < 2; ++w) {
+        if (w == 1 && all_ldf) break;  // one wave in the low-density-first order
         for (int gi = 0; gi < ng; ++gi) {
-            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], w == 0 ? kSmPairsT : kSmPairsF, g_pair_off[w][gi], st),
-                     "flat offsets");
             const int d = dgroups[gi];
-            RUN_CUDA(launch_merge_warp(dins, g_pair[w][gi], w, d, knob(GD_KNOB_MERGE_BUDGET, d, gn[gi]),
+            RUN_CUDA(launch_merge_list(dins, g_cells[gi], g_cells_tot[gi], w, d, knob(GD_KNOB_MERGE_BUDGET, d, gn[gi]),
                                        knob(GD_KNOB_MERGE_LANE, d, gn[gi]), knob(GD_KNOB_MERGE_SMALL, d, gn[gi]), st),
                      "merge (warp)");
         }
@@ -763,7 +778,7 @@ gd_status Run::go() {
             RUN_CUDA(launch_merge_block(dins, g_hard[w][gi], w, dgroups[gi], fm_blocks, (unsigned*)scr, wpb, st),
                      "merge (FastMerging)");
         }
-        if (w == 0) RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, st), "union-find flatten");
+        if (w == 0 && !all_ldf) RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, st), "union-find flatten");
     }
     mark(10);
     RUN_CUDA(launch_cluster_ids(dins, cells, total_cells, st), "cluster ids");
@@ -776,6 +791,19 @@ gd_status Run::go() {
     for (int k = 0; k < K; ++k)
         if ((unsigned)sm(k)[kSmStatus] & kDevTimeout)
             return fail(GD_ETIMEOUT, "a bounded device wait or retry loop hit its limit", k);
+    if (dstats) {
+        // (statistics runs are not timed: a plain synchronous copy)
+        void* hs = nullptr;
+        RUN_TRY(mem.host(kHostDesc, sizeof(unsigned long long) * kStatCount * K, &hs));
+        RUN_CUDA(cudaMemcpyAsync(hs, dstats, sizeof(unsigned long long) * kStatCount * K, cudaMemcpyDeviceToHost, st),
+                 "statistics");
+        RUN_CUDA(cudaStreamSynchronize(st), "synchronise");
+        const unsigned long long* v = (const unsigned long long*)hs;
+        for (int i = 0; i < kStatCount; ++i) info->stats[i] = 0;
+        for (int k = 0; k < K; ++k)
+            for (int i = 0; i < kStatCount; ++i) info->stats[i] += v[(size_t)k * kStatCount + i];
+        info->have_stats = true;
+    }
 
     if (info) {
         const HI& h = hi[0];
@@ -789,7 +817,7 @@ gd_status Run::go() {
         info->sizes[4] = h.dev.p.s;
         info->sizes[5] = h.dev.p.key_bits;
         info->sizes[6] = 0;  // filled by the caller (launch count)
-        info->sizes[7] = (long long)s0[kSmPairsT] + s0[kSmPairsF];
+        info->sizes[7] = (long long)s0[kSmPairsT];
         info->sizes[8] = h.dev.passes;
         info->sizes[9] = h.dev.digit_bits;
         info->sizes[10] = (long long)s0[kSmHard0] + s0[kSmHard1];
@@ -814,7 +842,7 @@ gd_status Run::go() {
 
 }  // namespace
 
-int knob_default(int knob) {
+int knob_default(int knob, int d) {
     switch (knob) {
         case GD_KNOB_MERGE_BUDGET: return 2;
         case GD_KNOB_MERGE_LANE: return 16;
@@ -822,7 +850,9 @@ int knob_default(int knob) {
         case GD_KNOB_CORE_BANDS: return 128;
         case GD_KNOB_FM_BLOCKS: return 152 * 8;
         case GD_KNOB_WALK_BLOCKS: return 152 * 32;
-        default: return 0;
+        case GD_KNOB_MERGE_ORDER: return 1;
+        case GD_KNOB_CORE_MODE: return d <= 4 ? 1 : 0;
+        default: return -1;
     }
 }
 
@@ -834,6 +864,8 @@ bool knob_in_range(int knob, int v) {
         case GD_KNOB_CORE_BANDS: return v >= 0 && v <= 65536;
         case GD_KNOB_FM_BLOCKS:
         case GD_KNOB_WALK_BLOCKS: return v >= 152 && v <= 152 * 128;
+        case GD_KNOB_MERGE_ORDER: return v == 0 || v == 1;
+        case GD_KNOB_CORE_MODE: return v == 0 || v == 1;
         default: return false;
     }
 }
@@ -841,7 +873,7 @@ bool knob_in_range(int knob, int v) {
 int Tuning::value(int knob, int d, long long n) const {
     for (int i = 0; i < count; ++i)
         if (e[i].knob == knob && (e[i].d == 0 || e[i].d == d) && n <= e[i].n_max) return e[i].value;
-    return knob_default(knob);
+    return knob_default(knob, d);
 }
 
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,

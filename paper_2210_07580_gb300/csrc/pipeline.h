@@ -13,8 +13,8 @@ namespace gd {
 // Where the driver's memory comes from: a context's growable buffers, or a
 // fixed static array (the no-allocation entry point).
 enum MemSlot {
-    kMemSmall, kMemDesc, kMemArena, kMemScanTmp, kMemNbr, kMemPairs, kMemHard, kMemScratch, kMemPool, kMemPoolSeg,
-    kMemSlots
+    kMemSmall, kMemDesc, kMemArena, kMemScanTmp, kMemNbr, kMemHard, kMemScratch, kMemPool, kMemPoolSeg,
+    kMemStats, kMemSlots
 };
 enum HostSlot { kHostSmall, kHostDesc, kHostSlots };
 
@@ -52,6 +52,10 @@ struct RunInfo {
     size_t view_bytes[7];
     long long launches;
     int sort_event_pairs = 0;
+    // statistics of the run (summed over its instances) when asked for
+    bool want_stats = false;
+    bool have_stats = false;
+    unsigned long long stats[kStatCount] = {};
     std::string error;
 };
 
@@ -64,7 +68,8 @@ struct Tuning {
     // has n points: the first matching entry, else the default.
     int value(int knob, int d, long long n) const;
 };
-int knob_default(int knob);
+// A knob's built-in value for instances of dimension d.
+int knob_default(int knob, int d);
 bool knob_in_range(int knob, int value);
 
 // Executable graphs of the driver's launch phases (the work between two reads

@@ -9,10 +9,11 @@ from paper_2210_07580_gb300 import Context, GdError, synth  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 LOW = [("merge_budget", 0, 1 << 62, 1), ("merge_lane", 0, 1 << 62, 1), ("merge_small", 0, 1 << 62, 32),
-       ("core_bands", 0, 1 << 62, 0), ("fm_blocks", 0, 1 << 62, 152), ("walk_blocks", 0, 1 << 62, 152)]
+       ("core_bands", 0, 1 << 62, 0), ("fm_blocks", 0, 1 << 62, 152), ("walk_blocks", 0, 1 << 62, 152),
+       ("merge_order", 0, 1 << 62, 0), ("core_mode", 0, 1 << 62, 0)]
 HIGH = [("merge_budget", 0, 1 << 62, 64), ("merge_lane", 0, 1 << 62, 256), ("merge_small", 0, 1 << 62, 1024),
         ("core_bands", 0, 1 << 62, 65536), ("fm_blocks", 0, 1 << 62, 152 * 128),
-        ("walk_blocks", 0, 1 << 62, 152 * 128)]
+        ("walk_blocks", 0, 1 << 62, 152 * 128), ("core_mode", 0, 1 << 62, 1)]
 
 
 def test_knob_extremes_give_identical_labels():

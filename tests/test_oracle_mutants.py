@@ -37,8 +37,14 @@ MUTANTS = [
     ("border_takes_largest_id", "if (best < 0 || c < best) best = c;", "if (best < 0 || c > best) best = c;"),
     ("triangle_missing_factor4", "(unsigned __int128)4 * (u64)A * (u64)eps2;",
      "(unsigned __int128)1 * (u64)A * (u64)eps2;"),
-    ("fastmerging_prunes_sj_around_p", "cb = prune_set(B, ib, cb, q, dpq, d, eps2);",
-     "cb = prune_set(B, ib, cb, p, dpq, d, eps2);"),
+    ("fastmerging_prunes_sj_around_p",
+     "cb = prune_set(B, ib, cb, q, p, dpq, angle_lambda(A, ia, ca, q, p, d, eps2), d, eps2);",
+     "cb = prune_set(B, ib, cb, p, q, dpq, angle_lambda(A, ia, ca, q, p, d, eps2), d, eps2);"),
+    ("angle_lambda_drops_arcsin",
+     "const double ly = asin(clamp1(eps / b)) + acos(",
+     "const double ly = 0.0 * asin(clamp1(eps / b)) + acos("),
+    ("angle_test_without_margin_sign", "if (lambda + ANGLE_MARGIN < theta)",
+     "if (lambda - 0.5 < theta)"),
     ("merge_skips_union", "if (yes) uf_union(parent, ci, cj);", "if (yes && ci < 0) uf_union(parent, ci, cj);"),
     ("border_strict_boundary", "if (sqdist(g.Xs + k * d, S + w * d, d) <= eps2) {",
      "if (sqdist(g.Xs + k * d, S + w * d, d) < eps2) {"),

@@ -31,7 +31,8 @@ def test_ordered_puts_small_buckets_and_specific_dims_first():
 
 def test_every_knob_has_candidates_defaults_and_a_number(tmp_path):
     for name, (cands, stages) in {**autotune.PER_GROUP, **autotune.PER_BATCH}.items():
-        assert name in KNOBS and autotune.DEFAULTS[name] in cands and stages
+        assert name in KNOBS and stages
+        assert all(autotune.default_value(name, d) in cands for d in range(1, 9))
     doc = {"entries": [{"knob": "merge_lane", "d": 7, "n_max": 4096, "value": 4}]}
     p = tmp_path / "t.json"
     p.write_text(json.dumps(doc))
