@@ -66,9 +66,10 @@ def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float, stat
     """Achieved bandwidth of the grid-build stages and (with run statistics)
     of the count stage: algorithmic bytes (each array the stage must read or
     write, once) over the stage's device time.  The count stage must write
-    every core flag (1 B/point) and read each non-full point's row and, once
-    per non-full grid, the rows of its neighbour grids (the statistic
-    count_rows)."""
+    every core flag (1 B/point) and read, at least once, each non-full
+    point's row and the rows of those points' neighbour grids (the statistic
+    count_rows counts them once per non-full grid; no row is read from DRAM
+    more than once at minimum, so the rows are capped at n)."""
     dp = 1 if d == 1 else 2 if d == 2 else 4 if d <= 4 else 8
     kc = sizes["key_class"]
     key_b = 16 if kc == 2 else 8
@@ -82,7 +83,7 @@ def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float, stat
         "compact": (2 * key_b + val_b + 4 + 4 + 4 * d + 4 * dp) * n,
     }
     if stats:
-        bytes_["core"] = n + (stats["nonfull_points"] + stats["count_rows"]) * 4 * dp
+        bytes_["core"] = n + min(n, stats["nonfull_points"] + stats["count_rows"]) * 4 * dp
     out = {}
     for st, b in bytes_.items():
         ms = stages.get(st, 0.0)

@@ -62,8 +62,12 @@ typedef enum {
 } gd_status;
 
 /* Create a context on CUDA device `device` (made current by the call).
- * *out receives the context, or NULL on failure. */
-gd_status gd_create(gd_ctx **out, int device);
+ * *out receives the context, or NULL on failure.  arena_bytes caps the device
+ * memory the context may hold (its workspace and, for gd_dbscan_host, the
+ * device copies); 0 means no cap.  A call that would need more returns
+ * GD_ENOMEM and leaves the context usable with the buffers it held.  (The
+ * paper has no counterpart: this is memory management of the GPU library.) */
+gd_status gd_create(gd_ctx **out, int device, size_t arena_bytes);
 
 /* Free the context and everything it owns.  NULL is ignored. */
 void gd_destroy(gd_ctx *ctx);
@@ -246,6 +250,22 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
  * (part of the "sort" stage). */
 gd_status gd_set_timing(gd_ctx *ctx, int enable);
 int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
+
+/* Failure paths, for tests (no counterpart in the paper).
+ *
+ * gd_set_retry_limit: the number of iterations each lock-free union-find
+ * loop of the merge (finds and CAS links) may take before it gives up and
+ * the call returns GD_ETIMEOUT; 0 restores the built-in limit (2^20, far
+ * above any legitimate count).  A tiny limit makes the bounded loops run out
+ * on purpose; the device stays usable and the next call with the built-in
+ * limit is exact again.
+ *
+ * gd_inject_alloc_failure: the k-th request for a device buffer that the
+ * context makes from now on (counting every request, whether or not it needs
+ * a new allocation) fails as a refused cudaMalloc would, with GD_ENOMEM; the
+ * injection is then spent.  0 cancels it.  GD_EINVAL for k < 0. */
+gd_status gd_set_retry_limit(gd_ctx *ctx, int32_t limit);
+gd_status gd_inject_alloc_failure(gd_ctx *ctx, int32_t k);
 
 /* Run statistics (no counterpart in the paper; the quantities are the ones
  * Section 4.3.3 and Section 5.2 discuss).  Off by default; when on, each call

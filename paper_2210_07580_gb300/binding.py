@@ -61,7 +61,7 @@ def load_library(path: str | None = None):
                                "(python -c 'import __graft_entry__ as g; g.build()')")
         lib = ctypes.CDLL(p)
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
-        lib.gd_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        lib.gd_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t]
         lib.gd_create.restype = ctypes.c_int
         lib.gd_destroy.argtypes = [vp]
         lib.gd_destroy.restype = None
@@ -84,6 +84,10 @@ def load_library(path: str | None = None):
         lib.gd_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.c_int]
         lib.gd_stage_times.restype = ctypes.c_int
+        lib.gd_set_retry_limit.argtypes = [vp, i32]
+        lib.gd_set_retry_limit.restype = ctypes.c_int
+        lib.gd_inject_alloc_failure.argtypes = [vp, i32]
+        lib.gd_inject_alloc_failure.restype = ctypes.c_int
         lib.gd_set_stats.argtypes = [vp, ctypes.c_int]
         lib.gd_set_stats.restype = ctypes.c_int
         lib.gd_run_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]
@@ -140,15 +144,16 @@ def _stream_handle(stream) -> int:
 class Context:
     """One gd_ctx: a device workspace reused across calls.  Not thread-safe."""
 
-    def __init__(self, device: int = 0, tuning="default", graphs: bool = True):
+    def __init__(self, device: int = 0, tuning="default", graphs: bool = True, arena_bytes: int = 0):
         """tuning: "default" loads the table shipped with the package (if
         present), None keeps the built-in defaults, or a list of entries as
         for set_tuning.  graphs: launch each phase of a call as a CUDA graph
-        kept by the context (gd_set_graphs)."""
+        kept by the context (gd_set_graphs).  arena_bytes: cap on the device
+        memory the context may hold (0: none)."""
         self._lib = load_library()
         self.device = int(device)
         h = ctypes.c_void_p()
-        st = self._lib.gd_create(ctypes.byref(h), self.device)
+        st = self._lib.gd_create(ctypes.byref(h), self.device, int(arena_bytes))
         if st != GD_OK:
             raise GdError(st, self._lib.gd_status_str(st).decode())
         self._h = h
@@ -289,6 +294,15 @@ class Context:
 
     def set_timing(self, enable: bool):
         self._check(self._lib.gd_set_timing(self._h, 1 if enable else 0))
+
+    def set_retry_limit(self, limit: int):
+        """Cap the union-find loops' iterations (0: the built-in limit); a
+        call whose loops run out raises GdError with GD_ETIMEOUT."""
+        self._check(self._lib.gd_set_retry_limit(self._h, int(limit)))
+
+    def inject_alloc_failure(self, k: int):
+        """Make the k-th device buffer request from now fail (0: cancel)."""
+        self._check(self._lib.gd_inject_alloc_failure(self._h, int(k)))
 
     def set_stats(self, enable: bool):
         """Keep run statistics (merge outcomes, FastMerging rounds, count

@@ -26,13 +26,24 @@ struct HostBuf {
 };
 
 // The context's memory: device buffers grown on demand with cudaMalloc (to
-// 1/8 more than asked, kept for reuse), pinned host staging likewise.
+// 1/8 more than asked, kept for reuse), pinned host staging likewise.  With
+// a cap, a buffer that would take the device bytes held past it is refused
+// (GD_ENOMEM) and the buffers held stay as they are.
 struct CtxMem : MemProvider {
     DevBuf dev[kMemSlots];
     HostBuf host_[kHostSlots];
     cudaStream_t st = nullptr;
     std::string* err = nullptr;
     double nbr_ratio = 0.0;  // most neighbour entries per grid seen
+    size_t cap_bytes = 0;    // 0: no cap
+    const size_t* extra_held = nullptr;  // other device bytes the context holds (I/O copies)
+    int fail_at = 0;         // > 0: the fail_at-th device request from now fails (tests)
+
+    size_t held() const {
+        size_t b = extra_held ? *extra_held : 0;
+        for (const DevBuf& d : dev) b += d.cap;
+        return b;
+    }
 
     bool pool_enabled() override { return true; }
     double nbr_per_grid() override { return nbr_ratio; }
@@ -42,7 +53,16 @@ struct CtxMem : MemProvider {
 
     gd_status device(int slot, size_t bytes, void** out) override {
         DevBuf& b = dev[slot];
+        if (fail_at > 0 && --fail_at == 0) {
+            if (err) *err = "device buffer request refused (injected failure)";
+            return GD_ENOMEM;
+        }
         if (b.cap < bytes) {
+            const size_t want0 = bytes + bytes / 8 + (1 << 16);
+            if (cap_bytes && held() - b.cap + want0 > cap_bytes) {
+                if (err) *err = "device buffer of " + std::to_string(want0) + " bytes exceeds the context's cap";
+                return GD_ENOMEM;
+            }
             if (b.ptr) {
                 if (cudaStreamSynchronize(st) != cudaSuccess) return GD_ECUDA;
                 cudaFree(b.ptr);
@@ -99,6 +119,7 @@ struct gd_ctx {
     int device = 0;
     CtxMem mem;
     DevBuf io;  // device copies for gd_dbscan_host
+    int uf_cap = 0;  // union-find retry cap (0: built-in)
     cudaEvent_t ev[kStageEvents] = {};
     bool timing = false;
     bool stats = false;
@@ -149,6 +170,7 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
     ctx->mem.err = &ctx->err;
     ctx->info = RunInfo();
     ctx->info.want_stats = ctx->stats;
+    ctx->info.uf_cap = ctx->uf_cap;
     const long long l0 = t_launches;
     gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning,
                             &ctx->graphs, ctx->timing ? ctx->sev : nullptr);
@@ -180,12 +202,14 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
 
 extern "C" {
 
-gd_status gd_create(gd_ctx** out, int device) {
+gd_status gd_create(gd_ctx** out, int device, size_t arena_bytes) {
     if (!out) return GD_EINVAL;
     *out = nullptr;
     gd_ctx* ctx = new (std::nothrow) gd_ctx();
     if (!ctx) return GD_ENOMEM;
     ctx->device = device;
+    ctx->mem.cap_bytes = arena_bytes;
+    ctx->mem.extra_held = &ctx->io.cap;
     cudaError_t e = cudaSetDevice(device);
     for (int i = 0; e == cudaSuccess && i < kStageEvents; ++i) e = cudaEventCreate(&ctx->ev[i]);
     for (int i = 0; e == cudaSuccess && i < 2 * kSortEventPairs; ++i) e = cudaEventCreate(&ctx->sev[i]);
@@ -259,6 +283,8 @@ gd_status gd_dbscan_host(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, i
     const size_t xb = (size_t)n * d * 4, lb = (size_t)n * 4, cb = (size_t)n;
     const size_t lo = (xb + 255) & ~(size_t)255, co = (lo + lb + 255) & ~(size_t)255;
     if (ctx->io.cap < co + cb) {
+        if (ctx->mem.cap_bytes && ctx->mem.held() - ctx->io.cap + co + cb > ctx->mem.cap_bytes)
+            return ctx->err = "input/output copies exceed the context's cap", GD_ENOMEM;
         if (ctx->io.ptr) {
             cudaStreamSynchronize(st);
             cudaFree(ctx->io.ptr);
@@ -373,6 +399,18 @@ gd_status gd_set_timing(gd_ctx* ctx, int enable) {
     if (!ctx) return GD_EINVAL;
     ctx->timing = enable != 0;
     ctx->nstages = 0;
+    return GD_OK;
+}
+
+gd_status gd_set_retry_limit(gd_ctx* ctx, int32_t limit) {
+    if (!ctx || limit < 0) return GD_EINVAL;
+    ctx->uf_cap = limit;
+    return GD_OK;
+}
+
+gd_status gd_inject_alloc_failure(gd_ctx* ctx, int32_t k) {
+    if (!ctx || k < 0) return GD_EINVAL;
+    ctx->mem.fail_at = k;
     return GD_OK;
 }
 

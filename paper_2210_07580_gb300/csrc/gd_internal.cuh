@@ -35,7 +35,8 @@ enum : unsigned { kDevTimeout = 1u, kDevOverflow = 2u };
 
 // Retry cap for the lock-free union-find loops: far above any legitimate
 // number of CAS retries, so reaching it means something is wrong; the kernel
-// then records kDevTimeout and gives up instead of spinning.
+// then records kDevTimeout and gives up instead of spinning.  A context can
+// lower it (gd_set_retry_limit, for tests of that path): Params::uf_cap.
 constexpr int kMaxUfRetries = 1 << 20;
 
 // Per-instance parameters, fixed once the bounds are known.
@@ -60,6 +61,7 @@ struct Params {
     int key_class;
     int pack_bits;
     int ldf;          // merge order: 0 = touching pairs first, 1 = low density first (Section 5.2)
+    int uf_cap;       // iterations a union-find loop may take before it gives up
     int mn[kMaxD];    // per-dimension minimum coordinate
     int bits[kMaxD];  // bits of each identifier in the key
     int shift[kMaxD]; // bit offset of identifier j (dimension 0 most significant)
@@ -269,8 +271,8 @@ __device__ __forceinline__ unsigned uf_priority(int x) {
 // Union-find root with path halving; -1 if the retry cap is reached.  Parents
 // are read through L2 (other SMs link roots concurrently) and every halving
 // store writes an ancestor, so concurrent finds and unions stay consistent.
-__device__ __forceinline__ int uf_find(int* parent, int x) {
-    for (int it = 0; it < kMaxUfRetries; ++it) {
+__device__ __forceinline__ int uf_find(int* parent, int x, int cap) {
+    for (int it = 0; it < cap; ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) return x;
         const int gp = __ldcg(parent + px);
@@ -283,8 +285,8 @@ __device__ __forceinline__ int uf_find(int* parent, int x) {
 // The root of x without writing anything.  Used where every grid's pointer
 // must end at its root: a halving store by one thread can put back an older
 // ancestor over the root another thread has just written.
-__device__ __forceinline__ int uf_find_ro(const int* parent, int x) {
-    for (int it = 0; it < kMaxUfRetries; ++it) {
+__device__ __forceinline__ int uf_find_ro(const int* parent, int x, int cap) {
+    for (int it = 0; it < cap; ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) return x;
         x = px;

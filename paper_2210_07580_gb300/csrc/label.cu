@@ -32,7 +32,7 @@ __global__ void uf_compress_kernel(const Inst* __restrict__ ins, Flat f, long lo
         I.cid_root[c] = INT_MAX;
         if (I.core_start[c + 1] > I.core_start[c]) {
             // read-only: concurrent halving could undo this grid's pointer
-            const int r = uf_find_ro(I.parent, c);
+            const int r = uf_find_ro(I.parent, c, I.p.uf_cap);
             if (r < 0)
                 set_status(I, kDevTimeout);
             else

@@ -295,7 +295,7 @@ __global__ void uf_flatten_kernel(const Inst* __restrict__ ins, Flat f, long lon
         const int k = cur.k;
         const Inst& I = ins[f.idx[k]];
         const int c = (int)(i - cur.lo);
-        const int r = uf_find(I.parent, c);
+        const int r = uf_find(I.parent, c, I.p.uf_cap);
         if (r < 0)
             set_status(I, kDevTimeout);
         else if (r != c)
@@ -311,10 +311,10 @@ cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cuda
 }
 
 // Returns false if the retry cap was hit.
-__device__ __forceinline__ bool uf_union(int* parent, int a, int b) {
-    for (int it = 0; it < kMaxUfRetries; ++it) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
+__device__ __forceinline__ bool uf_union(int* parent, int a, int b, int cap) {
+    for (int it = 0; it < cap; ++it) {
+        a = uf_find(parent, a, cap);
+        b = uf_find(parent, b, cap);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         if (uf_priority(a) < uf_priority(b)) {
@@ -396,6 +396,7 @@ __global__ void __launch_bounds__(256)
         const int d = I.p.d;
         const long long eps2 = I.p.eps2;
         int* parent = I.parent;
+        const int cap = I.p.uf_cap;
         unsigned long long* const stv = I.stats;
         const int gl = lane < d ? I.cell_coord[(long long)c * d + lane] : 0;
         const int t_begin = I.nbr_start[c];
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(256)
             int outcome = -1;    // statistics: the slot that decided the lane's pair
             unsigned ndist = 0;  // statistics: distances this lane evaluated
             if (keep) {
-                const int ra = uf_find(parent, c), rb = uf_find(parent, j2);
+                const int ra = uf_find(parent, c, cap), rb = uf_find(parent, j2, cap);
                 if (ra < 0 || rb < 0) {
                     set_status(I, kDevTimeout);
                 } else if (ra == rb) {
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(256)
                             outcome = -1;
                         }
                     }
-                    if (yes && !uf_union(parent, c, j2)) set_status(I, kDevTimeout);
+                    if (yes && !uf_union(parent, c, j2, cap)) set_status(I, kDevTimeout);
                 }
             }
             acc_pairs += __popc(__ballot_sync(kFull, keep));
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(256)
                 const int py = __shfl_sync(kFull, j2, src);
                 int same = 0;
                 if (lane == 0) {
-                    const int ra = uf_find(parent, c), rb = uf_find(parent, py);
+                    const int ra = uf_find(parent, c, cap), rb = uf_find(parent, py, cap);
                     if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
                     same = ra == rb;
                 }
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(256)
                     stat_add(stv, handed ? kStHanded : kStWarp, 1);
                     stat_add(stv, kStDistMerge, tile_dist);
                     if (yes) {
-                        if (!uf_union(parent, c, py)) set_status(I, kDevTimeout);
+                        if (!uf_union(parent, c, py, cap)) set_status(I, kDevTimeout);
                     } else if (handed) {
                         I.hard[hard_base + atomicAdd(I.small + kSmHard0 + wave, 1)] = make_int2(c, py);
                     }
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
         int* parent = I.parent;
         unsigned long long* const stv = I.stats;
         if (threadIdx.x == 0) {
-            const int ra = uf_find(parent, pr.x), rb = uf_find(parent, pr.y);
+            const int ra = uf_find(parent, pr.x, I.p.uf_cap), rb = uf_find(parent, pr.y, I.p.uf_cap);
             if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
             s_same = ra == rb;
             s_tri = 0;
@@ -874,7 +875,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
             ++kappa;
         }
         if (threadIdx.x == 0) {
-            if (yes && !uf_union(parent, pr.x, pr.y)) set_status(I, kDevTimeout);
+            if (yes && !uf_union(parent, pr.x, pr.y, I.p.uf_cap)) set_status(I, kDevTimeout);
             if (stv) {
                 stat_add(stv, yes ? kStFmYes : kStFmNo, 1);
                 stat_add(stv, kStKappa + min(kappa, (int)kKappaBins) - 1, 1);

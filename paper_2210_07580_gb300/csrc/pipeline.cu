@@ -398,6 +398,7 @@ gd_status Run::go() {
         p.eps2 = g.eps2 > cap ? cap : g.eps2;
         p.minpts = g.minpts;
         p.ldf = knob(GD_KNOB_MERGE_ORDER, g.d, g.n);
+        p.uf_cap = info && info->uf_cap > 0 ? info->uf_cap : kMaxUfRetries;
         p.s = 1 + (long long)isqrt_u64((unsigned long long)p.eps2 / (unsigned long long)g.d);
         p.s_mul = p.s >= 2 ? ~0ull / (unsigned long long)p.s + 1 : 0;
         p.r = p.eps2 == 0 ? 0 : 1 + ((long long)isqrt_u64((unsigned long long)p.eps2) - 1) / p.s;

@@ -52,6 +52,8 @@ struct RunInfo {
     size_t view_bytes[7];
     long long launches;
     int sort_event_pairs = 0;
+    // union-find retry cap for the run (0: the built-in kMaxUfRetries)
+    int uf_cap = 0;
     // statistics of the run (summed over its instances) when asked for
     bool want_stats = false;
     bool have_stats = false;

@@ -48,3 +48,44 @@ def test_noalloc_rejects_inputs_beyond_its_limit():
     with pytest.raises(GdError) as e:
         binding.dbscan_noalloc(X, 100, 3)
     assert e.value.status == binding.GD_ENOMEM
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a warm-up call (which may load the library's module and back the
+    static array), further calls leave the device's free memory unchanged."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    X, eps2, minpts = synth.workload("tiny", n=20000, seed=13)
+    Xd = torch.from_numpy(X).cuda()
+    lab = torch.empty(len(X), dtype=torch.int32, device="cuda")
+    core = torch.empty(len(X), dtype=torch.uint8, device="cuda")
+    binding.dbscan_noalloc(Xd, eps2, minpts, labels=lab, is_core=core)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        binding.dbscan_noalloc(Xd, eps2, minpts, labels=lab, is_core=core)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_lists_beyond_the_array_give_enomem_then_recover():
+    """Data whose neighbour lists need more than the static array has left
+    (65,536 points in 8 dimensions with a large eps: hundreds of neighbour
+    grids per grid) are refused with GD_ENOMEM; the next call still matches
+    gd_dbscan."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(14)
+    X = rng.integers(0, 100000, size=(binding.NOALLOC_MAX_POINTS, 8)).astype(np.int32)
+    with pytest.raises(GdError) as e:
+        binding.dbscan_noalloc(torch.from_numpy(X).cuda(), 50000 ** 2, 5)
+    assert e.value.status == binding.GD_ENOMEM
+    X1, e1, m1 = synth.workload("tiny", n=20000, seed=15)
+    Xd = torch.from_numpy(X1).cuda()
+    ctx = Context(0)
+    want_l, want_c = ctx.dbscan(Xd, e1, m1)
+    got_l, got_c = binding.dbscan_noalloc(Xd, e1, m1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got_l.cpu().numpy(), want_l.cpu().numpy())
+    np.testing.assert_array_equal(got_c.cpu().numpy().astype(bool), want_c.cpu().numpy())
+    ctx.close()
