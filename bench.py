@@ -291,11 +291,13 @@ def measure_workload(ctx, dev, workload: str, steps: int, warmup: int, flush, st
     core = torch.empty(n, dtype=torch.uint8, device=dev)
 
     def step():
-        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream)
+        # queued asynchronously; finished (status checked) after the events
+        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream, sync=False)
 
     for _ in range(warmup):
         flush.fill_(1)
         step()
+        ctx.sync(stream)
     torch.cuda.synchronize()
     ctx.set_timing(True)
     acc, times = {}, []
@@ -305,6 +307,7 @@ def measure_workload(ctx, dev, workload: str, steps: int, warmup: int, flush, st
         a.record(stream)
         step()
         b.record(stream)
+        ctx.sync(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
         for name, ms in ctx.stage_times().items():
@@ -313,6 +316,7 @@ def measure_workload(ctx, dev, workload: str, steps: int, warmup: int, flush, st
     sizes = ctx.last_sizes()
     ctx.set_stats(True)
     step()
+    ctx.sync(stream)
     torch.cuda.synchronize()
     stats = ctx.run_stats()
     ctx.set_stats(False)
@@ -390,7 +394,8 @@ def bench_batched(ctx, dev, args):
 
     def looped():
         for (Xd, e, m), (lab, core) in zip(djobs, outs_l):
-            ctx.dbscan(Xd, e, m, labels=lab, is_core=core, stream=stream)
+            ctx.dbscan(Xd, e, m, labels=lab, is_core=core, stream=stream, sync=False)
+        ctx.sync(stream)
 
     res = {}
     for name, fn in (("batched", batched), ("looped", looped)):
@@ -494,11 +499,14 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream)
+        # queued asynchronously (gd_dbscan); its status is read after the
+        # step's end event (gd_sync), outside the timed span
+        ctx.dbscan(Xd, eps2, minpts, labels=labels, is_core=core, stream=stream, sync=False)
 
     for _ in range(args.warmup):
         flush.fill_(1)
         step()
+        ctx.sync(stream)
     torch.cuda.synchronize()
     ctx.set_timing(True)
     sampler = ClockSampler(local)
@@ -516,6 +524,7 @@ def run_gpu(args):
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
+        ctx.sync(stream)
         for name, ms in ctx.stage_times().items():
             stage_acc[name] = stage_acc.get(name, 0.0) + ms
         launches += ctx.last_sizes()["launches"]

@@ -74,22 +74,44 @@ void gd_destroy(gd_ctx *ctx);
 
 /* Upper bound, in bytes, of the device workspace gd_dbscan needs for n points
  * in d dimensions before neighbour lists (which depend on the data: the
- * context grows them on demand).  Used for admission control. */
+ * context grows them on demand).  Used for admission control.  (No
+ * counterpart in the paper: memory sizing of the GPU library.) */
 size_t gd_workspace_bytes(int64_t n, int d);
 
-/* Exact DBSCAN of the device-resident points X (Section 4.4, Alg. 6).
- * X, labels and is_core are device pointers (is_core may be NULL); labels and
- * is_core must not overlap each other or X (labels also serves as scratch
- * during the call; its contents are final when the call returns).  Work is
- * issued on `stream`; the call returns after the result is complete on that
- * stream (it synchronises with it to size data-dependent buffers).  n == 0 is
- * a no-op returning GD_OK. */
+/* Exact DBSCAN of the device-resident points X (Section 4.4, Alg. 6: input
+ * P, eps, MinPts; output the clustering).  X, labels and is_core are device
+ * pointers (is_core may be NULL); labels and is_core must not overlap each
+ * other or X (labels also serves as scratch during the call).
+ *
+ * Asynchronous: the work is queued on `stream` and the call returns; the
+ * status of the clustering is deferred to gd_sync, and labels / is_core are
+ * final once gd_sync has returned GD_OK (work queued on `stream` after
+ * gd_sync sees them; X must stay unchanged until then).  When the context
+ * has clustered an instance of the same n, d and eps2 before, the call reads
+ * nothing back from the device while queueing; otherwise it waits twice for
+ * sizes the data decides (the coordinate bounds, the neighbour-list sizes).
+ * A context finishes its previous call before queueing a new one (a failure
+ * of that call is reported by the next gd_sync).  The return value reports
+ * errors found while queueing (bad arguments, GD_ENOMEM, GD_ECUDA, and
+ * GD_ERANGE when the bounds were read back).  n == 0 is a no-op returning
+ * GD_OK. */
 gd_status gd_dbscan(gd_ctx *ctx, const int32_t *X, int64_t n, int d, int64_t eps2,
                     int32_t minpts, int32_t *labels, uint8_t *is_core, gd_stream_t stream);
 
+/* Finishes the context's queued call, if any, and returns its deferred
+ * status: GD_OK, GD_ETIMEOUT (a bounded union-find loop ran out), GD_ERANGE
+ * (d * R^2 >= 2^62, found on the device), GD_ECUDA, or the failure of an
+ * earlier call finished implicitly by a later one.  If sizes reused from an
+ * earlier call did not fit the data, the call is run again with exact sizes
+ * before gd_sync returns (the result is the same).  Blocks the host until
+ * the call's work on its stream is done.  (The paper has no counterpart:
+ * this is the boundary of the GPU library.) */
+gd_status gd_sync(gd_ctx *ctx, gd_stream_t stream);
+
 /* As gd_dbscan, with X, labels and is_core in HOST memory (pinned memory
  * makes the copies asynchronous and fast).  The call copies X to the device,
- * clusters, and copies the results back before returning. */
+ * clusters, finishes (as gd_sync) and copies the results back before
+ * returning: it is synchronous. */
 gd_status gd_dbscan_host(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, int64_t eps2,
                          int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
                          gd_stream_t stream);
@@ -106,16 +128,20 @@ typedef struct {
 } gd_instance;
 
 /* Exact DBSCAN of k independent instances (uneven sizes, dimensions and
- * parameters) in one batch: every stage of the pipeline is one launch per
- * group of instances (grouped by dimension or key width) covering all of
- * them, and the host synchronises with `stream` a fixed handful of times per
- * batch instead of per instance.  Each instance's result equals gd_dbscan's
- * on it alone.  `inst` is a host array of k records; k == 0 is a no-op.  On
- * error the outputs of every instance are unspecified and gd_last_error
- * names the failing instance. */
+ * parameters) in one batch (no counterpart in the paper, which clusters one
+ * data set: Alg. 6 applied to each instance).  Every stage of the pipeline is
+ * one launch per group of instances (grouped by dimension or key width)
+ * covering all of them.  Asynchronous like gd_dbscan (gd_sync finishes it;
+ * nothing is read back while queueing when the context has seen every
+ * instance's shape, else the host waits twice per batch, whatever k is).
+ * Each instance's result equals gd_dbscan's on it alone.  `inst` is a host
+ * array of k records (copied by the call); k == 0 is a no-op.  On error the
+ * outputs of every instance are unspecified and gd_last_error names the
+ * failing instance. */
 gd_status gd_dbscan_batched(gd_ctx *ctx, int k, const gd_instance *inst, gd_stream_t stream);
 
-/* Device bytes the context currently holds (workspace kept for reuse). */
+/* Device bytes the context currently holds (workspace kept for reuse; no
+ * counterpart in the paper, like the rest of the context management). */
 size_t gd_ctx_bytes(const gd_ctx *ctx);
 
 /* Release the context's cached device and pinned host buffers (they are
@@ -129,8 +155,9 @@ const char *gd_status_str(gd_status s);
 const char *gd_last_error(const gd_ctx *ctx);
 
 /* ---------------------------------------------------------------------
- * Introspection of the last gd_dbscan call on a context (tests, tuning).
- * The arrays stay valid until the next call on the context.
+ * Introspection of the last gd_dbscan call on a context (tests, tuning; no
+ * counterpart in the paper).  These finish a queued call first.  The
+ * arrays stay valid until the next call on the context.
  * ------------------------------------------------------------------- */
 
 typedef enum {
@@ -231,9 +258,11 @@ gd_status gd_graph_stats(const gd_ctx *ctx, int64_t out[3]);
  * out[6]=kernel launches of the run, out[7]=candidate merge pairs,
  * out[8]=radix-sort passes, out[9]=bits per digit, out[10]=pairs decided by
  * FastMerging, out[11]=sort key class (0: key and point index packed in one
- * 64-bit word, 1: 64-bit key + 32-bit index, 2: 128-bit key + 32-bit index).
- * Returns GD_EINVAL before any run. */
-gd_status gd_last_sizes(const gd_ctx *ctx, int64_t out[12]);
+ * 64-bit word, 1: 64-bit key + 32-bit index, 2: 128-bit key + 32-bit index),
+ * out[12]=1 if the call was queued without reading anything back (the
+ * context had planned every instance's shape), else 0; a call run again with
+ * exact sizes reports 0.  Returns GD_EINVAL before any run. */
+gd_status gd_last_sizes(gd_ctx *ctx, int64_t out[13]);
 
 /* Copy `bytes` bytes of an internal array of the last run into host memory
  * (synchronous).  GD_EINVAL if bytes exceeds the array's size. */
@@ -249,7 +278,7 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
  * "sort_downsweep", the summed time of the radix sort's downsweep kernels
  * (part of the "sort" stage). */
 gd_status gd_set_timing(gd_ctx *ctx, int enable);
-int gd_stage_times(const gd_ctx *ctx, float *ms, const char **names, int max);
+int gd_stage_times(gd_ctx *ctx, float *ms, const char **names, int max);
 
 /* Failure paths, for tests (no counterpart in the paper).
  *
@@ -294,7 +323,7 @@ gd_status gd_inject_alloc_failure(gd_ctx *ctx, int32_t k);
  *                        Section 4.3.3)
  * Counting costs atomics: do not time calls that keep statistics. */
 gd_status gd_set_stats(gd_ctx *ctx, int enable);
-int gd_run_stats(const gd_ctx *ctx, int64_t *values, const char **names, int max);
+int gd_run_stats(gd_ctx *ctx, int64_t *values, const char **names, int max);
 
 /* Throughput ceiling of the exact squared-distance test in d dimensions on
  * CUDA device `device` (no counterpart in the paper; for measurement).  Runs

@@ -69,6 +69,8 @@ def load_library(path: str | None = None):
         lib.gd_workspace_bytes.restype = ctypes.c_size_t
         lib.gd_dbscan.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan.restype = ctypes.c_int
+        lib.gd_sync.argtypes = [vp, vp]
+        lib.gd_sync.restype = ctypes.c_int
         lib.gd_dbscan_host.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan_host.restype = ctypes.c_int
         lib.gd_status_str.argtypes = [ctypes.c_int]
@@ -206,10 +208,16 @@ class Context:
             raise GdError(st, msg)
 
     # -- clustering
-    def dbscan(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
+    def sync(self, stream=None):
+        """gd_sync: finish the queued call and raise GdError if it failed."""
+        self._check(self._lib.gd_sync(self._h, _stream_handle(stream)))
+
+    def dbscan(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None, sync: bool = True):
         """Cluster the device tensor X (torch.int32, [n, d], contiguous, on this
         context's device).  Returns (labels int32 [n], is_core bool [n]) as
-        device tensors (or fills the given ones; is_core must be uint8/bool)."""
+        device tensors (or fills the given ones; is_core must be uint8/bool).
+        With sync=False the call only queues the work (gd_dbscan is
+        asynchronous): the results are final after sync()."""
         import torch
         if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
             raise TypeError("X must be a CUDA int32 tensor of shape [n, d]")
@@ -222,9 +230,11 @@ class Context:
         st = self._lib.gd_dbscan(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
                                  is_core.data_ptr(), _stream_handle(stream))
         self._check(st)
+        if sync:
+            self.sync(stream)
         return labels, is_core.view(torch.bool) if is_core.dtype == torch.uint8 else is_core
 
-    def dbscan_batched(self, jobs, outputs=None, stream=None):
+    def dbscan_batched(self, jobs, outputs=None, stream=None, sync: bool = True):
         """Cluster a batch of instances in one gd_dbscan_batched call.  jobs is a
         list of (X, eps2, minpts) with X a CUDA int32 [n, d] tensor (n >= 1);
         returns a list of (labels, is_core) device tensors (or fills `outputs`,
@@ -249,6 +259,8 @@ class Context:
             arr[i] = GdInstance(X.data_ptr(), n, d, int(eps2), int(minpts), lab.data_ptr(), core.data_ptr())
         self._check(self._lib.gd_dbscan_batched(self._h, k, ctypes.cast(arr, ctypes.c_void_p),
                                                 _stream_handle(stream)))
+        if sync:
+            self.sync(stream)
         return [(lab, core.view(torch.bool) if core.dtype == torch.uint8 else core) for lab, core in outs]
 
     def dbscan_host(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
@@ -281,10 +293,10 @@ class Context:
 
     # -- introspection
     def last_sizes(self) -> dict:
-        out = (ctypes.c_int64 * 12)()
+        out = (ctypes.c_int64 * 13)()
         self._check(self._lib.gd_last_sizes(self._h, out))
         keys = ["n", "d", "grids", "nnbr", "side", "key_bits", "launches", "pairs", "sort_passes", "digit_bits",
-                "fastmerging_pairs", "key_class"]
+                "fastmerging_pairs", "key_class", "queued"]
         return {k: int(v) for k, v in zip(keys, out)}
 
     def copy_view(self, which: int, dtype, count: int) -> np.ndarray:

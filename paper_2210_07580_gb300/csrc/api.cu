@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gdbscan.h"
 #include "pipeline.h"
@@ -34,7 +35,8 @@ struct CtxMem : MemProvider {
     HostBuf host_[kHostSlots];
     cudaStream_t st = nullptr;
     std::string* err = nullptr;
-    double nbr_ratio = 0.0;  // most neighbour entries per grid seen
+    double pool_ratio = 0.0, runs_ratio = 0.0;  // most pool entries / runs per point seen
+    PlanCache cache;         // plans and sizes of earlier calls, per instance shape
     size_t cap_bytes = 0;    // 0: no cap
     const size_t* extra_held = nullptr;  // other device bytes the context holds (I/O copies)
     int fail_at = 0;         // > 0: the fail_at-th device request from now fails (tests)
@@ -46,10 +48,14 @@ struct CtxMem : MemProvider {
     }
 
     bool pool_enabled() override { return true; }
-    double nbr_per_grid() override { return nbr_ratio; }
-    void note_nbr_per_grid(double r) override {
-        if (r > nbr_ratio) nbr_ratio = r;
+    double pool_per_point() override { return pool_ratio; }
+    double runs_per_point() override { return runs_ratio; }
+    void note_pool(double entries, double runs) override {
+        if (entries > pool_ratio) pool_ratio = entries;
+        if (runs > runs_ratio) runs_ratio = runs;
     }
+    PlanCache* plans() override { return &cache; }
+    void* current(int slot) override { return dev[slot].ptr; }
 
     gd_status device(int slot, size_t bytes, void** out) override {
         DevBuf& b = dev[slot];
@@ -109,7 +115,8 @@ struct CtxMem : MemProvider {
             if (b.ptr) cudaFreeHost(b.ptr);
         for (DevBuf& b : dev) b = DevBuf();
         for (HostBuf& b : host_) b = HostBuf();
-        nbr_ratio = 0.0;
+        pool_ratio = runs_ratio = 0.0;
+        cache.clear();
     }
 };
 
@@ -132,9 +139,19 @@ struct gd_ctx {
     Tuning tuning;
     PhaseGraphs graphs;
     // graphs cannot be captured from the legacy default stream: such calls
-    // run on this stream, ordered after the caller's by an event
+    // run on this stream, ordered after the caller's by events
     cudaStream_t own = nullptr;
-    cudaEvent_t own_ev = nullptr;
+    cudaEvent_t own_ev = nullptr, own_done = nullptr;
+    // the call queued last and not finished yet: its instances (for a run
+    // with exact sizes), the stream it runs on and the caller's stream
+    bool pending = false;
+    std::vector<gd_instance> pend_inst;
+    cudaStream_t pend_st = nullptr, pend_caller = nullptr;
+    gd_status deferred = GD_OK;  // first failure of a call finished before gd_sync
+    std::string deferred_err;
+    // host staging sets (calls alternate) and their last-upload events
+    int next_set = 0;
+    cudaEvent_t stage_ev[2] = {};
 };
 
 namespace {
@@ -148,35 +165,80 @@ gd_status validate_one(const gd_instance& g, std::string* err) {
     return GD_OK;
 }
 
-gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) {
-    ctx->have_run = false;
-    ctx->nstages = 0;
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
-    if (ctx->graphs.enabled && (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)) {
+// The stream a call runs on: the caller's, or (graphs on the legacy
+// default stream, which cannot be captured) the context's own, ordered after
+// the caller's work by an event.
+gd_status call_stream(gd_ctx* ctx, cudaStream_t caller, cudaStream_t* st) {
+    *st = caller;
+    if (ctx->graphs.enabled && (caller == nullptr || caller == cudaStreamLegacy || caller == cudaStreamPerThread)) {
         if (!ctx->own) {
             if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&ctx->own_ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaEventCreateWithFlags(&ctx->own_ev, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ctx->own_done, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
                 return ctx->err = "stream creation failed", GD_ECUDA;
             }
         }
-        // the call returns after its work on `own` is done, so later work on
-        // the caller's stream is ordered after it
-        if (cudaEventRecord(ctx->own_ev, st) != cudaSuccess || cudaStreamWaitEvent(ctx->own, ctx->own_ev, 0) != cudaSuccess)
+        if (cudaEventRecord(ctx->own_ev, caller) != cudaSuccess || cudaStreamWaitEvent(ctx->own, ctx->own_ev, 0) != cudaSuccess)
             return ctx->err = "stream ordering failed", GD_ECUDA;
-        st = ctx->own;
+        *st = ctx->own;
     }
+    return GD_OK;
+}
+
+// Queues a call (see run_batch); with `allow_async` false it reads its sizes
+// back (a run with exact sizes).
+gd_status queue(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t caller, bool allow_async) {
+    cudaStream_t st;
+    gd_status s = call_stream(ctx, caller, &st);
+    if (s != GD_OK) return s;
     ctx->mem.st = st;
     ctx->mem.err = &ctx->err;
     ctx->info = RunInfo();
     ctx->info.want_stats = ctx->stats;
     ctx->info.uf_cap = ctx->uf_cap;
+    const int set = ctx->next_set;
+    ctx->next_set ^= 1;
     const long long l0 = t_launches;
-    gd_status s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning,
-                            &ctx->graphs, ctx->timing ? ctx->sev : nullptr);
+    s = run_batch(ctx->mem, k, inst, st, ctx->timing ? ctx->ev : nullptr, &ctx->info, &ctx->tuning, &ctx->graphs,
+                  ctx->timing ? ctx->sev : nullptr, StageSet{set, ctx->stage_ev[set]}, allow_async);
     ctx->info.sizes[6] = t_launches - l0;
+    if (st != caller && st == ctx->own) {
+        // later work on the caller's stream is ordered after the call
+        if (cudaEventRecord(ctx->own_done, st) != cudaSuccess || cudaStreamWaitEvent(caller, ctx->own_done, 0) != cudaSuccess)
+            if (s == GD_OK) s = (ctx->err = "stream ordering failed", GD_ECUDA);
+    }
     if (s != GD_OK) {
         if (ctx->err.empty()) ctx->err = ctx->info.error;
+        // what was queued must finish before the buffers are touched again
+        cudaStreamSynchronize(st);
+        return s;
+    }
+    ctx->pending = true;
+    ctx->pend_inst.assign(inst, inst + k);
+    ctx->pend_st = st;
+    ctx->pend_caller = caller;
+    return GD_OK;
+}
+
+// Finishes the pending call: waits for it, reads its status back, runs it
+// again with exact sizes if a plan or capacity from an earlier call did not
+// fit, and computes the stage times.
+gd_status finish(gd_ctx* ctx) {
+    if (!ctx->pending) return GD_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
+    const int k = (int)ctx->pend_inst.size();
+    gd_status s = finish_batch(ctx->mem, k, ctx->pend_inst.data(), ctx->pend_st, &ctx->info);
+    if (s == kGdRerun) {
+        ctx->pending = false;
+        const std::vector<gd_instance> again = ctx->pend_inst;  // queue() replaces pend_inst
+        s = queue(ctx, k, again.data(), ctx->pend_caller, false);
+        if (s == GD_OK) s = finish_batch(ctx->mem, k, again.data(), ctx->pend_st, &ctx->info);
+        if (s == kGdRerun) s = (ctx->info.error = "device buffers overflowed on a run with exact sizes", GD_ECUDA);
+    }
+    ctx->pending = false;
+    if (s != GD_OK) {
+        ctx->err = ctx->info.error;
         return s;
     }
     if (ctx->timing) {
@@ -193,9 +255,27 @@ gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) 
         }
         ctx->stage_ms[kStages] = ds;
         ctx->nstages = kStages + 1;
+        cudaGetLastError();
     }
     ctx->have_run = true;
     return GD_OK;
+}
+
+// A new call: the previous one is finished first (its failure is kept for
+// the next gd_sync).
+gd_status run_ctx(gd_ctx* ctx, int k, const gd_instance* inst, cudaStream_t st) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
+    if (ctx->pending) {
+        const gd_status p = finish(ctx);
+        if (p != GD_OK && ctx->deferred == GD_OK) {
+            ctx->deferred = p;
+            ctx->deferred_err = ctx->err;
+        }
+    }
+    ctx->err.clear();
+    ctx->have_run = false;
+    ctx->nstages = 0;
+    return queue(ctx, k, inst, st, true);
 }
 
 }  // namespace
@@ -213,6 +293,7 @@ gd_status gd_create(gd_ctx** out, int device, size_t arena_bytes) {
     cudaError_t e = cudaSetDevice(device);
     for (int i = 0; e == cudaSuccess && i < kStageEvents; ++i) e = cudaEventCreate(&ctx->ev[i]);
     for (int i = 0; e == cudaSuccess && i < 2 * kSortEventPairs; ++i) e = cudaEventCreate(&ctx->sev[i]);
+    for (int i = 0; e == cudaSuccess && i < 2; ++i) e = cudaEventCreateWithFlags(&ctx->stage_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         gd_destroy(ctx);
@@ -229,6 +310,9 @@ void gd_destroy(gd_ctx* ctx) {
     ctx->graphs.release();
     if (ctx->own) cudaStreamDestroy(ctx->own);
     if (ctx->own_ev) cudaEventDestroy(ctx->own_ev);
+    if (ctx->own_done) cudaEventDestroy(ctx->own_done);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->stage_ev[i]) cudaEventDestroy(ctx->stage_ev[i]);
     ctx->mem.release();
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     for (int i = 0; i < kStageEvents; ++i)
@@ -303,6 +387,9 @@ gd_status gd_dbscan_host(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, i
         return ctx->err = "copy in failed", GD_ECUDA;
     s = run_ctx(ctx, 1, &dg, st);
     if (s != GD_OK) return s;
+    // the result is final only once the call is finished (it may run again)
+    s = gd_sync(ctx, stream);
+    if (s != GD_OK) return s;
     if (cudaMemcpyAsync(labels_host, dg.labels, lb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return ctx->err = "copy out failed", GD_ECUDA;
     if (is_core_host && cudaMemcpyAsync(is_core_host, dg.is_core, cb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -318,9 +405,24 @@ size_t gd_ctx_bytes(const gd_ctx* ctx) {
     return b;
 }
 
+gd_status gd_sync(gd_ctx* ctx, gd_stream_t stream) {
+    if (!ctx) return GD_EINVAL;
+    (void)stream;  // a context has at most one call in flight: its own stream is known
+    gd_status s = finish(ctx);
+    if (ctx->deferred != GD_OK) {
+        const gd_status d = ctx->deferred;
+        ctx->err = ctx->deferred_err;
+        ctx->deferred = GD_OK;
+        ctx->deferred_err.clear();
+        return d;
+    }
+    return s;
+}
+
 gd_status gd_ctx_trim(gd_ctx* ctx) {
     if (!ctx) return GD_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return GD_ECUDA;
+    finish(ctx);
     if (ctx->mem.st) cudaStreamSynchronize(ctx->mem.st);
     ctx->graphs.release();
     ctx->mem.release();
@@ -379,13 +481,16 @@ const char* gd_status_str(gd_status s) {
 
 const char* gd_last_error(const gd_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
-gd_status gd_last_sizes(const gd_ctx* ctx, int64_t out[12]) {
-    if (!ctx || !out || !ctx->have_run) return GD_EINVAL;
-    for (int i = 0; i < 12; ++i) out[i] = ctx->info.sizes[i];
+gd_status gd_last_sizes(gd_ctx* ctx, int64_t out[13]) {
+    if (!ctx || !out) return GD_EINVAL;
+    if (ctx->pending) finish(ctx);
+    if (!ctx->have_run) return GD_EINVAL;
+    for (int i = 0; i < 13; ++i) out[i] = ctx->info.sizes[i];
     return GD_OK;
 }
 
 gd_status gd_copy_view(gd_ctx* ctx, gd_view which, void* host_dst, size_t bytes) {
+    if (ctx && ctx->pending) finish(ctx);
     if (!ctx || !ctx->have_run || (int)which < 0 || (int)which > 6 || (!host_dst && bytes)) return GD_EINVAL;
     if (bytes > ctx->info.view_bytes[which]) return ctx->err = "view smaller than requested bytes", GD_EINVAL;
     if (bytes == 0) return GD_OK;
@@ -427,7 +532,8 @@ static const char* const kStatNames[kStatCount] = {
     "kappa_1", "kappa_2", "kappa_3", "kappa_4", "kappa_5", "kappa_6", "kappa_7", "kappa_8", "kappa_9",
     "kappa_10", "kappa_11", "kappa_12", "kappa_13", "kappa_14", "kappa_15", "kappa_16_or_more"};
 
-int gd_run_stats(const gd_ctx* ctx, int64_t* values, const char** names, int max) {
+int gd_run_stats(gd_ctx* ctx, int64_t* values, const char** names, int max) {
+    if (ctx && ctx->pending) finish(ctx);
     if (!ctx || !ctx->have_run || !ctx->info.have_stats) return 0;
     const int k = kStatCount < max ? kStatCount : max;
     for (int i = 0; i < k; ++i) {
@@ -437,8 +543,9 @@ int gd_run_stats(const gd_ctx* ctx, int64_t* values, const char** names, int max
     return k;
 }
 
-int gd_stage_times(const gd_ctx* ctx, float* ms, const char** names, int max) {
+int gd_stage_times(gd_ctx* ctx, float* ms, const char** names, int max) {
     if (!ctx) return 0;
+    if (ctx->pending) finish(ctx);
     int k = ctx->nstages < max ? ctx->nstages : max;
     for (int i = 0; i < k; ++i) {
         if (ms) ms[i] = ctx->stage_ms[i];

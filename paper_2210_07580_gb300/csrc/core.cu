@@ -21,6 +21,7 @@ static int blocks_for(long long total) {
 constexpr int kFillLane = 64;  // largest grid a lane fills alone
 
 __global__ void __launch_bounds__(256) core_full_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     const int lane = lane_id();
     const long long stride = (long long)gridDim.x * blockDim.x;
     FlatCursor cur;
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(256) core_full_kernel(const Inst* __restrict__
 
 // nf_start[c] = size of grid c if it is not full, else 0 (scanned next).
 __global__ void nonfull_count_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -76,6 +78,7 @@ __global__ void nonfull_count_kernel(const Inst* __restrict__ ins, Flat f, long 
 // its neighbour grids -- the points a count that stages every neighbour grid
 // once per non-full grid reads.
 __global__ void core_stats_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -269,6 +272,7 @@ constexpr int kCoreWarps = 8;
 template <int D>
 __global__ void __launch_bounds__(32 * kCoreWarps)
     core_grid_kernel(const Inst* __restrict__ ins, Flat f, long long total, int band_limit) {
+    total = flat_total(f);
     constexpr int DP = Padded<D>::value;
     __shared__ int sx[kCoreWarps][32][D];      // the grid's points (32 at a time)
     __shared__ int sbox[kCoreWarps][2 * D][32];  // the entries' boxes: lo then hi, lane-major

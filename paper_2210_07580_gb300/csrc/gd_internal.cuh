@@ -31,7 +31,14 @@ inline int size_bucket(long long n) {
 constexpr unsigned kFull = 0xffffffffu;
 
 // Bits of an instance's device status word (OR-ed by kernels).
-enum : unsigned { kDevTimeout = 1u, kDevOverflow = 2u };
+//   kDevTimeout  a bounded union-find loop ran out (GD_ETIMEOUT);
+//   kDevOverflow a buffer sized from an earlier call was too small (the
+//                neighbour lists or FastMerging bitmaps): the result is not
+//                valid and the call is run again with exact sizes;
+//   kDevReplan   the grid key layout of the data does not fit the launch
+//                plan reused from an earlier call: likewise;
+//   kDevRange    d * R^2 >= 2^62 or a key wider than 128 bits (GD_ERANGE).
+enum : unsigned { kDevTimeout = 1u, kDevOverflow = 2u, kDevReplan = 4u, kDevRange = 8u };
 
 // Retry cap for the lock-free union-find loops: far above any legitimate
 // number of CAS retries, so reaching it means something is wrong; the kernel
@@ -84,6 +91,9 @@ enum SmallSlot {
     kSmHard0 = 23,      // pairs handed to FastMerging, wave 0
     kSmHard1 = 24,      // ... wave 1
     kSmPool = 26,       // [2] instance 0 only: 64-bit neighbour-pool counter
+    kSmKeyClass = 28,   // the sort plan: key class,
+    kSmKeyBits = 29,    // ... key bits (the device's layout when it computes it),
+    kSmKeyWords = 30,   // ... key words
     kSmLevelCount = 32, // [8] nodes per grid-tree level
     kSmallInts = 64
 };
@@ -150,6 +160,7 @@ struct Inst {
     int* nbr;
     int* nbr_fwd;
     int* nbr_bwd;
+    long long nbr_cap;  // entries the instance's list buffer holds (and its hard-pair buffer)
     int* nf_start;
     int* core_start;
     int* bbox;
@@ -166,7 +177,10 @@ struct Inst {
 };
 
 // Flat item space over the instances of a launch: item i belongs to instance
-// idx[k] for off[k] <= i < off[k+1] (off has K+1 entries).
+// idx[k] for off[k] <= i < off[k+1] (off has K+1 entries).  The offsets of a
+// space over grids are filled on the device (count_flat), so a kernel takes
+// its loop bound from off[K] (flat_total); the `total` a launcher receives
+// from the host only sizes the launch (an upper bound).
 struct Flat {
     const long long* off;
     const int* idx;
@@ -271,8 +285,12 @@ __device__ __forceinline__ unsigned uf_priority(int x) {
 // Union-find root with path halving; -1 if the retry cap is reached.  Parents
 // are read through L2 (other SMs link roots concurrently) and every halving
 // store writes an ancestor, so concurrent finds and unions stay consistent.
+// CAP: the loop bound is the run's (lowered) cap; otherwise the built-in
+// constant, which keeps the loop the compiler's to schedule (a runtime bound
+// measured about 30% slower in the merge).
+template <bool CAP = false>
 __device__ __forceinline__ int uf_find(int* parent, int x, int cap) {
-    for (int it = 0; it < cap; ++it) {
+    for (int it = 0; it < (CAP ? cap : kMaxUfRetries); ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) return x;
         const int gp = __ldcg(parent + px);
@@ -285,8 +303,9 @@ __device__ __forceinline__ int uf_find(int* parent, int x, int cap) {
 // The root of x without writing anything.  Used where every grid's pointer
 // must end at its root: a halving store by one thread can put back an older
 // ancestor over the root another thread has just written.
+template <bool CAP = false>
 __device__ __forceinline__ int uf_find_ro(const int* parent, int x, int cap) {
-    for (int it = 0; it < cap; ++it) {
+    for (int it = 0; it < (CAP ? cap : kMaxUfRetries); ++it) {
         const int px = __ldcg(parent + x);
         if (px == x) return x;
         x = px;
@@ -330,10 +349,12 @@ extern thread_local long long t_launches;
 struct ScanSeg {
     const int* in;
     int* out;
-    long long len;
-    long long blk0;
-    int* tot;  // also receives the segment's total (out[len]), if not null
+    long long len;        // the length, or (with len_dev) an upper bound of it
+    long long blk0;       // first tile of the segment (tiles counted from len)
+    int* tot;             // also receives the segment's total (out[len]), if not null
+    const int* len_dev;   // if not null: the length, read on the device
 };
+__device__ __forceinline__ long long seg_len(const ScanSeg& sg) { return sg.len_dev ? *sg.len_dev : sg.len; }
 constexpr int kScanTile = 2048;
 // tmp: at least (total tiles + K) ints.  longest: the longest segment's
 // length if known (segments of at most kScanOneLaunch elements are scanned
@@ -345,6 +366,20 @@ cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int
 // Device-side flat offsets: off[0] = 0, off[k+1] = off[k] + small[slot] of
 // instance idx[k].
 cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st);
+// Several such flat spaces in one launch (one thread each).
+struct FlatSpec {
+    const int* idx;
+    long long* off;
+    int m;
+    int slot;
+};
+cudaError_t count_flats(const Inst* ins, const FlatSpec* specs, int n, cudaStream_t st);
+// The grid-key layout of each instance from its bounds (Eq. 1 identifiers
+// packed, dimension 1 most significant): mn, bits, shift and key_bits in the
+// device records.  The launch plan (key class, passes, digit bits) is the
+// host's; a layout that does not fit it sets kDevReplan, a range too large
+// kDevRange.
+cudaError_t launch_layout(Inst* ins, int K, cudaStream_t st);
 
 // Grid construction (grid.cu).
 // Over the instances of dimension d.
@@ -410,7 +445,12 @@ struct WalkPool {
 enum WalkMode { kWalkCount = 0, kWalkFill = 1, kWalkPool = 2 };
 cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
                         cudaStream_t st);
-cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st);
+// The pool's runs into the lists (nothing when the pool overflowed; the
+// filling walk, kWalkFill, runs only then -- or always without a pool).
+cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, cudaStream_t st);
+// Lists whose total exceeds the instance's nbr_cap are given up (emptied,
+// kDevOverflow).
+cudaError_t launch_nbr_check(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // After a counting or pooled walk: nbr_start[c] = forward + backward entries
 // (scanned next), backward counts reset to serve as placement cursors.
 cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaStream_t st);
@@ -436,21 +476,22 @@ constexpr int kLdfBuckets = 128;
 cudaError_t launch_ldf_order(const Inst* ins, const int* idx, int K, Flat cells, long long total, cudaStream_t st);
 
 cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, bool cap, cudaStream_t st);
 // Warp-level test of the candidate pairs of one wave (touching order: 0 =
 // touching pairs, 1 = the others; LDF order: wave 0 only), taken from the
 // neighbour lists of the grids of `cells` (instances of dimension d);
 // undecided pairs go to the instance's hard list.
+// (cap: the union-find loops take the run's lowered cap, Params::uf_cap.)
 cudaError_t launch_merge_list(const Inst* ins, Flat cells, long long total, int wave, int d, int budget,
-                              int lane_limit, int small_set, cudaStream_t st);
+                              int lane_limit, int small_set, bool cap, cudaStream_t st);
 // FastMerging (Alg. 5) of the hard pairs of one wave: `blocks` blocks, block b
 // using the 2 * wpb bitmap words at scratch + 2 * wpb * b (wpb >= the largest
 // grid of the batch / 32 + 1).
 cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
-                               cudaStream_t st);
+                               bool cap, cudaStream_t st);
 
 // Labels (label.cu).
-cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, bool cap, cudaStream_t st);
 cudaError_t launch_labels(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
 
 }  // namespace gd

@@ -9,10 +9,14 @@ namespace gd {
 
 // ------------------------------------------------------- segmented scan
 // Three phases: per-tile sums, one block per segment scanning its tiles'
-// sums, per-tile scan.  A tile never spans two segments.
+// sums, per-tile scan.  A tile never spans two segments.  A segment's tiles
+// are laid out for its length bound; with a device-side length the tiles
+// past it hold nothing, and the tile kernels loop over the tiles from a
+// bounded grid, so unused tiles cost one test each.
 
 constexpr int kScanBlock = 256;
 constexpr int kScanItems = kScanTile / kScanBlock;
+constexpr int kScanGrid = 152 * 8;  // blocks of the tile kernels (grid-stride over tiles)
 
 __device__ __forceinline__ int seg_of_tile(const ScanSeg* segs, int K, long long b) {
     int lo = 0, hi = K - 1;
@@ -27,18 +31,25 @@ __device__ __forceinline__ int seg_of_tile(const ScanSeg* segs, int K, long long
 }
 
 __global__ void __launch_bounds__(kScanBlock) seg_reduce_kernel(const ScanSeg* __restrict__ segs, int K,
-                                                                int* __restrict__ bsum) {
+                                                                long long total_tiles, int* __restrict__ bsum) {
     __shared__ int sm[33];
-    const int k = seg_of_tile(segs, K, blockIdx.x);
-    const ScanSeg sg = segs[k];
-    const long long base = (blockIdx.x - sg.blk0) * (long long)kScanTile + (long long)threadIdx.x * kScanItems;
-    int s = 0;
+    for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const ScanSeg sg = segs[seg_of_tile(segs, K, t)];
+        const long long len = seg_len(sg);
+        const long long base = (t - sg.blk0) * (long long)kScanTile;
+        if (base >= len) {  // past the segment's length: block-uniform
+            if (threadIdx.x == 0) bsum[t] = 0;
+            continue;
+        }
+        const long long at = base + (long long)threadIdx.x * kScanItems;
+        int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
-        if (base + i < sg.len) s += sg.in[base + i];
-    int total;
-    block_exclusive_scan(s, sm, &total);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+        for (int i = 0; i < kScanItems; ++i)
+            if (at + i < len) s += sg.in[at + i];
+        int total;
+        block_exclusive_scan(s, sm, &total);
+        if (threadIdx.x == 0) bsum[t] = total;
+    }
 }
 
 // One block per segment: exclusive scan of its tiles' sums in place; the
@@ -47,7 +58,9 @@ __global__ void __launch_bounds__(1024) seg_top_kernel(const ScanSeg* __restrict
                                                        long long total_tiles) {
     __shared__ int sm[33];
     const ScanSeg sg = segs[blockIdx.x];
-    const long long end = (blockIdx.x + 1 < gridDim.x) ? segs[blockIdx.x + 1].blk0 : total_tiles;
+    const long long len = seg_len(sg);
+    long long end = (blockIdx.x + 1 < gridDim.x) ? segs[blockIdx.x + 1].blk0 : total_tiles;
+    end = min(end, sg.blk0 + (len + kScanTile - 1) / kScanTile);
     int carry = 0;
     for (long long base = sg.blk0; base < end; base += 1024) {
         const long long k = base + threadIdx.x;
@@ -58,30 +71,34 @@ __global__ void __launch_bounds__(1024) seg_top_kernel(const ScanSeg* __restrict
         carry += total;
     }
     if (threadIdx.x == 0) {
-        sg.out[sg.len] = carry;
+        sg.out[len] = carry;
         if (sg.tot) *sg.tot = carry;
     }
 }
 
 __global__ void __launch_bounds__(kScanBlock) seg_down_kernel(const ScanSeg* __restrict__ segs, int K,
-                                                              const int* __restrict__ bsum) {
+                                                              long long total_tiles, const int* __restrict__ bsum) {
     __shared__ int sm[33];
-    const int k = seg_of_tile(segs, K, blockIdx.x);
-    const ScanSeg sg = segs[k];
-    const long long base = (blockIdx.x - sg.blk0) * (long long)kScanTile + (long long)threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int s = 0;
+    for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const ScanSeg sg = segs[seg_of_tile(segs, K, t)];
+        const long long len = seg_len(sg);
+        const long long base = (t - sg.blk0) * (long long)kScanTile;
+        if (base >= len) continue;
+        const long long at = base + (long long)threadIdx.x * kScanItems;
+        int v[kScanItems];
+        int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < sg.len) ? sg.in[base + i] : 0;
-        s += v[i];
-    }
-    int total;
-    int run = bsum[blockIdx.x] + block_exclusive_scan(s, sm, &total);
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = (at + i < len) ? sg.in[at + i] : 0;
+            s += v[i];
+        }
+        int total;
+        int run = bsum[t] + block_exclusive_scan(s, sm, &total);
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < sg.len) sg.out[base + i] = run;
-        run += v[i];
+        for (int i = 0; i < kScanItems; ++i) {
+            if (at + i < len) sg.out[at + i] = run;
+            run += v[i];
+        }
     }
 }
 
@@ -91,27 +108,28 @@ constexpr int kScanOneItems = 8;
 __global__ void __launch_bounds__(1024) seg_single_kernel(const ScanSeg* __restrict__ segs) {
     __shared__ int sm[33];
     const ScanSeg sg = segs[blockIdx.x];
+    const long long len = seg_len(sg);
     int carry = 0;
-    for (long long base = 0; base < sg.len; base += 1024 * kScanOneItems) {
+    for (long long base = 0; base < len; base += 1024 * kScanOneItems) {
         const long long at = base + (long long)threadIdx.x * kScanOneItems;
         int v[kScanOneItems];
         int s = 0;
 #pragma unroll
         for (int i = 0; i < kScanOneItems; ++i) {
-            v[i] = at + i < sg.len ? sg.in[at + i] : 0;
+            v[i] = at + i < len ? sg.in[at + i] : 0;
             s += v[i];
         }
         int total;
         int run = carry + block_exclusive_scan(s, sm, &total);
 #pragma unroll
         for (int i = 0; i < kScanOneItems; ++i) {
-            if (at + i < sg.len) sg.out[at + i] = run;
+            if (at + i < len) sg.out[at + i] = run;
             run += v[i];
         }
         carry += total;
     }
     if (threadIdx.x == 0) {
-        sg.out[sg.len] = carry;
+        sg.out[len] = carry;
         if (sg.tot) *sg.tot = carry;
     }
 }
@@ -124,14 +142,15 @@ cudaError_t scan_segments(const ScanSeg* segs, int K, long long total_tiles, int
         GD_COUNT_LAUNCH();
         return cudaGetLastError();
     }
+    const int grid = (int)(total_tiles < kScanGrid ? (total_tiles > 0 ? total_tiles : 1) : kScanGrid);
     if (total_tiles > 0) {
-        seg_reduce_kernel<<<(unsigned)total_tiles, kScanBlock, 0, st>>>(segs, K, tmp);
+        seg_reduce_kernel<<<grid, kScanBlock, 0, st>>>(segs, K, total_tiles, tmp);
         GD_COUNT_LAUNCH();
     }
     seg_top_kernel<<<K, 1024, 0, st>>>(segs, tmp, total_tiles);
     GD_COUNT_LAUNCH();
     if (total_tiles > 0) {
-        seg_down_kernel<<<(unsigned)total_tiles, kScanBlock, 0, st>>>(segs, K, tmp);
+        seg_down_kernel<<<grid, kScanBlock, 0, st>>>(segs, K, total_tiles, tmp);
         GD_COUNT_LAUNCH();
     }
     return cudaGetLastError();
@@ -152,6 +171,72 @@ __global__ void count_flat_kernel(const Inst* __restrict__ ins, const int* __res
 
 cudaError_t count_flat(const Inst* ins, const int* idx, int K, int slot, long long* off, cudaStream_t st) {
     count_flat_kernel<<<1, 32, 0, st>>>(ins, idx, K, slot, off);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+__global__ void count_flats_kernel(const Inst* __restrict__ ins, const FlatSpec* __restrict__ specs, int n) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const FlatSpec sp = specs[t];
+        long long run = 0;
+        sp.off[0] = 0;
+        for (int k = 0; k < sp.m; ++k) {
+            run += ins[sp.idx[k]].small[sp.slot];
+            sp.off[k + 1] = run;
+        }
+    }
+}
+
+cudaError_t count_flats(const Inst* ins, const FlatSpec* specs, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    count_flats_kernel<<<(n + 63) / 64, 64, 0, st>>>(ins, specs, n);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- layout
+
+__device__ __forceinline__ int bit_length_u64(unsigned long long v) { return v ? 64 - __clzll(v) : 0; }
+
+__global__ void layout_kernel(Inst* __restrict__ ins, int K) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        Inst& I = ins[k];
+        Params& p = I.p;
+        unsigned long long rmax = 0;
+        int total_bits = 0;
+        for (int j = 0; j < p.d; ++j) {
+            const long long lo = I.small[kSmMnmx + j], up = I.small[kSmMnmx + kMaxD + j];
+            const unsigned long long rj = (unsigned long long)(up - lo);
+            if (rj > rmax) rmax = rj;
+            p.mn[j] = (int)lo;
+            p.bits[j] = bit_length_u64(rj / (unsigned long long)p.s);
+            total_bits += p.bits[j];
+        }
+        for (int j = p.d - 1, sh = 0; j >= 0; --j) {
+            p.shift[j] = sh;
+            sh += p.bits[j];
+        }
+        p.key_bits = total_bits;
+        I.small[kSmKeyBits] = total_bits;
+        unsigned st = 0;
+        // d * rmax^2 >= 2^62, in 128 bits
+        const unsigned long long r2lo = rmax * rmax, r2hi = __umul64hi(rmax, rmax);
+        const unsigned long long dlo = r2lo * (unsigned long long)p.d;
+        const unsigned long long dhi = r2hi * (unsigned long long)p.d + __umul64hi(r2lo, (unsigned long long)p.d);
+        if (dhi != 0 || dlo >= (1ull << 62) || total_bits > 128) st |= kDevRange;
+        // the plan's passes cover the key; the key class holds it
+        const int cap = I.passes * I.digit_bits;
+        const bool fits = total_bits <= cap &&
+                          (p.key_class == 2 ? total_bits <= 128
+                                            : (p.key_class == 1 ? total_bits <= 64 : total_bits + p.pack_bits <= 64));
+        if (!fits) st |= kDevReplan;
+        if (st) atomicOr(reinterpret_cast<unsigned*>(I.small + kSmStatus), st);
+    }
+}
+
+cudaError_t launch_layout(Inst* ins, int K, cudaStream_t st) {
+    if (K <= 0) return cudaSuccess;
+    layout_kernel<<<(K + 63) / 64, 64, 0, st>>>(ins, K);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
@@ -180,6 +265,7 @@ constexpr int kBoundsWarps = 8;  // 256 threads
 
 template <int D>
 __global__ void __launch_bounds__(kBoundsWarps * 32) bounds_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     const long long per = (((total + nwarps - 1) / nwarps) + 31) & ~31ll;
@@ -460,6 +546,7 @@ cudaError_t launch_compact_write(const Inst* ins, Flat tiles, long long total, i
 // steps over the rest of an instance, reduces the sizes in the warp and
 // applies one atomic.  small[kSmMaxCell] must be 0 first.
 __global__ void cell_max_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     const long long stride = (long long)gridDim.x * blockDim.x;
     FlatCursor cur;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;) {

@@ -22,7 +22,9 @@ static int blocks_for(long long total) {
 __device__ __forceinline__ const int* perm_of(const Inst& I) { return (I.passes & 1) ? I.valB : I.valA; }
 
 // Point every core grid at its root and reset the per-root minimum.
+template <bool CAP>
 __global__ void uf_compress_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -32,7 +34,7 @@ __global__ void uf_compress_kernel(const Inst* __restrict__ ins, Flat f, long lo
         I.cid_root[c] = INT_MAX;
         if (I.core_start[c + 1] > I.core_start[c]) {
             // read-only: concurrent halving could undo this grid's pointer
-            const int r = uf_find_ro(I.parent, c, I.p.uf_cap);
+            const int r = uf_find_ro<CAP>(I.parent, c, I.p.uf_cap);
             if (r < 0)
                 set_status(I, kDevTimeout);
             else
@@ -44,6 +46,7 @@ __global__ void uf_compress_kernel(const Inst* __restrict__ ins, Flat f, long lo
 // Grid order keeps input order inside a grid (the sort is stable), so the
 // first core point of a grid has the grid's smallest core input index.
 __global__ void cid_min_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -58,6 +61,7 @@ __global__ void cid_min_kernel(const Inst* __restrict__ ins, Flat f, long long t
 }
 
 __global__ void cell_cid_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -68,10 +72,13 @@ __global__ void cell_cid_kernel(const Inst* __restrict__ ins, Flat f, long long 
     }
 }
 
-cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+cudaError_t launch_cluster_ids(const Inst* ins, Flat cells, long long total, bool cap, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     const int nb = blocks_for(total);
-    uf_compress_kernel<<<nb, 256, 0, st>>>(ins, cells, total);
+    if (cap)
+        uf_compress_kernel<true><<<nb, 256, 0, st>>>(ins, cells, total);
+    else
+        uf_compress_kernel<false><<<nb, 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     cid_min_kernel<<<nb, 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
@@ -132,6 +139,7 @@ constexpr int kLabelChunk = 128;
 
 template <int D>
 __global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     constexpr int U = 4;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
@@ -181,6 +189,7 @@ __global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ in
 // core flag in bit 31) in labels[] split into the label and the flag.
 // Coalesced reads and writes.
 __global__ void __launch_bounds__(256) label_split_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);

@@ -22,6 +22,7 @@ static int blocks_for(long long total) {
 // m_c (core points per grid, into core_start before its scan) and reset of
 // the grid's core bounding box.
 __global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -78,6 +79,7 @@ __device__ __forceinline__ void box_flush(int* box, const int* lo, const int* hi
 
 template <int D>
 __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -211,6 +213,7 @@ __device__ __forceinline__ int core_m(const Inst& I, int c) { return I.core_star
 // starts: ldf_grid[slot] = grid.
 template <bool RANK>
 __global__ void __launch_bounds__(256) ldf_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
          base += (long long)gridDim.x * blockDim.x) {
@@ -270,6 +273,7 @@ cudaError_t launch_ldf_order(const Inst* ins, const int* idx, int K, Flat cells,
 // (Cluster ids do not depend on which grid ends up the root.)
 
 __global__ void uf_init_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -288,14 +292,16 @@ cudaError_t launch_uf_init(const Inst* ins, Flat cells, long long total, cudaStr
 
 // Between the waves: point every grid at its root, so that the second wave's
 // precheck costs two loads per pair.
+template <bool CAP>
 __global__ void uf_flatten_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
         const int k = cur.k;
         const Inst& I = ins[f.idx[k]];
         const int c = (int)(i - cur.lo);
-        const int r = uf_find(I.parent, c, I.p.uf_cap);
+        const int r = uf_find<CAP>(I.parent, c, I.p.uf_cap);
         if (r < 0)
             set_status(I, kDevTimeout);
         else if (r != c)
@@ -303,18 +309,22 @@ __global__ void uf_flatten_kernel(const Inst* __restrict__ ins, Flat f, long lon
     }
 }
 
-cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+cudaError_t launch_uf_flatten(const Inst* ins, Flat cells, long long total, bool cap, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    uf_flatten_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    if (cap)
+        uf_flatten_kernel<true><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    else
+        uf_flatten_kernel<false><<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }
 
 // Returns false if the retry cap was hit.
+template <bool CAP>
 __device__ __forceinline__ bool uf_union(int* parent, int a, int b, int cap) {
-    for (int it = 0; it < cap; ++it) {
-        a = uf_find(parent, a, cap);
-        b = uf_find(parent, b, cap);
+    for (int it = 0; it < (CAP ? cap : kMaxUfRetries); ++it) {
+        a = uf_find<CAP>(parent, a, cap);
+        b = uf_find<CAP>(parent, b, cap);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         if (uf_priority(a) < uf_priority(b)) {
@@ -367,10 +377,11 @@ __device__ __forceinline__ int box_decision(const int* bi, const int* bj, long l
 // handed to the block-level FastMerging kernel -- in particular a few points
 // against thousands, where one scan of the large set usually decides.  Hard
 // pairs of wave 1 are stored after wave 0's.
-template <int D>
-__global__ void __launch_bounds__(256)
+template <int D, bool CAP>
+__global__ void __launch_bounds__(256, 4)  // latency-bound: four blocks per SM (64 registers)
     merge_list_kernel(const Inst* __restrict__ ins, Flat f, long long total, int wave, int budget, int lane_limit,
                       int small_set) {
+    total = flat_total(f);
     constexpr int DP = Padded<D>::value;
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(256)
             int outcome = -1;    // statistics: the slot that decided the lane's pair
             unsigned ndist = 0;  // statistics: distances this lane evaluated
             if (keep) {
-                const int ra = uf_find(parent, c, cap), rb = uf_find(parent, j2, cap);
+                const int ra = uf_find<CAP>(parent, c, cap), rb = uf_find<CAP>(parent, j2, cap);
                 if (ra < 0 || rb < 0) {
                     set_status(I, kDevTimeout);
                 } else if (ra == rb) {
@@ -457,7 +468,7 @@ __global__ void __launch_bounds__(256)
                             outcome = -1;
                         }
                     }
-                    if (yes && !uf_union(parent, c, j2, cap)) set_status(I, kDevTimeout);
+                    if (yes && !uf_union<CAP>(parent, c, j2, cap)) set_status(I, kDevTimeout);
                 }
             }
             acc_pairs += __popc(__ballot_sync(kFull, keep));
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(256)
                 const int py = __shfl_sync(kFull, j2, src);
                 int same = 0;
                 if (lane == 0) {
-                    const int ra = uf_find(parent, c, cap), rb = uf_find(parent, py, cap);
+                    const int ra = uf_find<CAP>(parent, c, cap), rb = uf_find<CAP>(parent, py, cap);
                     if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
                     same = ra == rb;
                 }
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(256)
                     stat_add(stv, handed ? kStHanded : kStWarp, 1);
                     stat_add(stv, kStDistMerge, tile_dist);
                     if (yes) {
-                        if (!uf_union(parent, c, py, cap)) set_status(I, kDevTimeout);
+                        if (!uf_union<CAP>(parent, c, py, cap)) set_status(I, kDevTimeout);
                     } else if (handed) {
                         I.hard[hard_base + atomicAdd(I.small + kSmHard0 + wave, 1)] = make_int2(c, py);
                     }
@@ -534,14 +545,19 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_merge_list(const Inst* ins, Flat cells, long long total, int wave, int d, int budget,
-                              int lane_limit, int small_set, cudaStream_t st) {
+                              int lane_limit, int small_set, bool cap, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     long long b = (total * 32 + 255) / 256;
     if (b > kPersistBlocks) b = kPersistBlocks;
     switch (d) {
-#define GD_MW(DD)                                                                                             \
-    case DD:                                                                                                  \
-        merge_list_kernel<DD><<<(int)b, 256, 0, st>>>(ins, cells, total, wave, budget, lane_limit, small_set); \
+#define GD_MW(DD)                                                                                                    \
+    case DD:                                                                                                         \
+        if (cap)                                                                                                     \
+            merge_list_kernel<DD, true><<<(int)b, 256, 0, st>>>(ins, cells, total, wave, budget, lane_limit,       \
+                                                                 small_set);                                       \
+        else                                                                                                         \
+            merge_list_kernel<DD, false><<<(int)b, 256, 0, st>>>(ins, cells, total, wave, budget, lane_limit,      \
+                                                                  small_set);                                      \
         break;
         GD_MW(1) GD_MW(2) GD_MW(3) GD_MW(4) GD_MW(5) GD_MW(6) GD_MW(7) GD_MW(8)
 #undef GD_MW
@@ -565,24 +581,26 @@ cudaError_t launch_merge_list(const Inst* ins, Flat cells, long long total, int 
 //   - angle (Def. 8, Thm. 1): the angle between pq and px exceeds
 //     lambda = max over the other set's live points y of
 //     arcsin(eps / |py|) + angle(pq, py).
-// The angle test runs in double precision on exact int64 inputs (squared
-// lengths and dot products) and prunes only with a margin: cos(angle(pq, px))
-// < cos(lambda) - kAngleMargin, and never when some lambda_y may reach pi
-// (cos is decreasing only on [0, pi]).  Every quantity is a handful of
-// correctly rounded IEEE operations (+, -, *, /, sqrt: relative error at
-// most 2^-53 each; Higham, "Accuracy and Stability of Numerical
-// Algorithms", 2nd ed., Sec. 2.2 and Lemma 3.1), so the computed cosines are
-// within 1e-14 of the exact ones; the margin of 1e-9 makes every angle
-// prune one the exact test would also make.  Pruning less never changes the
-// answer (Thm. 2), only the number of rounds.
+// The angle test runs in single precision on exact int64 inputs (squared
+// lengths and dot products, each rounded once to float) and prunes only with
+// a margin: cos(angle(pq, px)) < cos(lambda) - kAngleMargin, and never when
+// some lambda_y may reach pi (cos is decreasing only on [0, pi]).  Every
+// quantity is a handful of correctly rounded IEEE operations (+, -, *, /,
+// sqrt: relative error at most 2^-24 each; Higham, "Accuracy and Stability
+// of Numerical Algorithms", 2nd ed., Sec. 2.2 and Lemma 3.1) on values of
+// magnitude at most 1, so the computed cosines are within 1e-6 of the exact
+// ones; the margin of 1e-4 makes every angle prune one the exact test would
+// also make.  Pruning less never changes the answer (Thm. 2), only the
+// number of rounds.  (Single precision: this GPU's double-precision rate is
+// a small fraction of its single-precision rate.)
 // s_i is the smaller set.  Each pruning is fused with the next argmin, so a
 // round is three passes over live points (the angle bound, then the pruning
 // with the argmin).  Every round removes p from s_i and q from s_j, so the
 // loop ends after at most min(m_i, m_j) rounds.  The live sets are bitmaps
 // (one word per 32 points) in the block's slice of the scratch.
 
-constexpr double kAngleMargin = 1e-9;
-constexpr double kNoAngle = -4.0;  // cos(lambda) sentinel: no angle pruning
+constexpr float kAngleMargin = 1e-4f;
+constexpr float kNoAngle = -4.0f;  // cos(lambda) sentinel: no angle pruning
 
 __device__ __forceinline__ bool triangle_trivial(long long A, long long B, long long eps2) {
     // x is trivial iff sqrt(A) + sqrt(eps2) < sqrt(B)
@@ -635,16 +653,16 @@ __device__ __forceinline__ BestPt block_best(BestPt v, int cnt, BestPt* sb, int*
     return r;
 }
 
-// Block-wide minimum of a double; every thread gets it.
-__device__ __forceinline__ double block_min(double v, double* sd) {
+// Block-wide minimum of a float; every thread gets it.
+__device__ __forceinline__ float block_min(float v, float* sd) {
     const int lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(kFull, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_down_sync(kFull, v, o));
     if (lane == 0) sd[warp] = v;
     __syncthreads();
-    double r = sd[0];
+    float r = sd[0];
 #pragma unroll
-    for (int w = 1; w < kFmWarps; ++w) r = fmin(r, sd[w]);
+    for (int w = 1; w < kFmWarps; ++w) r = fminf(r, sd[w]);
     __syncthreads();
     return r;
 }
@@ -681,12 +699,12 @@ __device__ __forceinline__ long long dot_from(const long long* o, const long lon
 // other set S of cos(arcsin(eps / |py|) + angle(pq, py)), or kNoAngle when
 // some lambda_y may reach pi.
 template <int D, int DP>
-__device__ double fm_cos_lambda(const int* __restrict__ S, int m, const unsigned* live, const long long* p,
-                                const long long* q, long long a2, long long eps2, double* sd,
-                                unsigned long long* ndist) {
+__device__ float fm_cos_lambda(const int* __restrict__ S, int m, const unsigned* live, const long long* p,
+                               const long long* q, long long a2, long long eps2, float* sd,
+                               unsigned long long* ndist) {
     const int lane = lane_id();
-    const double a = sqrt((double)a2), eps = sqrt((double)eps2);
-    double best = 2.0;
+    const float a = sqrtf((float)a2), eps = sqrtf((float)eps2);
+    float best = 2.0f;
     int nlive = 0;
     for (int base = 0; base < m; base += kFmBlock) {
         const int k = base + threadIdx.x;
@@ -696,14 +714,14 @@ __device__ double fm_cos_lambda(const int* __restrict__ S, int m, const unsigned
             load_pt<D, DP>(S, k, y);
             const long long b2 = sqdist_ll<D>(y, p);  // >= a2 > eps2 (q is p's nearest)
             const long long dt = dot_from<D>(p, q, y);
-            const double b = sqrt((double)b2);
-            const double sin_a = eps / b, cos_a = sqrt((double)(b2 - eps2)) / b;
-            double cos_t = (double)dt / (a * b);
-            cos_t = fmin(1.0, fmax(-1.0, cos_t));
-            const double sin_t = sqrt(fmax(0.0, 1.0 - cos_t * cos_t));
+            const float b = sqrtf((float)b2);
+            const float sin_a = eps / b, cos_a = sqrtf((float)(b2 - eps2)) / b;
+            float cos_t = (float)dt / (a * b);
+            cos_t = fminf(1.0f, fmaxf(-1.0f, cos_t));
+            const float sin_t = sqrtf(fmaxf(0.0f, 1.0f - cos_t * cos_t));
             // lambda_y < pi  <=>  cos(theta) + cos(alpha) > 0
-            const double v = (cos_t + cos_a > kAngleMargin) ? cos_a * cos_t - sin_a * sin_t : kNoAngle;
-            best = fmin(best, v);
+            const float v = (cos_t + cos_a > kAngleMargin) ? cos_a * cos_t - sin_a * sin_t : kNoAngle;
+            best = fminf(best, v);
             ++nlive;
         }
     }
@@ -721,12 +739,12 @@ __device__ double fm_cos_lambda(const int* __restrict__ S, int m, const unsigned
 // only the target of the argmin.
 template <int D, int DP, bool PRUNE>
 __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, const long long* piv, long long B,
-                          const long long* near, double cl, long long eps2, BestPt* sb, int* sc, int* count,
+                          const long long* near, float cl, long long eps2, BestPt* sb, int* sc, int* count,
                           int* pruned_tri, int* pruned_ang, unsigned long long* ndist) {
     const int lane = lane_id();
     BestPt best{0x7fffffffffffffffll, 0x7fffffff};
     int cnt = 0, ntri = 0, nang = 0;
-    const double sqB = PRUNE ? sqrt((double)B) : 0.0;
+    const float sqB = PRUNE ? sqrtf((float)B) : 0.0f;
     for (int base = 0; base < m; base += kFmBlock) {
         const int k = base + threadIdx.x;
         // the 32 lanes of a warp hold one bitmap word's 32 points; lane 0 has
@@ -742,7 +760,7 @@ __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, cons
                     alive = false;
                     ++ntri;
                 } else if (cl > kNoAngle && A > 0) {
-                    const double cg = (double)dot_from<D>(piv, near, x) / (sqB * sqrt((double)A));
+                    const float cg = (float)dot_from<D>(piv, near, x) / (sqB * sqrtf((float)A));
                     if (cg < cl - kAngleMargin) {
                         alive = false;
                         ++nang;
@@ -775,13 +793,13 @@ __device__ BestPt fm_pass(const int* __restrict__ S, int m, unsigned* live, cons
     return block_best(best, cnt, sb, sc, count);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __restrict__ ins, Flat f, int wave,
+template <int D, bool CAP>
+__global__ void __launch_bounds__(kFmBlock, 3) merge_block_kernel(const Inst* __restrict__ ins, Flat f, int wave,
                                                                unsigned* scratch, int wpb) {
     constexpr int DP = Padded<D>::value;
     __shared__ BestPt sb[kFmWarps];
     __shared__ int sc[kFmWarps];
-    __shared__ double sd[kFmWarps];
+    __shared__ float sd[kFmWarps];
     __shared__ int s_same;
     __shared__ int s_tri, s_ang;  // statistics: points pruned by each test
     __shared__ unsigned long long s_dist;  // statistics: distances evaluated
@@ -797,7 +815,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
         int* parent = I.parent;
         unsigned long long* const stv = I.stats;
         if (threadIdx.x == 0) {
-            const int ra = uf_find(parent, pr.x, I.p.uf_cap), rb = uf_find(parent, pr.y, I.p.uf_cap);
+            const int ra = uf_find<CAP>(parent, pr.x, I.p.uf_cap), rb = uf_find<CAP>(parent, pr.y, I.p.uf_cap);
             if (ra < 0 || rb < 0) set_status(I, kDevTimeout);
             s_same = ra == rb;
             s_tri = 0;
@@ -828,6 +846,13 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
         const int ma = core_start[gi + 1] - core_start[gi];
         const int mb = core_start[gj + 1] - core_start[gj];
         const int wa = (ma + 31) >> 5, wb = (mb + 31) >> 5;
+        if (wa > wpb || wb > wpb) {
+            // the block's bitmaps (sized from an earlier call's largest grid)
+            // are too small: the call is run again with exact sizes
+            if (threadIdx.x == 0) set_status(I, kDevOverflow);
+            __syncthreads();
+            continue;
+        }
         for (int w = threadIdx.x; w < wa; w += kFmBlock)
             live_a[w] = (w < wa - 1 || (ma & 31) == 0) ? 0xffffffffu : ((1u << (ma & 31)) - 1u);
         for (int w = threadIdx.x; w < wb; w += kFmBlock)
@@ -839,12 +864,12 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
 #pragma unroll
         for (int j = 0; j < D; ++j) tgt[j] = ((long long)bj[j] + bj[D + j]) / 2;
         int cnt;
-        BestPt bp = fm_pass<D, DP, false>(A, ma, live_a, nullptr, 0, tgt, 0.0, eps2, sb, sc, &cnt, ptri, pang, pdist);
+        BestPt bp = fm_pass<D, DP, false>(A, ma, live_a, nullptr, 0, tgt, 0.0f, eps2, sb, sc, &cnt, ptri, pang, pdist);
         int px[D];
         load_pt<D, DP>(A, bp.i, px);
 #pragma unroll
         for (int j = 0; j < D; ++j) piv[j] = px[j];
-        BestPt bq = fm_pass<D, DP, false>(B, mb, live_b, nullptr, 0, piv, 0.0, eps2, sb, sc, &cnt, ptri, pang, pdist);
+        BestPt bq = fm_pass<D, DP, false>(B, mb, live_b, nullptr, 0, piv, 0.0f, eps2, sb, sc, &cnt, ptri, pang, pdist);
         bool yes = false;
         int kappa = 1;  // rounds: one per nearest point q found in s_j
         for (int round = 0; round <= ma + mb; ++round) {
@@ -858,7 +883,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
             long long qv[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) qv[j] = qx[j];
-            double cl = fm_cos_lambda<D, DP>(B, mb, live_b, piv, qv, bq.d, eps2, sd, pdist);
+            float cl = fm_cos_lambda<D, DP>(B, mb, live_b, piv, qv, bq.d, eps2, sd, pdist);
             bp = fm_pass<D, DP, true>(A, ma, live_a, piv, bq.d, qv, cl, eps2, sb, sc, &cnt, ptri, pang, pdist);
             if (cnt == 0) break;
             if (bp.d <= eps2) {
@@ -875,7 +900,7 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
             ++kappa;
         }
         if (threadIdx.x == 0) {
-            if (yes && !uf_union(parent, pr.x, pr.y, I.p.uf_cap)) set_status(I, kDevTimeout);
+            if (yes && !uf_union<CAP>(parent, pr.x, pr.y, I.p.uf_cap)) set_status(I, kDevTimeout);
             if (stv) {
                 stat_add(stv, yes ? kStFmYes : kStFmNo, 1);
                 stat_add(stv, kStKappa + min(kappa, (int)kKappaBins) - 1, 1);
@@ -890,11 +915,16 @@ __global__ void __launch_bounds__(kFmBlock) merge_block_kernel(const Inst* __res
 
 
 cudaError_t launch_merge_block(const Inst* ins, Flat hard, int wave, int d, int blocks, unsigned* scratch, int wpb,
-                               cudaStream_t st) {
+                               bool cap, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
     switch (d) {
-#define GD_MB(DD) \
-    case DD: merge_block_kernel<DD><<<blocks, kFmBlock, 0, st>>>(ins, hard, wave, scratch, wpb); break;
+#define GD_MB(DD)                                                                                       \
+    case DD:                                                                                            \
+        if (cap)                                                                                        \
+            merge_block_kernel<DD, true><<<blocks, kFmBlock, 0, st>>>(ins, hard, wave, scratch, wpb);  \
+        else                                                                                            \
+            merge_block_kernel<DD, false><<<blocks, kFmBlock, 0, st>>>(ins, hard, wave, scratch, wpb); \
+        break;
         GD_MB(1) GD_MB(2) GD_MB(3) GD_MB(4) GD_MB(5) GD_MB(6) GD_MB(7) GD_MB(8)
 #undef GD_MB
         default: return cudaErrorInvalidValue;

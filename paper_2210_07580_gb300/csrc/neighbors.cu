@@ -49,6 +49,7 @@ constexpr int kBoxPoints = 32;
 // Box of every grid: one warp per grid; the lanes reduce the points of grids
 // of at most kBoxPoints points, larger grids take their identifier range.
 __global__ void __launch_bounds__(256) point_box_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     FlatCursor cur;
@@ -114,6 +115,7 @@ cudaError_t launch_point_boxes(const Inst* ins, Flat cells, long long total, cud
 
 // L[c] = first dimension in which grid c differs from grid c-1 (0 for c = 0).
 __global__ void level_diff_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -138,20 +140,22 @@ __global__ void level_diff_kernel(const Inst* __restrict__ ins, Flat f, long lon
 // A grid c starts a node on level j iff L[c] <= j.  Flat space: the grids of
 // instances with d - 1 > j.
 __global__ void level_flag_kernel(const Inst* __restrict__ ins, Flat f, long long total, int j) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
         const int k = cur.k;
         const Inst& I = ins[f.idx[k]];
         const long long c = i - cur.lo;
-        const int C = I.small[kSmCells];
-        I.lv_E[(long long)j * (C + 1) + c] = I.lv_L[c] <= j ? 1 : 0;
+        I.lv_E[(long long)j * (I.p.n + 1) + c] = I.lv_L[c] <= j ? 1 : 0;
     }
 }
 
 // After the scans, E_j[c] (exclusive) is the node index on level j of the node
-// starting at grid c, and E_j[C] the node count of level j.
+// starting at grid c, and E_j[C] the node count of level j.  Row j of lv_E
+// starts at j * (n + 1): n bounds the grid count C.
 __global__ void level_write_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -159,18 +163,19 @@ __global__ void level_write_kernel(const Inst* __restrict__ ins, Flat f, long lo
         const Inst& I = ins[f.idx[k]];
         const long long c = i - cur.lo;
         const int d = I.p.d, C = I.small[kSmCells];
+        const long long R = (long long)I.p.n + 1;  // row stride of lv_E
         const int* E = I.lv_E;
         const int l = I.lv_L[c];
         for (int j = l; j < d; ++j) {
-            const long long u = (j < d - 1) ? E[(long long)j * (C + 1) + c] : c;
+            const long long u = (j < d - 1) ? E[j * R + c] : c;
             I.lv_key[j][u] = I.cell_coord[c * d + j];
-            if (j < d - 1) I.lv_cb[j][u] = (j + 1 < d - 1) ? E[(long long)(j + 1) * (C + 1) + c] : (int)c;
+            if (j < d - 1) I.lv_cb[j][u] = (j + 1 < d - 1) ? E[(j + 1) * R + c] : (int)c;
         }
         if (c == 0) {
             for (int j = 0; j < d; ++j) {
-                const int nj = (j < d - 1) ? E[(long long)j * (C + 1) + C] : C;
+                const int nj = (j < d - 1) ? E[j * R + C] : C;
                 I.small[kSmLevelCount + j] = nj;
-                if (j < d - 1) I.lv_cb[j][nj] = (j + 1 < d - 1) ? E[(long long)(j + 1) * (C + 1) + C] : C;
+                if (j < d - 1) I.lv_cb[j][nj] = (j + 1 < d - 1) ? E[(j + 1) * R + C] : C;
             }
         }
     }
@@ -294,15 +299,30 @@ __device__ __forceinline__ void pool_flush(const WalkPool& pool, const int* buf,
 }
 
 // The backward entry c in the list of grid u > c (fill mode and the pool
-// scatter): after the forward part, at the next free slot.
+// scatter): after the forward part, at the next free slot.  Writes stay
+// inside the list buffer whatever the counts say.
 __device__ __forceinline__ void put_backward(const Inst& I, int u, int c) {
-    const int at = I.nbr_start[u] + I.nbr_fwd[u] + atomicAdd(I.nbr_bwd + u, 1);
-    I.nbr[at] = c;
+    const long long at = (long long)I.nbr_start[u] + I.nbr_fwd[u] + atomicAdd(I.nbr_bwd + u, 1);
+    if (at < I.nbr_cap) I.nbr[at] = c;
+}
+
+// Whether the neighbour lists of an instance were given up (see nbr_check).
+__device__ __forceinline__ bool lists_dropped(const Inst& I) {
+    return (*reinterpret_cast<const volatile unsigned*>(I.small + kSmStatus) & kDevOverflow) != 0;
+}
+
+// Whether the pool held the whole walk (else the lists are filled by a
+// second walk).
+__device__ __forceinline__ bool pool_fits(const WalkPool& pool) {
+    if (!pool.data) return false;
+    const unsigned long long t = *pool.ctr;
+    return (long long)(t & ((1ull << kPoolBits) - 1)) <= pool.cap && (long long)(t >> kPoolBits) <= pool.seg_cap;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * kWalkWarps)
     walk_kernel(const Inst* __restrict__ ins, Flat f, long long total, WalkPool pool) {
+    total = flat_total(f);
     constexpr bool FILL = MODE == kWalkFill, POOL = MODE == kWalkPool;
     __shared__ WalkShared sh;
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -312,11 +332,14 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     signed char* const slvl = sh.lvl[w];
     const long long warps = (long long)gridDim.x * kWalkWarps;
     const unsigned lt = lanemask_lt();
+    // the filling walk runs only when the pool could not hold the walk
+    if (FILL && pool_fits(pool)) return;
     FlatCursor cur;
     for (long long q = (long long)blockIdx.x * kWalkWarps + w; q < total; q += warps) {
         cur.seek(f, q);
         const int kin = f.idx[cur.k];
         const Inst& I = ins[kin];
+        if (FILL && lists_dropped(I)) continue;
         const long long c = q - cur.lo;
         const int d = I.p.d;
         const long long r = I.p.r, s = I.p.s, eps2 = I.p.eps2;
@@ -436,7 +459,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     else
                         atomicAdd(I.nbr_bwd + u, 1);
                 }
-                if (FILL && ok) out[found + __popc(m & lt)] = u;
+                if (FILL && ok) {
+                    const int at = found + __popc(m & lt);
+                    if (I.nbr_start[c] + (long long)at < I.nbr_cap) out[at] = u;
+                }
                 found += __popc(m);
                 if (POOL) {
                     if (ok) buf[nbuf + __popc(m & lt)] = u;
@@ -498,25 +524,60 @@ cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, 
 // The pool's segments into the scanned lists, one warp per segment: each
 // run of forward neighbours of query c goes to its place in c's list, and
 // every neighbour u > c receives the backward entry c.
-__global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restrict__ ins, WalkPool pool,
-                                                           long long nseg) {
+// The segment count is the pool counter's (read on the device); nothing is
+// done when the pool overflowed (the filling walk runs instead).
+__global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restrict__ ins, WalkPool pool) {
+    if (!pool_fits(pool)) return;
+    const long long nseg = (long long)(*pool.ctr >> kPoolBits);
     const int lane = lane_id();
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long sgi = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); sgi < nseg;
          sgi += warps) {
         const PoolSeg sg = pool.seg[sgi];
         const Inst& I = ins[sg.inst];
+        if (lists_dropped(I)) continue;
         if (lane < sg.len) {
             const int u = pool.data[sg.pos + lane];
-            I.nbr[(long long)I.nbr_start[sg.c] + sg.off + lane] = u;
+            const long long at = (long long)I.nbr_start[sg.c] + sg.off + lane;
+            if (at < I.nbr_cap) I.nbr[at] = u;
             if (u != sg.c) put_backward(I, u, sg.c);
         }
     }
 }
 
+// After the list scan: an instance whose lists need more entries than its
+// buffer holds (a capacity taken from an earlier call) gives them up -- every
+// list empty, forward parts included, so that no later kernel reads an
+// entry that was not written -- and records kDevOverflow: the call is then
+// run again with exact sizes.
+__global__ void nbr_check_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
+    FlatCursor cur;
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        if ((long long)(unsigned)I.small[kSmNnbr] <= I.nbr_cap) continue;
+        const long long c = i - cur.lo;
+        I.nbr_start[c] = 0;
+        I.nbr_fwd[c] = 0;
+        if (c == 0) {
+            I.nbr_start[I.small[kSmCells]] = 0;
+            set_status(I, kDevOverflow);
+        }
+    }
+}
+
+cudaError_t launch_nbr_check(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    nbr_check_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 // List lengths before the scan: forward + backward entries of each grid; the
 // backward counts restart at zero as the cursors that place the entries.
 __global__ void nbr_total_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
     FlatCursor cur;
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
@@ -534,11 +595,11 @@ cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, long long nseg, cudaStream_t st) {
-    if (nseg <= 0) return cudaSuccess;
-    long long b = (nseg * 32 + 255) / 256;
+cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, cudaStream_t st) {
+    if (!pool.data || pool.seg_cap <= 0) return cudaSuccess;
+    long long b = (pool.seg_cap * 32 + 255) / 256;
     if (b > kPersistBlocks) b = kPersistBlocks;
-    pool_scatter_kernel<<<(int)b, 256, 0, st>>>(ins, pool, nseg);
+    pool_scatter_kernel<<<(int)b, 256, 0, st>>>(ins, pool);
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

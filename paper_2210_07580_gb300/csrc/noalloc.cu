@@ -61,6 +61,7 @@ struct StaticMem : MemProvider {
         *out = g_host[slot];
         return GD_OK;
     }
+    void* current(int slot) override { return slot_ptr[slot]; }
 };
 
 // The FastMerging kernel's bitmaps come from the static array too: few blocks.
@@ -102,7 +103,12 @@ extern "C" gd_status gd_dbscan_noalloc(const int32_t* X, int64_t n, int d, int64
     // it, so nothing left in the array by an earlier call leaks into this one.
     const gd_instance g{X, n, d, eps2, minpts, labels, is_core};
     const cudaStream_t st = (cudaStream_t)stream;
-    const gd_status s = run_batch(mem, 1, &g, st, nullptr, nullptr, &noalloc_tuning());
+    // Sizes are read back while queueing (there is no plan of earlier calls),
+    // so the run never has to be repeated; finish_batch waits for it and
+    // reads its status.
+    gd_status s = run_batch(mem, 1, &g, st, nullptr, nullptr, &noalloc_tuning(), nullptr, nullptr, StageSet(), false);
+    if (s == GD_OK) s = finish_batch(mem, 1, &g, st, nullptr);
+    if (s == kGdRerun) s = GD_ECUDA;  // cannot happen with exact sizes
     // A failed run may return with kernels still queued on the stream; they
     // use the shared array, so they must finish before the next caller gets
     // the lock.

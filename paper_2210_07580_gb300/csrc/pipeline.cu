@@ -2,15 +2,26 @@
 //
 // The K instances go through every stage together: each launch covers a flat
 // space over all of them (or over the ones sharing a dimension or a key
-// width, for kernels specialised on those).  The host synchronises with the
-// stream four times per batch, whatever K is:
-//   1. after the bounds      -> per-instance key layout, workspace sizes;
-//   2. after the compaction  -> grid counts C, largest grid;
-//   3. after the walk count  -> neighbour-list lengths (buffer sizes);
-//   4. at the end            -> status words.
-// Everything else -- pair counts, non-full point counts, pairs handed to
-// FastMerging -- stays on the device: the kernels that consume those spaces
-// read their offsets from tables the device fills (count_flat).
+// width, for kernels specialised on those).  Sizes that only the data
+// decides stay on the device: the grid count C (flat spaces over grids and
+// the scans over per-grid arrays read it there), the pair counts, the
+// non-full point counts and the FastMerging pairs.  The host must know
+// before it launches
+//   - the sort's launch plan (key class, digit passes), which depends on the
+//     coordinate bounds, and
+//   - the size of the neighbour lists and the largest grid (buffers).
+// A call whose instance shapes (n, d, eps2) the context has seen takes both
+// from that earlier call (plus margins) and is queued at once, with nothing
+// read back: the device computes the real key layout and checks that it
+// fits the plan and that the lists fit their buffers; if not, finish_batch
+// asks for the call to be queued again with exact sizes.  Any other call
+// reads the bounds back after the first phase and the list sizes after the
+// third.  The device-side fit checks keep every kernel inside its buffers
+// even when the data did not fit.
+//
+// Launch phases: 1. bounds (+ key layout); 2. keys, sort, compaction;
+// 3. point boxes, grid tree, neighbour walk, list sizes; 4. lists, core
+// points, merging, labels.
 #include <climits>
 #include <cstring>
 #include <utility>
@@ -53,7 +64,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Host view of one instance.
 struct HI {
     Inst dev;            // the record uploaded to the device
-    long long C, maxcell, nnbr;
+    long long C, maxcell, nnbr;  // read back (synchronous path) or bounds (queued path)
     int q_tiles, c_tiles;
     size_t arena_off, arena_bytes;
 };
@@ -75,11 +86,6 @@ struct Builder {
         }
         return at;
     }
-    template <typename T> T* put(const T* data, size_t count) {
-        const size_t at = take(sizeof(T) * count);
-        if (!overflow && count) memcpy(host + at, data, sizeof(T) * count);
-        return reinterpret_cast<T*>(dev + at);
-    }
     template <typename T> T* hostp(T* devp) { return reinterpret_cast<T*>(host + ((char*)devp - dev)); }
 };
 
@@ -96,8 +102,10 @@ struct HostBump {
     }
 };
 
-size_t desc_bound(int K) { return (size_t)4096 * (size_t)(K + 16); }
+// Descriptor tables of a whole call (all phases).
+size_t desc_bound(int K) { return (size_t)16384 * (size_t)(K + 16); }
 size_t host_work_bound(int K) { return (size_t)(sizeof(HI) + 256) * (size_t)K + (size_t)64 * K * 8 + 65536; }
+constexpr int kMaxFlatSpecs = 4 * kMaxD * kSizeBuckets + 16;
 
 // Per-instance workspace, laid out from `base` (or only sized when base is
 // null).  Arrays indexed by grid are sized for n grids, the upper bound.
@@ -144,12 +152,27 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     return align256(off) + 256;
 }
 
+// The sort plan of a key layout (host side; the device computes the layout
+// itself on the queued path and checks it against this plan).
+void set_plan(HI& h, int key_words, int key_class, int key_bits) {
+    Params& p = h.dev.p;
+    p.key_bits = key_bits;
+    p.key_words = key_words;
+    p.key_class = key_class;
+    const int ib = p.n > 1 ? bit_length((unsigned long long)(p.n - 1)) : 1;
+    p.pack_bits = key_class == 0 ? ib : 0;
+    const SortPlan sp = sort_plan(p.n, key_words, key_bits);
+    h.dev.passes = sp.passes;
+    h.dev.digit_bits = sp.bits;
+    h.dev.tiles = sp.tiles;
+}
 
-#define RUN_TRY_P(x)                  \
+#define RUN_TRY(x)                    \
     do {                              \
-        gd_status sp_ = (x);          \
-        if (sp_ != GD_OK) return sp_; \
+        gd_status s_ = (x);           \
+        if (s_ != GD_OK) return s_;   \
     } while (0)
+#define RUN_CUDA(x, what) RUN_TRY(cuda((x), what))
 
 struct Run {
     MemProvider& mem;
@@ -161,6 +184,8 @@ struct Run {
     const Tuning* tune;
     PhaseGraphs* graphs;
     cudaEvent_t* sort_ev;  // kSortEventPairs pairs, or null
+    StageSet stage;
+    bool allow_async;
     long long total_points = 0;
     int knob(int kn, int d, long long n) const { return tune ? tune->value(kn, d, n) : knob_default(kn, d); }
 
@@ -170,7 +195,7 @@ struct Run {
     // busy while the host captures and updates the graph of the rest.  A
     // capture that fails is discarded and the launches are issued directly.
     template <typename H, typename F> gd_status phase(int id, H&& head, F&& body) {
-        RUN_TRY_P(head());
+        RUN_TRY(head());
         // small batches re-capture more than they save in launches
         if (!graphs || !graphs->enabled || total_points < kGraphMinPoints) return body();
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -217,11 +242,14 @@ struct Run {
     int* hsmall = nullptr;   // host mirror of the small blocks [K][kSmallInts]
     int* dsmall = nullptr;   // device small blocks
     Builder b{};
-    Inst* dins = nullptr;    // device Inst array (in the descriptor buffer)
+    Inst* dins = nullptr;    // device Inst array (at the start of the descriptor buffer)
     int* scan_tmp = nullptr;
     size_t scan_tmp_ints = 0;
     HostBump hw{};
     int* all_idx = nullptr;  // 0..K-1
+    size_t uploaded = 0;     // descriptor bytes already uploaded
+    FlatSpec* spec_dev = nullptr;
+    int nspecs = 0, specs_done = 0;
 
     gd_status fail(gd_status s, const char* msg, int k = -1) {
         if (info) {
@@ -243,7 +271,7 @@ struct Run {
         void* h = nullptr;
         void* d = nullptr;
         const size_t cap = desc_bound(K);
-        gd_status s = mem.host(kHostDesc, cap, &h);
+        gd_status s = mem.host(stage.set ? kHostDesc1 : kHostDesc0, cap, &h);
         if (s != GD_OK) return fail(s, "descriptor staging");
         s = mem.device(kMemDesc, cap, &d);
         if (s != GD_OK) return fail(s, "descriptor buffer");
@@ -252,17 +280,31 @@ struct Run {
         b.off = 0;
         b.dev = (char*)d;
         b.overflow = false;
-        // the Inst array always comes first
+        // the Inst array always comes first, then the table of device-filled
+        // flat spaces
         dins = reinterpret_cast<Inst*>(b.dev + b.take(sizeof(Inst) * K));
+        spec_dev = reinterpret_cast<FlatSpec*>(b.dev + b.take(sizeof(FlatSpec) * kMaxFlatSpecs));
+        nspecs = specs_done = 0;
+        uploaded = 0;
         seg_tabs = 0;
         all_idx = nullptr;
         return GD_OK;
     }
+    // Uploads the instance records, the table of device-filled spaces and
+    // the tables built since the last upload (earlier ones are on the
+    // device already, some with offsets the device has filled since).
     gd_status upload_desc() {
         if (b.overflow) return fail(GD_ENOMEM, "descriptor tables exceed their staging buffer");
         Inst* h = b.hostp(dins);
         for (int k = 0; k < K; ++k) h[k] = hi[k].dev;
-        return cuda(cudaMemcpyAsync(b.dev, b.host, b.off, cudaMemcpyHostToDevice, st), "upload descriptors");
+        const size_t head = (size_t)((char*)(spec_dev + kMaxFlatSpecs) - b.dev);
+        RUN_CUDA(cudaMemcpyAsync(b.dev, b.host, head, cudaMemcpyHostToDevice, st), "upload descriptors");
+        const size_t from = uploaded > head ? uploaded : head;
+        if (b.off > from)
+            RUN_CUDA(cudaMemcpyAsync(b.dev + from, b.host + from, b.off - from, cudaMemcpyHostToDevice, st),
+                     "upload descriptors");
+        uploaded = b.off;
+        return GD_OK;
     }
     const int* idx_all() {
         if (!all_idx) {
@@ -306,15 +348,39 @@ struct Run {
         *off_dev = reinterpret_cast<long long*>(b.dev + at_off);
         return Flat{*off_dev, reinterpret_cast<const int*>(b.dev + at_idx), m};
     }
+    // Flat space over the grids of `m` members, filled on the device once C
+    // is known (count_pending); *upper receives a bound of its size (points).
+    Flat gflat(const int* members, int m, long long* upper) {
+        long long* off = nullptr;
+        const Flat f = dflat(members, m, &off);
+        long long u = 0;
+        for (int t = 0; t < m; ++t) u += in[members[t]].n;
+        *upper = u;
+        if (nspecs >= kMaxFlatSpecs) {
+            b.overflow = true;
+        } else if (!b.overflow) {
+            b.hostp(spec_dev)[nspecs] = FlatSpec{f.idx, off, m, kSmCells};
+        }
+        ++nspecs;
+        return f;
+    }
+    gd_status count_pending() {
+        if (nspecs > specs_done)
+            RUN_CUDA(count_flats(dins, spec_dev + specs_done, nspecs - specs_done, st), "grid spaces");
+        specs_done = nspecs;
+        return GD_OK;
+    }
     // Segmented scans over one array per member instance.
     // (longest segment of each table built since the descriptors were begun,
     // so that scan() can pick the one-launch form for short segments)
-    const ScanSeg* seg_tab[64] = {};
-    long long seg_longest[64] = {};
+    const ScanSeg* seg_tab[128] = {};
+    long long seg_longest[128] = {};
     int seg_tabs = 0;
     // tot_slot >= 0: each segment's total also goes to that slot of its
-    // instance's small block (read back with it).
-    template <typename F> ScanSeg* segs(const int* members, int m, F arr, long long* tiles, int tot_slot = -1) {
+    // instance's small block.  len_slot >= 0: the segment's length is that
+    // slot of the small block (read on the device); arr gives its bound.
+    template <typename F>
+    ScanSeg* segs(const int* members, int m, F arr, long long* tiles, int tot_slot = -1, int len_slot = -1) {
         const size_t at = b.take(sizeof(ScanSeg) * (m > 0 ? m : 1));
         long long blk = 0, longest = 0;
         ScanSeg* h = reinterpret_cast<ScanSeg*>(b.host + at);
@@ -323,13 +389,14 @@ struct Run {
             long long len = 0;
             arr(members[t], &a, &len);
             int* tot = tot_slot >= 0 ? dsmall + (size_t)members[t] * kSmallInts + tot_slot : nullptr;
-            if (!b.overflow) h[t] = ScanSeg{a, a, len, blk, tot};
+            const int* ld = len_slot >= 0 ? dsmall + (size_t)members[t] * kSmallInts + len_slot : nullptr;
+            if (!b.overflow) h[t] = ScanSeg{a, a, len, blk, tot, ld};
             blk += (len + kScanTile - 1) / kScanTile;
             if (len > longest) longest = len;
         }
         *tiles = blk;
         ScanSeg* dev = reinterpret_cast<ScanSeg*>(b.dev + at);
-        if (seg_tabs < 64) {
+        if (seg_tabs < 128) {
             seg_tab[seg_tabs] = dev;
             seg_longest[seg_tabs++] = longest;
         }
@@ -353,17 +420,12 @@ struct Run {
     gd_status go();
 };
 
-#define RUN_TRY(x)                    \
-    do {                              \
-        gd_status s_ = (x);           \
-        if (s_ != GD_OK) return s_;   \
-    } while (0)
-#define RUN_CUDA(x, what) RUN_TRY(cuda((x), what))
-
 gd_status Run::go() {
     // ---------------------------------------------------------- set-up
+    // this call's host staging set: its previous user's uploads must be done
+    if (stage.done) RUN_CUDA(cudaEventSynchronize(stage.done), "staging");
     void* hwp = nullptr;
-    RUN_TRY(mem.host(kHostSmall, sizeof(int) * kSmallInts * K + host_work_bound(K), &hwp));
+    RUN_TRY(mem.host(stage.set ? kHostSmall1 : kHostSmall0, sizeof(int) * kSmallInts * K + host_work_bound(K), &hwp));
     hsmall = (int*)hwp;
     hw = HostBump{(unsigned char*)hwp + sizeof(int) * kSmallInts * K, host_work_bound(K), 0};
     hi = hw.take<HI>(K);
@@ -381,6 +443,8 @@ gd_status Run::go() {
         RUN_CUDA(cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * kStatCount * K, st), "statistics");
     }
 
+    PlanCache* pc = mem.plans();
+    bool queued = allow_async && pc != nullptr;  // every shape planned by an earlier call
     long long total_pts = 0;
     int dmax = 1;
     bool any_ldf = false, all_ldf = true;
@@ -418,7 +482,30 @@ gd_status Run::go() {
         if (g.d > dmax) dmax = g.d;
         if (p.ldf) any_ldf = true;
         else all_ldf = false;
+        if (queued) {
+            const ShapePlan* sp = pc->find(g.n, g.d, p.eps2);
+            if (!sp || sp->key_bits <= 0) {
+                queued = false;
+            } else {
+                set_plan(h, sp->key_words, sp->key_class, sp->key_bits);
+                // capacities: what the shape needed last time, plus a margin
+                h.nnbr = sp->nnbr + sp->nnbr / 4 + 4096;
+                h.maxcell = sp->maxcell + sp->maxcell / 4 + 32;
+            }
+        }
     }
+    if (info) {
+        info->queued_async = queued;
+        info->sizes[12] = queued ? 1 : 0;
+    }
+    auto note_plan = [&]() {
+        for (int k = 0; k < K; ++k) {
+            sm(k)[kSmKeyClass] = hi[k].dev.p.key_class;
+            sm(k)[kSmKeyBits] = hi[k].dev.p.key_bits;
+            sm(k)[kSmKeyWords] = hi[k].dev.p.key_words;
+        }
+    };
+    if (queued) note_plan();
     // scan scratch: enough for any segmented scan of the batch
     scan_tmp_ints = (size_t)K + 64;
     for (int k = 0; k < K; ++k) scan_tmp_ints += (size_t)(in[k].n / kScanTile + 2);
@@ -428,10 +515,14 @@ gd_status Run::go() {
     total_points = total_pts;
     for (int k = 0; k < K; ++k) members[k] = k;
     auto n_of = [&](int k) { return (long long)in[k].n; };
-    auto C_of = [&](int k) { return hi[k].C; };
     long long tot;
+    long long n_largest = 1;
+    for (int k = 0; k < K; ++k) n_largest = in[k].n > n_largest ? in[k].n : n_largest;
+    const int fm_blocks = knob(GD_KNOB_FM_BLOCKS, dmax, n_largest);
+    const bool uf_capped = info && info->uf_cap > 0;  // a lowered union-find cap (tests)
+    const int walk_blocks = knob(GD_KNOB_WALK_BLOCKS, dmax, n_largest);
 
-    // --------------------------------------------- phase 1: bounds (sync 1)
+    // ------------------------------------------------ phase 1: bounds
     RUN_TRY(begin_desc());
     Flat pts_d[kMaxD];
     long long tot_d[kMaxD] = {};
@@ -441,52 +532,60 @@ gd_status Run::go() {
             if (in[k].d == d) members2[m++] = k;
         pts_d[d - 1] = flat(members2, m, n_of, &tot_d[d - 1]);
     }
-    RUN_TRY(upload_desc());
-    // (one or a few launches: no graph)
-    mark(0);
-    RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
-    for (int d = 1; d <= kMaxD; ++d) RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
-    mark(kStages + 1);
-    RUN_TRY(readback());
+    auto launch1 = [&]() -> gd_status {
+        mark(0);
+        RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "init");
+        for (int d = 1; d <= kMaxD; ++d)
+            RUN_CUDA(launch_bounds(dins, pts_d[d - 1], tot_d[d - 1], d, st), "bounds");
+        if (queued) RUN_CUDA(launch_layout(dins, K, st), "key layout");
+        mark(kStages + 1);
+        return GD_OK;
+    };
+    if (!queued) {
+        RUN_TRY(upload_desc());
+        RUN_TRY(launch1());
+        RUN_TRY(readback());
+        // the key layout and sort plan of each instance from its bounds
+        for (int k = 0; k < K; ++k) {
+            HI& h = hi[k];
+            Params& p = h.dev.p;
+            const int* s = sm(k);
+            unsigned long long rmax = 0;
+            int total_bits = 0;
+            for (int j = 0; j < p.d; ++j) {
+                const long long lo = s[kSmMnmx + j], up = s[kSmMnmx + kMaxD + j];
+                const unsigned long long rj = (unsigned long long)(up - lo);
+                if (rj > rmax) rmax = rj;
+                p.mn[j] = (int)lo;
+                p.bits[j] = bit_length(rj / (unsigned long long)p.s);
+                total_bits += p.bits[j];
+            }
+            if ((unsigned __int128)p.d * rmax * rmax >= ((unsigned __int128)1 << 62))
+                return fail(GD_ERANGE, "coordinate range too large: d * R^2 >= 2^62", k);
+            if (total_bits > 128) return fail(GD_ERANGE, "packed grid key needs more than 128 bits", k);
+            for (int j = p.d - 1, sh = 0; j >= 0; --j) {
+                p.shift[j] = sh;
+                sh += p.bits[j];
+            }
+            const int kw = total_bits <= 64 ? 1 : 2;
+            const int ib = p.n > 1 ? bit_length((unsigned long long)(p.n - 1)) : 1;
+            set_plan(h, kw, kw == 2 ? 2 : (total_bits + ib <= 64 ? 0 : 1), total_bits);
+        }
+        // the plans into the small blocks (read back with the results)
+        note_plan();
+        RUN_CUDA(cudaMemcpyAsync(dsmall, hsmall, sizeof(int) * kSmallInts * K, cudaMemcpyHostToDevice, st), "plans");
+    }
 
-    // ------------------------- phase 2: keys, sort, compaction (sync 2)
+    // workspaces of the plan
     int max_buckets = 1;
     size_t arena = 0;
     for (int k = 0; k < K; ++k) {
         HI& h = hi[k];
         Params& p = h.dev.p;
-        const int* s = sm(k);
-        unsigned long long rmax = 0;
-        int total_bits = 0;
-        for (int j = 0; j < p.d; ++j) {
-            const long long lo = s[kSmMnmx + j], up = s[kSmMnmx + kMaxD + j];
-            const unsigned long long rj = (unsigned long long)(up - lo);
-            if (rj > rmax) rmax = rj;
-            p.mn[j] = (int)lo;
-            p.bits[j] = bit_length(rj / (unsigned long long)p.s);
-            total_bits += p.bits[j];
-        }
-        if ((unsigned __int128)p.d * rmax * rmax >= ((unsigned __int128)1 << 62))
-            return fail(GD_ERANGE, "coordinate range too large: d * R^2 >= 2^62", k);
-        if (total_bits > 128) return fail(GD_ERANGE, "packed grid key needs more than 128 bits", k);
-        for (int j = p.d - 1, sh = 0; j >= 0; --j) {
-            p.shift[j] = sh;
-            sh += p.bits[j];
-        }
-        p.key_bits = total_bits;
-        p.key_words = total_bits <= 64 ? 1 : 2;
-        {
-            const int ib = p.n > 1 ? bit_length((unsigned long long)(p.n - 1)) : 1;
-            p.key_class = p.key_words == 2 ? 2 : (total_bits + ib <= 64 ? 0 : 1);
-            p.pack_bits = p.key_class == 0 ? ib : 0;
-        }
-        const SortPlan sp = sort_plan(p.n, p.key_words, p.key_bits);
-        h.dev.passes = sp.passes;
-        h.dev.digit_bits = sp.bits;
-        h.dev.tiles = sp.tiles;
         h.q_tiles = (p.n + kQuantTile - 1) / kQuantTile;
         h.c_tiles = (p.n + kCompactTile - 1) / kCompactTile;
-        if (sp.buckets > max_buckets) max_buckets = sp.buckets;
+        const int R = 1 << h.dev.digit_bits;
+        if (R > max_buckets) max_buckets = R;
         h.arena_off = arena;
         h.arena_bytes = carve(h.dev, nullptr, p.n, p.d, p.key_words, p.key_bits);
         arena += h.arena_bytes;
@@ -498,7 +597,7 @@ gd_status Run::go() {
         carve(h.dev, (char*)ap + h.arena_off, h.dev.p.n, h.dev.p.d, h.dev.p.key_words, h.dev.p.key_bits);
     }
 
-    RUN_TRY(begin_desc());
+    // ------------------------- phase 2: keys, sort, compaction
     const Flat pts1 = flat(members, K, n_of, &tot);
     // one group per key class (packed 64-bit, 64-bit + values, 128-bit + values)
     Flat qflat[3], cflat[3];
@@ -531,55 +630,40 @@ gd_status Run::go() {
         },
         &cseg_tiles);
     const int* idx = idx_all();
-    RUN_TRY(upload_desc());
     RUN_CUDA(prepare_sort(), "sort set-up");
-
-    RUN_TRY(phase(1, [&]() -> gd_status {
-    mark(1);
-    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_quantise(dins, qflat[w], qtot[w], w, st), "quantise");
-    return GD_OK;
-    }, [&]() -> gd_status {
-    mark(2);
-    int pairs = 0;
-    for (int w = 0; w < 3; ++w)
-        for (int ps = 0; ps < gpasses[w]; ++ps) {
-            cudaEvent_t a = nullptr, b2 = nullptr;
-            if (sort_ev && otot[w][ps] > 0 && pairs < kSortEventPairs) {
-                a = sort_ev[2 * pairs];
-                b2 = sort_ev[2 * pairs + 1];
-                ++pairs;
+    auto launch2 = [&]() -> gd_status {
+        return phase(1, [&]() -> gd_status {
+        mark(1);
+        for (int w = 0; w < 3; ++w) RUN_CUDA(launch_quantise(dins, qflat[w], qtot[w], w, st), "quantise");
+        return GD_OK;
+        }, [&]() -> gd_status {
+        mark(2);
+        int pairs = 0;
+        for (int w = 0; w < 3; ++w)
+            for (int ps = 0; ps < gpasses[w]; ++ps) {
+                cudaEvent_t a = nullptr, b2 = nullptr;
+                if (sort_ev && otot[w][ps] > 0 && pairs < kSortEventPairs) {
+                    a = sort_ev[2 * pairs];
+                    b2 = sort_ev[2 * pairs + 1];
+                    ++pairs;
+                }
+                RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st, a, b2),
+                         "sort pass");
             }
-            RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st, a, b2), "sort pass");
-        }
-    if (info) info->sort_event_pairs = pairs;
-    mark(3);
-    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w, st), "compact count");
-    RUN_TRY(scan(cseg, K, cseg_tiles));
-    for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w, st), "compact write");
-    RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
-    mark(kStages + 2);
-    return GD_OK;
-    }));
-    RUN_TRY(readback());
+        if (info) info->sort_event_pairs = pairs;
+        mark(3);
+        for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_count(dins, cflat[w], ctot[w], w, st), "compact count");
+        RUN_TRY(scan(cseg, K, cseg_tiles));
+        for (int w = 0; w < 3; ++w) RUN_CUDA(launch_compact_write(dins, cflat[w], ctot[w], w, st), "compact write");
+        RUN_CUDA(launch_cell_max(dins, pts1, total_pts, st), "largest grid");
+        mark(kStages + 2);
+        return GD_OK;
+        });
+    };
 
-    // ------------------------ phase 3: levels, walk count (sync 3)
-    long long max_cell = 1;
-    for (int k = 0; k < K; ++k) {
-        hi[k].C = sm(k)[kSmCells];
-        hi[k].maxcell = sm(k)[kSmMaxCell];
-        if (hi[k].maxcell > max_cell) max_cell = hi[k].maxcell;
-    }
-    const int wpb = (int)((max_cell + 31) / 32 + 1);
-    long long n_largest = 1;
-    for (int k = 0; k < K; ++k) n_largest = in[k].n > n_largest ? in[k].n : n_largest;
-    const int fm_blocks = knob(GD_KNOB_FM_BLOCKS, dmax, n_largest);
-    const int walk_blocks = knob(GD_KNOB_WALK_BLOCKS, dmax, n_largest);
-    void* scr = nullptr;
-    RUN_TRY(mem.device(kMemScratch, (size_t)fm_blocks * 2 * wpb * 4, &scr));
-
-    RUN_TRY(begin_desc());
-    const Flat cells2 = flat(members, K, C_of, &tot);
-    const long long total_cells = tot;
+    // --------------------------- phase 3: levels, walk, list sizes
+    long long total_cells = 0;  // bound of the grids (points)
+    const Flat cells = gflat(members, K, &total_cells);
     Flat lflat[kMaxD];
     long long ltot[kMaxD] = {};
     const ScanSeg* lseg[kMaxD] = {};
@@ -590,33 +674,32 @@ gd_status Run::go() {
         for (int k = 0; k < K; ++k)
             if (hi[k].dev.p.d - 1 > j) members2[m++] = k;
         lm[j] = m;
-        lflat[j] = flat(members2, m, C_of, &ltot[j]);
+        lflat[j] = gflat(members2, m, &ltot[j]);
         lseg[j] = segs(
             members2, m,
             [&](int k, int** a, long long* len) {
-                *a = hi[k].dev.lv_E + (size_t)j * (hi[k].C + 1);
-                *len = hi[k].C;
+                *a = hi[k].dev.lv_E + (size_t)j * ((size_t)in[k].n + 1);
+                *len = in[k].n;
             },
-            &lseg_tiles[j]);
+            &lseg_tiles[j], -1, kSmCells);
     }
     long long nseg_tiles = 0;
     const ScanSeg* nseg = segs(
         members, K,
         [&](int k, int** a, long long* len) {
             *a = hi[k].dev.nbr_start;
-            *len = hi[k].C;
+            *len = in[k].n;
         },
-        &nseg_tiles, kSmNnbr);
-    idx = idx_all();
-    RUN_TRY(upload_desc());
+        &nseg_tiles, kSmNnbr, kSmCells);
 
-    // Single pass when a pool can be had: sized from the most neighbour
-    // entries per grid this memory has seen (a first run guesses).
+    // Single-pass walk when a pool can be had: sized from the most pool
+    // entries and runs per point this memory has seen (a first call guesses).
     WalkPool pool{};
     if (mem.pool_enabled()) {
-        const double ratio = mem.nbr_per_grid() > 0 ? mem.nbr_per_grid() * 1.25 : 48.0;
-        const long long cap = (long long)(ratio * (double)total_cells) + 4096;
-        const long long seg_cap = total_cells + cap / 32 + 64;
+        const double per = mem.pool_per_point() > 0 ? mem.pool_per_point() * 1.25 : 4.0;
+        const double runs = mem.runs_per_point() > 0 ? mem.runs_per_point() * 1.25 : 0.25;
+        const long long cap = (long long)(per * (double)total_pts) + 4096;
+        const long long seg_cap = (long long)(runs * (double)total_pts) + cap / 32 + 64;
         void *pd = nullptr, *ps = nullptr;
         if (cap < (1ll << kPoolBits) && seg_cap < (1ll << (64 - kPoolBits)) &&
             mem.device(kMemPool, (size_t)cap * 4, &pd) == GD_OK &&
@@ -625,63 +708,66 @@ gd_status Run::go() {
         }
     }
     const bool pooled = pool.data != nullptr;
-    RUN_TRY(phase(2, [&]() -> gd_status {
-    mark(4);
-    RUN_CUDA(launch_point_boxes(dins, cells2, total_cells, st), "point boxes");
-    RUN_CUDA(launch_level_diff(dins, cells2, total_cells, st), "levels");
-    return GD_OK;
-    }, [&]() -> gd_status {
-    for (int j = 0; j + 1 < dmax; ++j) {
-        RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
-        RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
-    }
-    RUN_CUDA(launch_level_write(dins, cells2, total_cells, st), "level write");
-    mark(5);
-    RUN_CUDA(launch_walk(dins, cells2, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
-             "walk");
-    RUN_CUDA(launch_nbr_total(dins, cells2, total_cells, st), "list lengths");
-    RUN_TRY(scan(nseg, K, nseg_tiles));
-    mark(kStages + 3);
-    return GD_OK;
-    }));
-    RUN_TRY(readback());
-    long long pool_segs = -1;  // -1: fill by a second walk
-    if (pooled) {
-        unsigned long long ctr;
-        memcpy(&ctr, sm(0) + kSmPool, sizeof(ctr));
-        const long long used = (long long)(ctr & ((1ull << kPoolBits) - 1)), segs = (long long)(ctr >> kPoolBits);
-        if (used <= pool.cap && segs <= pool.seg_cap) pool_segs = segs;
-    }
+    // whether the lists need the filling walk (the pool was too small or
+    // absent): known after phase 3 on the synchronous path, else always
+    // launched (it returns at once when the pool held the walk)
+    bool need_fill = true;
+    auto launch3 = [&]() -> gd_status {
+        return phase(2, [&]() -> gd_status {
+        mark(4);
+        RUN_TRY(count_pending());
+        RUN_CUDA(launch_point_boxes(dins, cells, total_cells, st), "point boxes");
+        RUN_CUDA(launch_level_diff(dins, cells, total_cells, st), "levels");
+        return GD_OK;
+        }, [&]() -> gd_status {
+        for (int j = 0; j + 1 < dmax; ++j) {
+            RUN_CUDA(launch_level_flag(dins, lflat[j], ltot[j], j, st), "level flags");
+            RUN_TRY(scan(lseg[j], lm[j], lseg_tiles[j]));
+        }
+        RUN_CUDA(launch_level_write(dins, cells, total_cells, st), "level write");
+        mark(5);
+        RUN_CUDA(launch_walk(dins, cells, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
+                 "walk");
+        RUN_CUDA(launch_nbr_total(dins, cells, total_cells, st), "list lengths");
+        RUN_TRY(scan(nseg, K, nseg_tiles));
+        RUN_CUDA(launch_nbr_check(dins, cells, total_cells, st), "list capacity");
+        mark(kStages + 3);
+        return GD_OK;
+        });
+    };
 
-    // ------------- phase 4: neighbours, core, merge, labels (sync 4)
-    long long total_nbr = 0;
-    for (int k = 0; k < K; ++k) {
-        hi[k].nnbr = (unsigned)sm(k)[kSmNnbr];
-        if (hi[k].nnbr >= INT_MAX) return fail(GD_ERANGE, "neighbour lists exceed 2^31 entries", k);
-        total_nbr += hi[k].nnbr;
-    }
-    if (total_cells > 0) mem.note_nbr_per_grid((double)total_nbr / (double)total_cells);
-    void *nbp = nullptr, *hp = nullptr;
-    // hard pairs: each candidate pair at most once, at most one per forward
-    // list entry
-    RUN_TRY(mem.device(kMemNbr, (size_t)total_nbr * 4 + 256 * (size_t)K + 256, &nbp));
-    RUN_TRY(mem.device(kMemHard, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &hp));
-    {
+    // sizes of the lists and of the FastMerging bitmaps: exact (read back
+    // after phase 3) or from the shape's earlier call
+    void* scr = nullptr;
+    int wpb = 1;
+    auto size_lists = [&]() -> gd_status {
+        long long total_nbr = 0, max_cell = 1;
+        for (int k = 0; k < K; ++k) {
+            if (hi[k].nnbr >= INT_MAX) return fail(GD_ERANGE, "neighbour lists exceed 2^31 entries", k);
+            total_nbr += hi[k].nnbr;
+            if (hi[k].maxcell > max_cell) max_cell = hi[k].maxcell;
+        }
+        wpb = (int)((max_cell + 31) / 32 + 1);
+        RUN_TRY(mem.device(kMemScratch, (size_t)fm_blocks * 2 * wpb * 4, &scr));
+        void *nbp = nullptr, *hp = nullptr;
+        // hard pairs: each candidate pair at most once, at most one per list entry
+        RUN_TRY(mem.device(kMemNbr, (size_t)total_nbr * 4 + 256 * (size_t)K + 256, &nbp));
+        RUN_TRY(mem.device(kMemHard, (size_t)total_nbr * 8 + 256 * (size_t)K + 256, &hp));
         size_t o4 = 0, o8 = 0;
         for (int k = 0; k < K; ++k) {
             hi[k].dev.nbr = (int*)((char*)nbp + o4);
             hi[k].dev.hard = (int2*)((char*)hp + o8);
+            hi[k].dev.nbr_cap = hi[k].nnbr;
             o4 += align256((size_t)hi[k].nnbr * 4);
             o8 += align256((size_t)hi[k].nnbr * 8);
         }
-    }
+        return GD_OK;
+    };
 
-    RUN_TRY(begin_desc());
-    const Flat cells = flat(members, K, C_of, &tot);
-    const Flat pts = flat(members, K, n_of, &tot);
+    // ------------- phase 4: lists, core, merge, labels
     // groups of instances by dimension and size bucket: the kernels that
-    // take the dimension as a template argument, and the tuning knobs, go
-    // by group
+    // take the dimension as a template argument, and the tuning knobs, go by
+    // group
     constexpr int kGroups = kMaxD * kSizeBuckets;
     int dgroups[kGroups], gbucket[kGroups], ng = 0;
     long long gn[kGroups];
@@ -702,141 +788,151 @@ gd_status Run::go() {
     long long g_pts_tot[kGroups], g_cells_tot[kGroups];
     int g_m[kGroups];
     const int* g_idx[kGroups];
-    for (int gi = 0; gi < ng; ++gi) {
-        int m = 0;
-        for (int k = 0; k < K; ++k)
-            if (hi[k].dev.p.d == dgroups[gi] && size_bucket(in[k].n) == gbucket[gi]) members2[m++] = k;
-        g_m[gi] = m;
-        g_pts[gi] = flat(members2, m, n_of, &g_pts_tot[gi]);
-        g_cells[gi] = flat(members2, m, C_of, &g_cells_tot[gi]);
-        g_idx[gi] = g_pts[gi].idx;
-        g_nf[gi] = dflat(members2, m, &g_nf_off[gi]);
-        for (int w = 0; w < 2; ++w) g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
-    }
-    auto arr_seg = [&](int* Inst::*field, int tot_slot) {
-        long long tiles = 0;
-        const ScanSeg* sgp = segs(
-            members, K,
-            [&](int k, int** a, long long* len) {
-                *a = hi[k].dev.*field;
-                *len = hi[k].C;
-            },
-            &tiles, tot_slot);
-        return std::make_pair(sgp, tiles);
+    long long coreseg_tiles = 0, nfseg_tiles = 0;
+    const ScanSeg* coreseg = nullptr;
+    const ScanSeg* nfseg = nullptr;
+    auto build4 = [&]() {
+        for (int gi = 0; gi < ng; ++gi) {
+            int m = 0;
+            for (int k = 0; k < K; ++k)
+                if (hi[k].dev.p.d == dgroups[gi] && size_bucket(in[k].n) == gbucket[gi]) members2[m++] = k;
+            g_m[gi] = m;
+            g_pts[gi] = flat(members2, m, n_of, &g_pts_tot[gi]);
+            g_cells[gi] = gflat(members2, m, &g_cells_tot[gi]);
+            g_idx[gi] = g_pts[gi].idx;
+            g_nf[gi] = dflat(members2, m, &g_nf_off[gi]);
+            for (int w = 0; w < 2; ++w) g_hard[w][gi] = dflat(members2, m, &g_hard_off[w][gi]);
+        }
+        auto arr_seg = [&](int* Inst::*field, int tot_slot, long long* tiles) {
+            return segs(
+                members, K,
+                [&](int k, int** a, long long* len) {
+                    *a = hi[k].dev.*field;
+                    *len = in[k].n;
+                },
+                tiles, tot_slot, kSmCells);
+        };
+        nfseg = arr_seg(&Inst::nf_start, kSmNonfull, &nfseg_tiles);
+        coreseg = arr_seg(&Inst::core_start, -1, &coreseg_tiles);
     };
-    const auto nfseg = arr_seg(&Inst::nf_start, kSmNonfull);
-    const auto coreseg = arr_seg(&Inst::core_start, -1);
-    idx = idx_all();
-    RUN_TRY(upload_desc());
+    auto launch4 = [&]() -> gd_status {
+        return phase(3, [&]() -> gd_status {
+        RUN_TRY(count_pending());
+        // the lists: from the pool's runs, or (the pool too small, or none) by
+        // a second, filling walk -- the device decides
+        RUN_CUDA(launch_pool_scatter(dins, pool, st), "neighbour scatter");
+        if (need_fill) RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
+        mark(6);
+        RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
+        return GD_OK;
+        }, [&]() -> gd_status {
+        // a warp per point (the non-full points as a flat space, scanned on
+        // the device) or a warp per grid, per group
+        bool any_point_mode = false;
+        for (int gi = 0; gi < ng; ++gi)
+            if (!knob(GD_KNOB_CORE_MODE, dgroups[gi], gn[gi])) any_point_mode = true;
+        if (any_point_mode) {
+            RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
+            RUN_TRY(scan(nfseg, K, nfseg_tiles));
+        }
+        for (int gi = 0; gi < ng; ++gi) {
+            const int d = dgroups[gi], bands = knob(GD_KNOB_CORE_BANDS, d, gn[gi]);
+            if (knob(GD_KNOB_CORE_MODE, d, gn[gi])) {
+                RUN_CUDA(launch_core_grid(dins, g_cells[gi], g_cells_tot[gi], d, bands, st), "core (counting)");
+            } else {
+                RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
+                RUN_CUDA(launch_core_point(dins, g_nf[gi], d, bands, st), "core (counting)");
+            }
+        }
+        if (info && info->want_stats) RUN_CUDA(launch_core_stats(dins, cells, total_cells, st), "core statistics");
+        mark(7);
+        RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
+        RUN_TRY(scan(coreseg, K, coreseg_tiles));
+        for (int gi = 0; gi < ng; ++gi)
+            RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
+        mark(8);
+        if (any_ldf) RUN_CUDA(launch_ldf_order(dins, idx, K, cells, total_cells, st), "low-density-first order");
+        RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
+        mark(9);
+        for (int w = 0; w < 2; ++w) {
+            if (w == 1 && all_ldf) break;  // one wave in the low-density-first order
+            for (int gi = 0; gi < ng; ++gi) {
+                const int d = dgroups[gi];
+                RUN_CUDA(launch_merge_list(dins, g_cells[gi], g_cells_tot[gi], w, d,
+                                           knob(GD_KNOB_MERGE_BUDGET, d, gn[gi]), knob(GD_KNOB_MERGE_LANE, d, gn[gi]),
+                                           knob(GD_KNOB_MERGE_SMALL, d, gn[gi]), uf_capped, st),
+                         "merge (warp)");
+            }
+            for (int gi = 0; gi < ng; ++gi) {
+                RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmHard0 + w, g_hard_off[w][gi], st), "flat offsets");
+                RUN_CUDA(launch_merge_block(dins, g_hard[w][gi], w, dgroups[gi], fm_blocks, (unsigned*)scr, wpb, uf_capped,
+                                            st),
+                         "merge (FastMerging)");
+            }
+            if (w == 0 && !all_ldf)
+                RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, uf_capped, st), "union-find flatten");
+        }
+        mark(10);
+        RUN_CUDA(launch_cluster_ids(dins, cells, total_cells, uf_capped, st), "cluster ids");
+        for (int gi = 0; gi < ng; ++gi)
+            RUN_CUDA(launch_labels(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "labels");
+        mark(11);
+        return GD_OK;
+        });
+    };
 
-    RUN_TRY(phase(3, [&]() -> gd_status {
-    if (pool_segs >= 0)
-        RUN_CUDA(launch_pool_scatter(dins, pool, pool_segs, st), "neighbour scatter");
-    else
-        RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
-    mark(6);
-    RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
-    return GD_OK;
-    }, [&]() -> gd_status {
-    // a warp per point (the non-full points as a flat space, scanned on the
-    // device) or a warp per grid, per group
-    bool any_point_mode = false;
-    for (int gi = 0; gi < ng; ++gi)
-        if (!knob(GD_KNOB_CORE_MODE, dgroups[gi], gn[gi])) any_point_mode = true;
-    if (any_point_mode) {
-        RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
-        RUN_TRY(scan(nfseg.first, K, nfseg.second));
-    }
-    for (int gi = 0; gi < ng; ++gi) {
-        const int d = dgroups[gi], bands = knob(GD_KNOB_CORE_BANDS, d, gn[gi]);
-        if (knob(GD_KNOB_CORE_MODE, d, gn[gi])) {
-            RUN_CUDA(launch_core_grid(dins, g_cells[gi], g_cells_tot[gi], d, bands, st), "core (counting)");
-        } else {
-            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmNonfull, g_nf_off[gi], st), "flat offsets");
-            RUN_CUDA(launch_core_point(dins, g_nf[gi], d, bands, st), "core (counting)");
+    if (queued) {
+        // everything is known: one upload, then the four phases back to back
+        RUN_TRY(size_lists());
+        build4();
+        RUN_TRY(upload_desc());
+        if (stage.done) RUN_CUDA(cudaEventRecord(stage.done, st), "staging");
+        RUN_TRY(launch1());
+        RUN_TRY(launch2());
+        RUN_TRY(launch3());
+        RUN_TRY(launch4());
+    } else {
+        for (int k = 0; k < K; ++k) hi[k].dev.nbr_cap = LLONG_MAX;  // phase 3 writes no list
+        RUN_TRY(upload_desc());
+        RUN_TRY(launch2());
+        RUN_TRY(launch3());
+        RUN_TRY(readback());
+        for (int k = 0; k < K; ++k) {
+            hi[k].C = sm(k)[kSmCells];
+            hi[k].maxcell = sm(k)[kSmMaxCell];
+            hi[k].nnbr = (unsigned)sm(k)[kSmNnbr];
         }
-    }
-    if (dstats) RUN_CUDA(launch_core_stats(dins, cells, total_cells, st), "core statistics");
-    mark(7);
-    RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
-    RUN_TRY(scan(coreseg.first, K, coreseg.second));
-    for (int gi = 0; gi < ng; ++gi)
-        RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
-    mark(8);
-    if (any_ldf) RUN_CUDA(launch_ldf_order(dins, idx, K, cells, total_cells, st), "low-density-first order");
-    RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
-    mark(9);
-    for (int w = 0; w < 2; ++w) {
-        if (w == 1 && all_ldf) break;  // one wave in the low-density-first order
-        for (int gi = 0; gi < ng; ++gi) {
-            const int d = dgroups[gi];
-            RUN_CUDA(launch_merge_list(dins, g_cells[gi], g_cells_tot[gi], w, d, knob(GD_KNOB_MERGE_BUDGET, d, gn[gi]),
-                                       knob(GD_KNOB_MERGE_LANE, d, gn[gi]), knob(GD_KNOB_MERGE_SMALL, d, gn[gi]), st),
-                     "merge (warp)");
+        if (pooled) {
+            unsigned long long ctr;
+            memcpy(&ctr, sm(0) + kSmPool, sizeof(ctr));
+            need_fill = (long long)(ctr & ((1ull << kPoolBits) - 1)) > pool.cap ||
+                        (long long)(ctr >> kPoolBits) > pool.seg_cap;
         }
-        for (int gi = 0; gi < ng; ++gi) {
-            RUN_CUDA(count_flat(dins, g_idx[gi], g_m[gi], kSmHard0 + w, g_hard_off[w][gi], st), "flat offsets");
-            RUN_CUDA(launch_merge_block(dins, g_hard[w][gi], w, dgroups[gi], fm_blocks, (unsigned*)scr, wpb, st),
-                     "merge (FastMerging)");
-        }
-        if (w == 0 && !all_ldf) RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, st), "union-find flatten");
-    }
-    mark(10);
-    RUN_CUDA(launch_cluster_ids(dins, cells, total_cells, st), "cluster ids");
-    for (int gi = 0; gi < ng; ++gi)
-        RUN_CUDA(launch_labels(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "labels");
-    mark(11);
-    return GD_OK;
-    }));
-    RUN_TRY(readback());
-    for (int k = 0; k < K; ++k)
-        if ((unsigned)sm(k)[kSmStatus] & kDevTimeout)
-            return fail(GD_ETIMEOUT, "a bounded device wait or retry loop hit its limit", k);
-    if (dstats) {
-        // (statistics runs are not timed: a plain synchronous copy)
-        void* hs = nullptr;
-        RUN_TRY(mem.host(kHostDesc, sizeof(unsigned long long) * kStatCount * K, &hs));
-        RUN_CUDA(cudaMemcpyAsync(hs, dstats, sizeof(unsigned long long) * kStatCount * K, cudaMemcpyDeviceToHost, st),
-                 "statistics");
-        RUN_CUDA(cudaStreamSynchronize(st), "synchronise");
-        const unsigned long long* v = (const unsigned long long*)hs;
-        for (int i = 0; i < kStatCount; ++i) info->stats[i] = 0;
-        for (int k = 0; k < K; ++k)
-            for (int i = 0; i < kStatCount; ++i) info->stats[i] += v[(size_t)k * kStatCount + i];
-        info->have_stats = true;
+        RUN_TRY(size_lists());
+        build4();
+        RUN_TRY(upload_desc());
+        if (stage.done) RUN_CUDA(cudaEventRecord(stage.done, st), "staging");
+        RUN_TRY(launch4());
     }
 
     if (info) {
+        // what is known now; finish_batch adds the sizes the device found
         const HI& h = hi[0];
-        const int* s0 = sm(0);
         const int n = h.dev.p.n, d = h.dev.p.d;
-        const long long C = h.C;
         info->sizes[0] = n;
         info->sizes[1] = d;
-        info->sizes[2] = C;
-        info->sizes[3] = h.nnbr;
         info->sizes[4] = h.dev.p.s;
         info->sizes[5] = h.dev.p.key_bits;
-        info->sizes[6] = 0;  // filled by the caller (launch count)
-        info->sizes[7] = (long long)s0[kSmPairsT];
         info->sizes[8] = h.dev.passes;
         info->sizes[9] = h.dev.digit_bits;
-        info->sizes[10] = (long long)s0[kSmHard0] + s0[kSmHard1];
         info->sizes[11] = h.dev.p.key_class;
         info->view_ptr[GD_VIEW_PERM] = (h.dev.passes & 1) ? h.dev.valB : h.dev.valA;
-        info->view_bytes[GD_VIEW_PERM] = (size_t)n * 4;
         info->view_ptr[GD_VIEW_CELL_START] = h.dev.cell_start;
-        info->view_bytes[GD_VIEW_CELL_START] = (size_t)(C + 1) * 4;
         info->view_ptr[GD_VIEW_CELL_COORD] = h.dev.cell_coord;
-        info->view_bytes[GD_VIEW_CELL_COORD] = (size_t)C * d * 4;
         info->view_ptr[GD_VIEW_NBR_START] = h.dev.nbr_start;
-        info->view_bytes[GD_VIEW_NBR_START] = (size_t)(C + 1) * 4;
         info->view_ptr[GD_VIEW_NBR] = h.dev.nbr;
-        info->view_bytes[GD_VIEW_NBR] = (size_t)h.nnbr * 4;
         info->view_ptr[GD_VIEW_CORE_SORTED] = h.dev.core_s;
-        info->view_bytes[GD_VIEW_CORE_SORTED] = (size_t)n;
         info->view_ptr[GD_VIEW_CELL_CID] = h.dev.cell_cid;
-        info->view_bytes[GD_VIEW_CELL_CID] = (size_t)C * 4;
     }
     return GD_OK;
 }
@@ -878,12 +974,100 @@ int Tuning::value(int knob, int d, long long n) const {
 }
 
 gd_status run_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, cudaEvent_t* events,
-                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs, cudaEvent_t* sort_events) {
-    Run r{mem, K, inst, st, events, info, tuning, graphs, sort_events};
+                    RunInfo* info, const Tuning* tuning, PhaseGraphs* graphs, cudaEvent_t* sort_events,
+                    StageSet stage, bool allow_async) {
+    Run r{mem, K, inst, st, events, info, tuning, graphs, sort_events, stage, allow_async};
     const long long l0 = t_launches;
     const gd_status s = r.go();
     if (info) info->launches = t_launches - l0;
     return s;
+}
+
+gd_status finish_batch(MemProvider& mem, int K, const gd_instance* inst, cudaStream_t st, RunInfo* info) {
+    auto cuda_fail = [&](cudaError_t e, const char* where) {
+        if (info) info->error = std::string(where) + ": " + cudaGetErrorString(e);
+        return GD_ECUDA;
+    };
+    const size_t small_bytes = sizeof(int) * kSmallInts * K;
+    const bool stats = info && info->want_stats;
+    const size_t stat_bytes = stats ? sizeof(unsigned long long) * kStatCount * K : 0;
+    void* h = nullptr;
+    gd_status s = mem.host(kHostFinish, small_bytes + stat_bytes + 64, &h);
+    if (s != GD_OK) return s;
+    // (the buffers exist and are large enough: the run asked for them)
+    void* dsm = mem.current(kMemSmall);
+    void* dst = mem.current(kMemStats);
+    if (!dsm || (stats && !dst)) {
+        if (info) info->error = "no run to finish";
+        return GD_EINVAL;
+    }
+    cudaError_t e = cudaMemcpyAsync(h, dsm, small_bytes, cudaMemcpyDeviceToHost, st);
+    unsigned long long* hst = reinterpret_cast<unsigned long long*>((char*)h + ((small_bytes + 63) & ~(size_t)63));
+    if (e == cudaSuccess && stats) e = cudaMemcpyAsync(hst, dst, stat_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "read back");
+    const int* sm = (const int*)h;
+    gd_status result = GD_OK;
+    unsigned any = 0;
+    for (int k = 0; k < K; ++k) {
+        const unsigned bits = (unsigned)sm[(size_t)k * kSmallInts + kSmStatus];
+        any |= bits;
+        if ((bits & kDevRange) && result == GD_OK) {
+            result = GD_ERANGE;
+            if (info) info->error = "coordinate range too large: d * R^2 >= 2^62 (instance " + std::to_string(k) + ")";
+        }
+    }
+    if (result == GD_OK && (any & (kDevReplan | kDevOverflow))) result = kGdRerun;
+    if (result == GD_OK && (any & kDevTimeout)) {
+        result = GD_ETIMEOUT;
+        if (info) info->error = "a bounded device wait or retry loop hit its limit";
+    }
+    if (result == GD_OK) {
+        // the shapes' plans and sizes for later calls; the pool's use
+        PlanCache* pc = mem.plans();
+        double entries = 0, runs = 0, pts = 0;
+        for (int k = 0; k < K; ++k) {
+            const int* s0 = sm + (size_t)k * kSmallInts;
+            pts += (double)inst[k].n;
+            if (!pc) continue;
+            const long long cap = (1ll << 62) - 1;
+            ShapePlan* p = pc->slot(inst[k].n, inst[k].d, inst[k].eps2 > cap ? cap : inst[k].eps2);
+            p->stamp = ++pc->clock;
+            p->key_class = s0[kSmKeyClass];
+            p->key_words = s0[kSmKeyWords];
+            p->key_bits = s0[kSmKeyBits];
+            p->nnbr = (unsigned)s0[kSmNnbr];
+            p->maxcell = s0[kSmMaxCell];
+            entries += (double)(unsigned)s0[kSmNnbr];
+        }
+        const unsigned long long ctr = *reinterpret_cast<const unsigned long long*>(sm + kSmPool);
+        runs = (double)(ctr >> kPoolBits);
+        const double used = (double)(ctr & ((1ull << kPoolBits) - 1));
+        if (pts > 0) mem.note_pool((used > 0 ? used : entries) / pts, runs / pts);
+    }
+    if (info) {
+        const int* s0 = sm;
+        const long long C = s0[kSmCells], nnbr = (unsigned)s0[kSmNnbr];
+        const long long n = info->sizes[0], d = info->sizes[1];
+        info->sizes[2] = C;
+        info->sizes[3] = nnbr;
+        info->sizes[7] = (long long)s0[kSmPairsT];
+        info->sizes[10] = (long long)s0[kSmHard0] + s0[kSmHard1];
+        info->view_bytes[GD_VIEW_PERM] = (size_t)n * 4;
+        info->view_bytes[GD_VIEW_CELL_START] = (size_t)(C + 1) * 4;
+        info->view_bytes[GD_VIEW_CELL_COORD] = (size_t)C * d * 4;
+        info->view_bytes[GD_VIEW_NBR_START] = (size_t)(C + 1) * 4;
+        info->view_bytes[GD_VIEW_NBR] = (size_t)nnbr * 4;
+        info->view_bytes[GD_VIEW_CORE_SORTED] = (size_t)n;
+        info->view_bytes[GD_VIEW_CELL_CID] = (size_t)C * 4;
+        if (stats) {
+            for (int i = 0; i < kStatCount; ++i) info->stats[i] = 0;
+            for (int k = 0; k < K; ++k)
+                for (int i = 0; i < kStatCount; ++i) info->stats[i] += hst[(size_t)k * kStatCount + i];
+            info->have_stats = true;
+        }
+    }
+    return result;
 }
 
 }  // namespace gd
