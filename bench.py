@@ -46,7 +46,7 @@ L2_FLUSH_BYTES = 256 << 20
 # kernel's source text: a changed kernel reports no traffic until it is
 # captured again.
 SORT_PASS_TRAFFIC = {
-    "5a717ff6a2d61758": {"workload": "ss3d_10m", "key_class": 0, "bytes": 116.5e6},
+    "5a717ff6a2d61758": {"workload": "ss3d_10m", "key_class": 0, "bytes": 115.6e6},
 }
 
 
@@ -489,7 +489,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
 
     # each rank clusters its own independent instance (replicas, weak scaling)
-    X, eps2, minpts = synth.workload(args.workload, seed=1 + rank)
+    X, eps2, minpts = synth.workload(args.workload, seed=1 + rank, n=args.n)
     n, d = X.shape
     Xd = torch.from_numpy(X).to(dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
@@ -652,6 +652,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gdbscan", "reference"], default="gdbscan")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ss3d_10m")
+    ap.add_argument("--n", type=int, default=None,
+                    help="points of the headline workload (default: its full size; for profiling captures)")
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="points of the workload the CPU oracle times (default: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
