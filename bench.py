@@ -38,7 +38,7 @@ WORKLOADS = {
 # skewed-mix variant.
 CONFIGS = [("T", "tiny", 20), ("S", "ss3d_2m", 10), ("L3", "ss3d_10m", 10), ("L3_skew", "skew3d_10m", 10),
            ("L5", "skew5d_10m", 5)]
-HBM_STAGES = ("bounds", "quantise", "sort", "compact", "core")
+HBM_STAGES = ("bounds", "quantise", "sort", "compact", "lists", "core")
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) per downsweep launch, from one `ncu --set full`
@@ -82,6 +82,11 @@ def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float, stat
         "sort": (P * 2 * (key_b + val_b) + (P - (1 if first_hist else 0)) * key_b) * n,
         "compact": (2 * key_b + val_b + 4 + 4 + 4 * d + 4 * dp) * n,
     }
+    # the lists: the walk's forward entries (each pair once, self included)
+    # read from its pool, every entry written into the scanned lists
+    nnbr, grids = sizes.get("nnbr", 0), sizes.get("grids", 0)
+    if nnbr:
+        bytes_["lists"] = 4 * ((nnbr + grids) // 2 + nnbr)
     if stats:
         bytes_["core"] = n + min(n, stats["nonfull_points"] + stats["count_rows"]) * 4 * dp
     out = {}
@@ -350,6 +355,39 @@ def oracle_check(m: dict, fastmerging: bool = True) -> dict:
     return out
 
 
+def stencil_offsets(d: int, eps2: int) -> int:
+    """Identifier offsets delta (a stencil) whose grids can hold points
+    within eps of the query grid's: sum over j of gap_j^2 <= eps2, with
+    gap_j = (|delta_j| - 1) s + 1 for delta_j != 0 (the relation of Eq. 2 in
+    integers, s the integer cell side).  The alternative to the tree query
+    would probe each of these per grid (half of them, pairs once)."""
+    import math
+    s = 1 + math.isqrt(eps2 // d)
+    r = 0 if eps2 == 0 else 1 + (math.isqrt(eps2) - 1) // s
+    sums = {0: 1}  # partial sum of squared gaps -> number of offset prefixes
+    for _ in range(d):
+        nxt = {}
+        for v, c in sums.items():
+            for dl in range(-r, r + 1):
+                g = 0 if dl == 0 else (abs(dl) - 1) * s + 1
+                w = v + g * g
+                if w <= eps2:
+                    nxt[w] = nxt.get(w, 0) + c
+        sums = nxt
+    return sum(sums.values())
+
+
+def walk_summary(stats: dict, grids: int, d: int, eps2: int) -> dict:
+    """Work of the neighbour query (Alg. 3 on the sorted levels) per query
+    grid, beside the size of the offset stencil it replaces."""
+    if not grids or "walk_nodes" not in stats:
+        return {}
+    st = stencil_offsets(d, eps2)
+    return {"nodes_tested_per_grid": round(stats["walk_nodes"] / grids, 1),
+            "warp_steps_per_grid": round(stats["walk_steps"] / grids, 2),
+            "stencil_offsets": st, "stencil_probes_per_grid": (st + 1) // 2}
+
+
 def config_line(label: str, workload: str, m: dict, peak: float, dist_peak: float, check: dict | None) -> dict:
     n, d = m["X"].shape
     stages = m["stages"]
@@ -364,7 +402,8 @@ def config_line(label: str, workload: str, m: dict, peak: float, dist_peak: floa
             "dominant_stage": {"name": dom, "ms": round(main[dom], 4), "share": round(main[dom] / total, 3)},
             "stage_bandwidth": sb,
             "alu": alu_utilisation(stages, m["stats"], dist_peak),
-            "merge": merge_summary(m["stats"])}
+            "merge": merge_summary(m["stats"]),
+            "walk": walk_summary(m["stats"], m["sizes"]["grids"], d, m["eps2"])}
     # roofline of the config's dominant HBM-bound stage (grid build or count)
     hb = {k: v for k, v in sb.items() if k in HBM_STAGES}
     if hb:

@@ -116,7 +116,18 @@ gd_status gd_dbscan_host(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, i
                          int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
                          gd_stream_t stream);
 
-/* One instance of a batch: device pointers and parameters as for gd_dbscan. */
+/* One instance of a batch: device pointers and parameters as for gd_dbscan.
+ *
+ * eps2_yes selects approximate FastMerging (the Remark after Alg. 5, O(1)
+ * rounds whatever eps and d): 0 (what a zero-initialised record holds) is
+ * exact DBSCAN; a value >= eps2, normally floor((eps + delta)^2) for a
+ * constant delta > 0, lets FastMerging answer "yes" for two core grids as
+ * soon as it meets a pair of their core points at squared distance <=
+ * eps2_yes.  Core flags, the pruning of FastMerging, every other merge test
+ * and the border rule stay exact at eps2, so the clustering lies between
+ * exact DBSCAN at eps and at eps + delta: every exact cluster's core points
+ * fall in one cluster of the result, and every cluster of the result lies
+ * in one cluster of DBSCAN at eps2_yes.  A value in (0, eps2) is GD_EINVAL. */
 typedef struct {
     const int32_t *X;  /* [n][d] row-major, device */
     int64_t n;
@@ -125,6 +136,7 @@ typedef struct {
     int32_t minpts;
     int32_t *labels;   /* [n], device */
     uint8_t *is_core;  /* [n], device, or NULL */
+    int64_t eps2_yes;  /* 0: exact; else approximate FastMerging's acceptance radius^2 */
 } gd_instance;
 
 /* Exact DBSCAN of k independent instances (uneven sizes, dimensions and
@@ -270,9 +282,10 @@ gd_status gd_copy_view(gd_ctx *ctx, gd_view which, void *host_dst, size_t bytes)
 
 /* Per-stage device timing (CUDA events around each stage of gd_dbscan).
  * Off by default; when on, gd_stage_times fills up to max entries of
- * milliseconds and names for the last run and returns the count: the 11
- * stages in order -- bounds, quantise, sort, compact, levels, walk, core,
- * core_pack, merge_order, merge, labels -- (device time from a stage's first
+ * milliseconds and names for the last run and returns the count: the 12
+ * stages in order -- bounds, quantise, sort, compact, levels, walk, lists
+ * (the neighbour lists placed from the walk's pool, or a second filling
+ * walk), core, core_pack, merge_order, merge, labels -- (device time from a stage's first
  * launch to its last; the host's work between the call's phases is in none
  * of them), then
  * "sort_downsweep", the summed time of the radix sort's downsweep kernels
@@ -318,6 +331,10 @@ gd_status gd_inject_alloc_failure(gd_ctx *ctx, int32_t k);
  *                        exact squared distances evaluated by core
  *                        counting, the warp-level merge, FastMerging and
  *                        border labelling
+ *   walk_nodes           grid-tree nodes the neighbour query (Alg. 3) tested,
+ *                        summed over query grids (each pair of grids is
+ *                        enumerated from one side only)
+ *   walk_steps           warp steps of that query (up to 32 nodes each)
  *   kappa_1 .. kappa_15, kappa_16_or_more
  *                        FastMerging calls by number of rounds (kappa of
  *                        Section 4.3.3)

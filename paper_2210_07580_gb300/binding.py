@@ -23,7 +23,8 @@ VIEW_PERM, VIEW_CELL_START, VIEW_CELL_COORD, VIEW_NBR_START, VIEW_NBR, VIEW_CORE
 class GdInstance(ctypes.Structure):
     """gd_instance of include/gdbscan.h."""
     _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int), ("eps2", ctypes.c_int64),
-                ("minpts", ctypes.c_int32), ("labels", ctypes.c_void_p), ("is_core", ctypes.c_void_p)]
+                ("minpts", ctypes.c_int32), ("labels", ctypes.c_void_p), ("is_core", ctypes.c_void_p),
+                ("eps2_yes", ctypes.c_int64)]
 
 
 class GdTuning(ctypes.Structure):
@@ -212,12 +213,15 @@ class Context:
         """gd_sync: finish the queued call and raise GdError if it failed."""
         self._check(self._lib.gd_sync(self._h, _stream_handle(stream)))
 
-    def dbscan(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None, sync: bool = True):
+    def dbscan(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None, sync: bool = True,
+               eps2_yes: int = 0):
         """Cluster the device tensor X (torch.int32, [n, d], contiguous, on this
         context's device).  Returns (labels int32 [n], is_core bool [n]) as
         device tensors (or fills the given ones; is_core must be uint8/bool).
         With sync=False the call only queues the work (gd_dbscan is
-        asynchronous): the results are final after sync()."""
+        asynchronous): the results are final after sync().  eps2_yes > 0
+        selects approximate FastMerging (gd_instance.eps2_yes; a batch of one
+        instance)."""
         import torch
         if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
             raise TypeError("X must be a CUDA int32 tensor of shape [n, d]")
@@ -227,8 +231,13 @@ class Context:
             labels = torch.empty(n, dtype=torch.int32, device=X.device)
         if is_core is None:
             is_core = torch.empty(n, dtype=torch.uint8, device=X.device)
-        st = self._lib.gd_dbscan(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
-                                 is_core.data_ptr(), _stream_handle(stream))
+        if eps2_yes:
+            one = (GdInstance * 1)(GdInstance(X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
+                                              is_core.data_ptr(), int(eps2_yes)))
+            st = self._lib.gd_dbscan_batched(self._h, 1, ctypes.cast(one, ctypes.c_void_p), _stream_handle(stream))
+        else:
+            st = self._lib.gd_dbscan(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
+                                     is_core.data_ptr(), _stream_handle(stream))
         self._check(st)
         if sync:
             self.sync(stream)
@@ -236,7 +245,8 @@ class Context:
 
     def dbscan_batched(self, jobs, outputs=None, stream=None, sync: bool = True):
         """Cluster a batch of instances in one gd_dbscan_batched call.  jobs is a
-        list of (X, eps2, minpts) with X a CUDA int32 [n, d] tensor (n >= 1);
+        list of (X, eps2, minpts) or (X, eps2, minpts, eps2_yes) with X a CUDA
+        int32 [n, d] tensor (n >= 1; eps2_yes as gd_instance.eps2_yes);
         returns a list of (labels, is_core) device tensors (or fills `outputs`,
         a list of (labels int32, is_core uint8) tensor pairs)."""
         import torch
@@ -244,7 +254,9 @@ class Context:
         arr = (GdInstance * max(k, 1))()
         outs = []
         keep = []
-        for i, (X, eps2, minpts) in enumerate(jobs):
+        for i, job in enumerate(jobs):
+            X, eps2, minpts = job[:3]
+            eps2_yes = int(job[3]) if len(job) > 3 else 0
             if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.int32 and X.dim() == 2):
                 raise TypeError("each X must be a CUDA int32 tensor of shape [n, d]")
             X = X.contiguous()
@@ -256,7 +268,7 @@ class Context:
                 lab = torch.empty(n, dtype=torch.int32, device=X.device)
                 core = torch.empty(n, dtype=torch.uint8, device=X.device)
             outs.append((lab, core))
-            arr[i] = GdInstance(X.data_ptr(), n, d, int(eps2), int(minpts), lab.data_ptr(), core.data_ptr())
+            arr[i] = GdInstance(X.data_ptr(), n, d, int(eps2), int(minpts), lab.data_ptr(), core.data_ptr(), eps2_yes)
         self._check(self._lib.gd_dbscan_batched(self._h, k, ctypes.cast(arr, ctypes.c_void_p),
                                                 _stream_handle(stream)))
         if sync:

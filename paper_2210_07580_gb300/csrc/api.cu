@@ -160,6 +160,7 @@ gd_status validate_one(const gd_instance& g, std::string* err) {
     if (g.d < 1 || g.d > kMaxD) return *err = "d must be in [1, 8]", GD_EINVAL;
     if (g.n < 0 || g.n >= (int64_t)INT_MAX) return *err = "n must be in [0, 2^31 - 1)", GD_EINVAL;
     if (g.eps2 < 0) return *err = "eps2 must be >= 0", GD_EINVAL;
+    if (g.eps2_yes != 0 && g.eps2_yes < g.eps2) return *err = "eps2_yes must be 0 or >= eps2", GD_EINVAL;
     if (g.minpts < 1) return *err = "minpts must be >= 1", GD_EINVAL;
     if (g.n > 0 && (!g.X || !g.labels)) return *err = "null pointer with n > 0", GD_EINVAL;
     return GD_OK;
@@ -528,7 +529,7 @@ gd_status gd_set_stats(gd_ctx* ctx, int enable) {
 static const char* const kStatNames[kStatCount] = {
     "pairs", "pairs_skipped", "pairs_box_no", "pairs_box_yes", "pairs_lane", "pairs_warp", "pairs_fastmerging",
     "fm_yes", "fm_no", "fm_pruned_triangle", "fm_pruned_angle", "nonfull_points", "count_rows",
-    "dist_core", "dist_merge", "dist_fastmerging", "dist_labels",
+    "dist_core", "dist_merge", "dist_fastmerging", "dist_labels", "walk_nodes", "walk_steps",
     "kappa_1", "kappa_2", "kappa_3", "kappa_4", "kappa_5", "kappa_6", "kappa_7", "kappa_8", "kappa_9",
     "kappa_10", "kappa_11", "kappa_12", "kappa_13", "kappa_14", "kappa_15", "kappa_16_or_more"};
 

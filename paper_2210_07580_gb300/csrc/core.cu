@@ -142,17 +142,61 @@ __device__ __forceinline__ BoxDist box_dist(const long long* x, const int* __res
     return r;
 }
 
+// Points of the straddling grids of one 32-entry chunk of a neighbour list,
+// streamed as one flat sequence (lane k taking the k-th point): lane t holds
+// the chunk's t-th grid as (first row st, rows sz; sz = 0 for a grid that is
+// not straddling).  Adds the hits to cnt and stops once it reaches MinPts.
+template <int D, int DP>
+__device__ __forceinline__ void count_straddling(const int* __restrict__ Xs, const long long* x, int st, int sz,
+                                                 long long eps2, int minpts, int& cnt, unsigned& ndist) {
+    const int lane = lane_id();
+    const int incl = warp_inclusive_scan(sz);
+    const int flat = __shfl_sync(kFull, incl, 31);
+    for (int k0 = 0; k0 < flat; k0 += 32) {
+        const int k = k0 + lane;
+        int lo2 = 0, hi2 = 31;
+#pragma unroll
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo2 + hi2) >> 1;
+            if (__shfl_sync(kFull, incl, mid) > k)
+                hi2 = mid;
+            else
+                lo2 = mid + 1;
+        }
+        const int gst = __shfl_sync(kFull, st, lo2);
+        const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
+        bool hit = false;
+        if (k < flat) {
+            const long long qi = (long long)gst + (k - gex);
+            long long dd = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const long long t = (long long)Xs[qi * DP + j] - x[j];
+                dd += t * t;
+            }
+            hit = dd <= eps2;
+        }
+        cnt += __popc(__ballot_sync(kFull, hit));
+        ndist += (unsigned)min(32, flat - k0);
+        if (cnt >= minpts) break;
+    }
+}
+
 // One warp per point p of a non-full grid g.  The lanes take the grids of
 // Nei(g) 32 at a time and compare each grid's point box with p:
 //   - box entirely within eps of p: all its points count, no distances;
 //   - box entirely beyond eps: skipped;
-//   - otherwise its points are tested one by one (the straddling grids'
-//     points are streamed as one flat sequence, lane k taking the k-th).
+//   - otherwise (straddling) its points are tested one by one
+//     (count_straddling).
 // g itself is always entirely within eps (its diameter is <= eps).  Whole
-// grids are counted first; straddling grids are then scanned -- for short
-// neighbour lists in three bands of increasing box distance (up to eps/4,
-// eps/2, eps), so that a core point usually reaches MinPts among the nearest
-// points.  The warp stops as soon as the count reaches MinPts.
+// grids are counted first, over the whole list, which also gives the points
+// of the straddling grids; the straddling grids are then scanned -- for
+// short neighbour lists in three bands of increasing box distance (up to
+// eps/4, eps/2, eps), so that a core point usually reaches MinPts among the
+// nearest points.  The warp stops as soon as the count reaches MinPts, or
+// as soon as the straddling points not yet tested could no longer bring it
+// there (p is then not core; in sparse data most non-core points stop
+// before testing any distance).
 template <int D>
 __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict__ ins, Flat f, int band_limit) {
     constexpr int DP = Padded<D>::value;
@@ -186,28 +230,31 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
 #pragma unroll
         for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];
         int cnt = 0;
+        long long rest = 0;  // points of the straddling grids not yet tested
         unsigned ndist = 0;  // statistics: distances this warp evaluated
         const int t_begin = I.nbr_start[c], t_end = I.nbr_start[c + 1];
         const int* nbr = I.nbr;
-        // whole grids
+        // whole grids, and the size of the straddling ones
         for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
-            int whole = 0;
+            int whole = 0, part = 0;
             if (t0 + lane < t_end) {
                 const int cc = nbr[t0 + lane];
+                const int a = cell_start[cc], b = cell_start[cc + 1];
                 const BoxDist bd = box_dist<D>(x, pbox, cc);
-                if (bd.maxd <= eps2) whole = cell_start[cc + 1] - cell_start[cc];
+                if (bd.maxd <= eps2) whole = b - a;
+                else if (bd.mind <= eps2) part = b - a;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) whole += __shfl_xor_sync(kFull, whole, o);
-            cnt += whole;
+            cnt += __reduce_add_sync(kFull, whole);
+            rest += __reduce_add_sync(kFull, part);
         }
-        // straddling grids, nearest band first when the list is short (dense
-        // neighbourhoods: few grids, many points each); one pass otherwise
+        // straddling grids, nearest band first when the list is short
+        // (dense neighbourhoods: few grids, many points each); one pass
+        // otherwise
         const int nbands = (t_end - t_begin) <= band_limit ? 3 : 1;
-        for (int band = 0; band < nbands && cnt < minpts; ++band) {
+        for (int band = 0; band < nbands && cnt < minpts && cnt + rest >= minpts; ++band) {
             const long long blo = band == 0 ? -1 : (band == 1 ? eps2 / 16 : eps2 / 4);
             const long long bhi = nbands == 1 ? eps2 : (band == 0 ? eps2 / 16 : (band == 1 ? eps2 / 4 : eps2));
-            for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
+            for (int t0 = t_begin; t0 < t_end && cnt < minpts && cnt + rest >= minpts; t0 += 32) {
                 int st = 0, sz = 0;
                 if (t0 + lane < t_end) {
                     const int cc = nbr[t0 + lane];
@@ -217,36 +264,8 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
                         sz = cell_start[cc + 1] - st;
                     }
                 }
-                const int incl = warp_inclusive_scan(sz);
-                const int flat = __shfl_sync(kFull, incl, 31);
-                for (int k0 = 0; k0 < flat; k0 += 32) {
-                    const int k = k0 + lane;
-                    int lo2 = 0, hi2 = 31;
-#pragma unroll
-                    for (int step = 0; step < 5; ++step) {
-                        const int mid = (lo2 + hi2) >> 1;
-                        if (__shfl_sync(kFull, incl, mid) > k)
-                            hi2 = mid;
-                        else
-                            lo2 = mid + 1;
-                    }
-                    const int gst = __shfl_sync(kFull, st, lo2);
-                    const int gex = __shfl_sync(kFull, incl, lo2) - __shfl_sync(kFull, sz, lo2);
-                    bool hit = false;
-                    if (k < flat) {
-                        const long long qi = (long long)gst + (k - gex);
-                        long long dd = 0;
-#pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const long long t = (long long)Xs[qi * DP + j] - x[j];
-                            dd += t * t;
-                        }
-                        hit = dd <= eps2;
-                    }
-                    cnt += __popc(__ballot_sync(kFull, hit));
-                    ndist += (unsigned)min(32, flat - k0);
-                    if (cnt >= minpts) break;
-                }
+                count_straddling<D, DP>(Xs, x, st, sz, eps2, minpts, cnt, ndist);
+                rest -= __reduce_add_sync(kFull, sz);
             }
         }
         if (lane == 0) {
@@ -266,7 +285,9 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
 //   pass 2, while p is short of MinPts: the straddling grids' points are
 //     streamed as one flat sequence (lane k taking the k-th) -- for short
 //     lists nearest band first, as in core_point_kernel.
-// A point stops as soon as its count reaches MinPts.
+// A point stops as soon as its count reaches MinPts.  (Bounding the count by
+// the straddling points left, as core_point_kernel does, costs a second
+// reduction per point and entry here and did not pay on 3-d data.)
 constexpr int kCoreWarps = 8;
 
 template <int D>

@@ -52,6 +52,10 @@ struct Params {
     int d;            // dimensions (1..8)
     int dp;           // padded row stride of the grid-order coordinates (1,2,4,8)
     long long eps2;   // squared radius (clamped below 2^62)
+    // FastMerging's "yes" radius^2: eps2 (exact), or larger for approximate
+    // FastMerging (the Remark after Alg. 5), which accepts a pair within
+    // eps + delta and prunes as the exact one does
+    long long eps2_yes;
     int minpts;
     long long s;      // integer cell side: largest s with d*(s-1)^2 <= eps2
     // floor(x / s) for 32-bit x as the high word of s_mul * x (s_mul =
@@ -119,6 +123,8 @@ enum StatSlot {
     kStDistMerge,      // ... merging (lane loops and warp tiles),
     kStDistFm,         // ... FastMerging (every pass, the angle bound included),
     kStDistLabels,     // ... border labels
+    kStWalkNodes,      // tree nodes whose key the neighbour walk tested (Alg. 3)
+    kStWalkSteps,      // warp steps of the walk (up to 32 node tests each)
     kStKappa,          // [kKappaBins] FastMerging rounds 1, 2, ..., then >= kKappaBins
     kKappaBins = 16,
     kStatCount = kStKappa + kKappaBins

@@ -810,6 +810,7 @@ __global__ void __launch_bounds__(kFmBlock, 3) merge_block_kernel(const Inst* __
         const int kk = flat_find(f, h);
         const Inst& I = ins[f.idx[kk]];
         const long long eps2 = I.p.eps2;
+        const long long yes2 = I.p.eps2_yes;  // eps2, or (eps + delta)^2 in approximate FastMerging
         const int base = wave == 0 ? 0 : I.small[kSmHard0];
         const int2 pr = I.hard[base + (h - f.off[kk])];
         int* parent = I.parent;
@@ -873,7 +874,7 @@ __global__ void __launch_bounds__(kFmBlock, 3) merge_block_kernel(const Inst* __
         bool yes = false;
         int kappa = 1;  // rounds: one per nearest point q found in s_j
         for (int round = 0; round <= ma + mb; ++round) {
-            if (bq.d <= eps2) {
+            if (bq.d <= yes2) {
                 yes = true;
                 break;
             }
@@ -886,7 +887,7 @@ __global__ void __launch_bounds__(kFmBlock, 3) merge_block_kernel(const Inst* __
             float cl = fm_cos_lambda<D, DP>(B, mb, live_b, piv, qv, bq.d, eps2, sd, pdist);
             bp = fm_pass<D, DP, true>(A, ma, live_a, piv, bq.d, qv, cl, eps2, sb, sc, &cnt, ptri, pang, pdist);
             if (cnt == 0) break;
-            if (bp.d <= eps2) {
+            if (bp.d <= yes2) {
                 yes = true;
                 break;
             }

@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             }
         }
         __syncwarp();
+        long long nodes = 0, steps = 0;  // statistics
         while (top > 0) {
             // the group: the entries of the top level, lane i holding entry top-1-i
             const int J = slvl[top - 1] & (kTight - 1);
@@ -416,6 +417,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const long long my_part = __shfl_sync(kFull, epart, src);
             const int my_tight = __shfl_sync(kFull, etight, src);
             top -= consumed;
+            nodes += taken;
+            ++steps;
             __syncwarp();
 
             const bool act = lane < taken;
@@ -501,7 +504,11 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             __syncwarp();
         }
         if (POOL && nbuf > 0) pool_flush(pool, buf, nbuf, kin, (int)c, flushed, lane);
-        if (!FILL && lane == 0) I.nbr_fwd[c] = found;
+        if (!FILL && lane == 0) {
+            I.nbr_fwd[c] = found;
+            stat_add(I.stats, kStWalkNodes, (unsigned long long)nodes);
+            stat_add(I.stats, kStWalkSteps, (unsigned long long)steps);
+        }
         __syncwarp();
     }
 }

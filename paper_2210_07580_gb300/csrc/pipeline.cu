@@ -30,8 +30,8 @@
 
 namespace gd {
 
-const char* const kStageNames[kStages] = {"bounds", "quantise", "sort",        "compact", "levels", "walk",
-                                          "core",   "core_pack", "merge_order", "merge",   "labels"};
+const char* const kStageNames[kStages] = {"bounds", "quantise",  "sort",        "compact", "levels", "walk",
+                                          "lists",  "core",      "core_pack",   "merge_order", "merge", "labels"};
 
 namespace {
 
@@ -460,6 +460,7 @@ gd_status Run::go() {
         // a larger eps2 changes nothing; clamping keeps the gap sums in range.
         const long long cap = (1ll << 62) - 1;
         p.eps2 = g.eps2 > cap ? cap : g.eps2;
+        p.eps2_yes = g.eps2_yes <= p.eps2 ? p.eps2 : (g.eps2_yes > cap ? cap : g.eps2_yes);
         p.minpts = g.minpts;
         p.ldf = knob(GD_KNOB_MERGE_ORDER, g.d, g.n);
         p.uf_cap = info && info->uf_cap > 0 ? info->uf_cap : kMaxUfRetries;
@@ -818,11 +819,12 @@ gd_status Run::go() {
     auto launch4 = [&]() -> gd_status {
         return phase(3, [&]() -> gd_status {
         RUN_TRY(count_pending());
+        mark(6);
         // the lists: from the pool's runs, or (the pool too small, or none) by
         // a second, filling walk -- the device decides
         RUN_CUDA(launch_pool_scatter(dins, pool, st), "neighbour scatter");
         if (need_fill) RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
-        mark(6);
+        mark(7);
         RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
         return GD_OK;
         }, [&]() -> gd_status {
@@ -845,15 +847,15 @@ gd_status Run::go() {
             }
         }
         if (info && info->want_stats) RUN_CUDA(launch_core_stats(dins, cells, total_cells, st), "core statistics");
-        mark(7);
+        mark(8);
         RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
         RUN_TRY(scan(coreseg, K, coreseg_tiles));
         for (int gi = 0; gi < ng; ++gi)
             RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
-        mark(8);
+        mark(9);
         if (any_ldf) RUN_CUDA(launch_ldf_order(dins, idx, K, cells, total_cells, st), "low-density-first order");
         RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");
-        mark(9);
+        mark(10);
         for (int w = 0; w < 2; ++w) {
             if (w == 1 && all_ldf) break;  // one wave in the low-density-first order
             for (int gi = 0; gi < ng; ++gi) {
@@ -872,11 +874,11 @@ gd_status Run::go() {
             if (w == 0 && !all_ldf)
                 RUN_CUDA(launch_uf_flatten(dins, cells, total_cells, uf_capped, st), "union-find flatten");
         }
-        mark(10);
+        mark(11);
         RUN_CUDA(launch_cluster_ids(dins, cells, total_cells, uf_capped, st), "cluster ids");
         for (int gi = 0; gi < ng; ++gi)
             RUN_CUDA(launch_labels(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "labels");
-        mark(11);
+        mark(12);
         return GD_OK;
         });
     };

@@ -84,7 +84,7 @@ struct MemProvider {
 // events[kStages] at the end; stages that end at a read-back of sizes
 // (bounds, compact, walk) also record events[kStages + 1 + i], i = 0, 1, 2,
 // when their last kernel is issued, so that no stage includes host work.
-constexpr int kStages = 11;
+constexpr int kStages = 12;
 constexpr int kStageEvents = kStages + 4;
 extern const char* const kStageNames[kStages];
 

@@ -14,6 +14,9 @@ LOW = [("merge_budget", 0, 1 << 62, 1), ("merge_lane", 0, 1 << 62, 1), ("merge_s
 HIGH = [("merge_budget", 0, 1 << 62, 64), ("merge_lane", 0, 1 << 62, 256), ("merge_small", 0, 1 << 62, 1024),
         ("core_bands", 0, 1 << 62, 65536), ("fm_blocks", 0, 1 << 62, 152 * 128),
         ("walk_blocks", 0, 1 << 62, 152 * 128), ("core_mode", 0, 1 << 62, 1)]
+# the per-point core count with and without bands, the per-grid one with bands
+POINT_BANDS = [("core_mode", 0, 1 << 62, 0), ("core_bands", 0, 1 << 62, 65536)]
+GRID_BANDS = [("core_mode", 0, 1 << 62, 1), ("core_bands", 0, 1 << 62, 65536)]
 
 
 def test_knob_extremes_give_identical_labels():
@@ -22,13 +25,14 @@ def test_knob_extremes_give_identical_labels():
     jobs = synth.batch_instances(24, seed=5, n_lo=300, n_hi=60000)
     dj = [(torch.from_numpy(X).cuda(), e, m) for X, e, m in jobs]
     res = {}
-    for name, table in (("none", None), ("low", LOW), ("high", HIGH), ("default", "default")):
+    for name, table in (("none", None), ("low", LOW), ("high", HIGH), ("default", "default"),
+                        ("point_bands", POINT_BANDS), ("grid_bands", GRID_BANDS)):
         ctx = Context(0, tuning=table)
         out = ctx.dbscan_batched(dj)
         torch.cuda.synchronize()
         res[name] = [(lab.cpu().numpy(), core.cpu().numpy()) for lab, core in out]
         ctx.close()
-    for name in ("low", "high", "default"):
+    for name in ("low", "high", "default", "point_bands", "grid_bands"):
         for i, ((a, ac), (b, bc)) in enumerate(zip(res["none"], res[name])):
             np.testing.assert_array_equal(ac, bc, err_msg=f"{name} core {i}")
             np.testing.assert_array_equal(a, b, err_msg=f"{name} labels {i}")
