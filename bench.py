@@ -477,40 +477,91 @@ def _replay(srv, jobs, arrivals):
     return res, srv.stats()
 
 
+def _stream(srv, pool, picks, arrivals):
+    """A request stream: request i is pool job picks[i], submitted at
+    arrivals[i] seconds from now.  Results are checked for errors and then
+    dropped (a long stream would not fit in host memory).  Returns the
+    latencies in submission order (seconds) and the server's stats."""
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    futs = []
+    for i, k in enumerate(picks):
+        wait = t0 + arrivals[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        X, e, m = pool[k]
+        futs.append(srv.submit(X, e, m))
+    for f in futs:
+        f.result(timeout=900)
+    st = srv.stats()
+    return srv.latencies(), st
+
+
+def _pcts(lat) -> dict:
+    lat = np.asarray(lat) * 1e3
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2)}
+
+
 def bench_serve(dev, args):
-    """Serving: the same job list through (a) the sequential plain path -- one
+    """Serving: the same jobs through (a) the sequential plain path -- one
     slot, one job per gd_dbscan call, host arrays in and out -- and (b) the
     continuous-batching server (several slots, small jobs coalesced into
-    gd_dbscan_batched).  Throughput with every job queued at once, then
-    p50/p99 latency under one Poisson arrival stream at `load` times the
-    sequential path's throughput.  Each server first runs the list once
-    untimed (resident workspaces)."""
+    gd_dbscan_batched).
+    - Capacity: the job pool queued all at once, three times per path after
+      an untimed pass (resident workspaces); jobs/s of each repeat.
+    - Latency: a Poisson stream of `serve_requests` requests drawn from the
+      pool (seeded) after `serve_warmup` untimed ones, at `load` times the
+      sequential path's measured capacity; p50/p99 over all requests and per
+      third of the stream (their spread), and the mean batch size.
+    - Results: every pool job's labels and core flags from the two paths
+      must be identical."""
     from paper_2210_07580_gb300 import synth
     from paper_2210_07580_gb300.serve import Server
-    jobs = synth.serve_jobs(args.serve_jobs, seed=11)
-    npts = int(sum(len(X) for X, _, _ in jobs))
-    out = {"workload": f"{len(jobs)} jobs: n log-uniform in [1e3, 1e7], d in 2..7, eps in [200, 2000], "
+    pool = synth.serve_jobs(args.serve_jobs, seed=11)
+    npts = int(sum(len(X) for X, _, _ in pool))
+    rng = np.random.default_rng(13)
+    nreq, nwarm = args.serve_requests, args.serve_warmup
+    picks = rng.integers(0, len(pool), size=nreq + nwarm)
+    out = {"workload": f"pool of {len(pool)} jobs: n log-uniform in [1e3, 1e7], d in 2..7, eps in [200, 2000], "
                        f"MinPts in {{5,10,50,100}}, blobs + 5% noise; host int32 arrays in, labels + core flags out",
-           "jobs": len(jobs), "points": npts, "load": args.serve_load}
+           "jobs": len(pool), "points": npts, "load": args.serve_load,
+           "stream": f"{nreq} Poisson requests drawn from the pool after {nwarm} warm-up requests"}
     configs = (("sequential", dict(slots=1, small_job_points=0)),
                ("served", dict(slots=args.serve_slots, small_job_points=200_000)))
     results = {}
+    rate = None
     for name, kw in configs:
         with Server(device=dev.index or 0, **kw) as srv:
-            _replay(srv, jobs, None)  # warm-up
-            res, st = _replay(srv, jobs, None)
+            # warm-up: two passes, so that every slot's workspace has grown to
+            # the jobs it will see (growth reallocates, once)
+            res, _ = _replay(srv, pool, None)
+            _replay(srv, pool, None)
             results[name] = res
-            out[name] = {"slots": kw["slots"], "jobs_per_s": round(st["jobs_per_s"], 2),
-                         "saturated_p50_ms": round(st["p50_ms"], 2), "saturated_p99_ms": round(st["p99_ms"], 2),
-                         "mean_batch": round(st["mean_batch"], 2)}
-            if name == "sequential":
-                rate = args.serve_load * st["jobs_per_s"]
-                arrivals = synth.poisson_arrivals(len(jobs), rate, seed=12)
+            caps, batch = [], []
+            for _ in range(3):
+                _, st = _replay(srv, pool, None)
+                caps.append(round(st["jobs_per_s"], 2))
+                batch.append(st["mean_batch"])
+            o = {"slots": kw["slots"], "jobs_per_s": round(float(np.mean(caps)), 2), "jobs_per_s_repeats": caps,
+                 "mean_batch": round(float(np.mean(batch)), 2)}
+            if rate is None:
+                rate = args.serve_load * float(np.mean(caps))
+                arrivals = synth.poisson_arrivals(nreq + nwarm, rate, seed=12)
                 out["rate_per_s"] = round(rate, 2)
-            _, st = _replay(srv, jobs, arrivals)
-            out[name].update({"poisson_p50_ms": round(st["p50_ms"], 2), "poisson_p99_ms": round(st["p99_ms"], 2),
-                              "poisson_mean_batch": round(st["mean_batch"], 2)})
-    out["speedup_jobs_per_s"] = round(out["served"]["jobs_per_s"] / out["sequential"]["jobs_per_s"], 2)
+            if nwarm:
+                _stream(srv, pool, picks[:nwarm], arrivals[:nwarm])
+            lat, st = _stream(srv, pool, picks[nwarm:], arrivals[nwarm:] - (arrivals[nwarm - 1] if nwarm else 0.0))
+            thirds = [_pcts(part) for part in np.array_split(lat, 3)]
+            o.update({"poisson_" + k: v for k, v in _pcts(lat).items()})
+            o.update({"poisson_requests": int(len(lat)), "poisson_mean_batch": round(st["mean_batch"], 2),
+                      "poisson_jobs_per_s": round(st["jobs_per_s"], 2),
+                      "poisson_p99_ms_thirds": [t["p99_ms"] for t in thirds],
+                      "poisson_p50_ms_thirds": [t["p50_ms"] for t in thirds]})
+            out[name] = o
+            del res
+    seq, srv_ = out["sequential"]["jobs_per_s_repeats"], out["served"]["jobs_per_s_repeats"]
+    out["speedup_jobs_per_s"] = round(out["served"]["jobs_per_s"] / out["sequential"]["jobs_per_s"], 3)
+    out["speedup_range"] = [round(min(srv_) / max(seq), 3), round(max(srv_) / min(seq), 3)]
     out["labels_identical"] = bool(all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
                                        for a, b in zip(results["sequential"], results["served"])))
     return out
@@ -705,8 +756,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-jobs", type=int, default=48)
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--serve-load", type=float, default=0.8,
+    ap.add_argument("--serve-load", type=float, default=0.7,
                     help="Poisson arrival rate as a fraction of the sequential path's jobs/s")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="timed requests of the Poisson stream")
+    ap.add_argument("--serve-warmup", type=int, default=100, help="untimed requests before them")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

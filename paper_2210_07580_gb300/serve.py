@@ -307,8 +307,10 @@ class Server:
             self.done = []
 
     def latencies(self):
+        """Latencies (seconds) of the finished jobs, in submission order."""
         with self.cv:
-            return np.array([j.t_done - j.t_submit for j in self.done])
+            jobs = sorted(self.done, key=lambda j: j.t_submit)
+        return np.array([j.t_done - j.t_submit for j in jobs])
 
     def stats(self) -> dict:
         lat = self.latencies()
