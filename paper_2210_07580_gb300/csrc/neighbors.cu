@@ -230,14 +230,13 @@ constexpr int kTight = 0x10;
 
 // Narrow the key-sorted range [*lo, *hi) to keys in [vlo, vhi]: the two
 // bisections run side by side, so their loads overlap.
-__device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* lo, int* hi, long long vlo,
-                                             long long vhi) {
+__device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* lo, int* hi, int vlo, int vhi) {
     const int a = *lo, b = *hi;
     int l1 = a, h1 = b, l2 = a, h2 = b;  // first key >= vlo; first key > vhi
     while (l1 < h1 || l2 < h2) {
         const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1;
-        const long long k1 = l1 < h1 ? (long long)__ldg(key + m1) : 0;
-        const long long k2 = l2 < h2 ? (long long)__ldg(key + m2) : 0;
+        const int k1 = l1 < h1 ? __ldg(key + m1) : 0;
+        const int k2 = l2 < h2 ? __ldg(key + m2) : 0;
         if (l1 < h1) {
             if (k1 < vlo) l1 = m1 + 1;
             else h1 = m1;
@@ -275,7 +274,7 @@ struct WalkShared {
     int hi[kWalkWarps][kWalkStack];
     long long part[kWalkWarps][kWalkStack];
     signed char lvl[kWalkWarps][kWalkStack];
-    long long qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];    // query point box
+    int qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];  // query point box
     int g[kWalkWarps][kMaxD];                                    // query identifier
     // squared gap in dimension j between the query's point box and the cell
     // at key offset delta = key - g_j, index delta + kMaxR (saturated at 2^62,
@@ -343,6 +342,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         const long long c = q - cur.lo;
         const int d = I.p.d;
         const long long r = I.p.r, s = I.p.s, eps2 = I.p.eps2;
+        const int ri = (int)r;  // <= kMaxR
         if (lane < d) {
             const int gi = I.cell_coord[c * d + lane];
             const long long g = gi, ql = I.pbox[c * 2 * d + lane], qh = I.pbox[c * 2 * d + d + lane];
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             int a0 = 0, b0 = I.small[kSmLevelCount];
             int dlo, dhi;
             budget_window(sh.gap2[w][0], eps2, r, true, &dlo, &dhi);
-            narrow_range(I.lv_key[0], &a0, &b0, (long long)sh.g[w][0] + dlo, (long long)sh.g[w][0] + dhi);
+            narrow_range(I.lv_key[0], &a0, &b0, sh.g[w][0] + dlo, sh.g[w][0] + dhi);
             if (b0 > a0) {
                 if (lane == 0) {
                     slo[0] = a0;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     chi = __ldg(I.lv_cb[J] + u + 1);
                 }
                 const int dl = key - sh.g[w][J];
-                if (dl >= -r && dl <= r) {
+                if (dl >= -ri && dl <= ri) {
                     off = my_part + sh.gap2[w][J][dl + kMaxR];
                     ok = off <= eps2;
                     tight = my_tight && dl == 0;
@@ -444,14 +444,17 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 // leaf: the two grids' boxes (a forward neighbour u >= c)
                 if (ok) {
                     const int* ub = pbox + (long long)u * 2 * d;
+                    // coordinates span less than 2^31 per dimension (the
+                    // range check), so each gap fits in 32 bits; its square
+                    // and the sum take 64
                     long long g2 = 0;
                     for (int t = 0; t < d; ++t) {
-                        const long long bl = __ldg(ub + t), bh = __ldg(ub + d + t);
-                        const long long ql = sh.qlo[w][t], qh = sh.qhi[w][t];
-                        long long gg = 0;
+                        const int bl = __ldg(ub + t), bh = __ldg(ub + d + t);
+                        const int ql = sh.qlo[w][t], qh = sh.qhi[w][t];
+                        int gg = 0;
                         if (bl > qh) gg = bl - qh;
                         else if (ql > bh) gg = ql - bh;
-                        g2 += gg * gg;
+                        g2 += (long long)gg * gg;
                     }
                     ok = g2 <= eps2;
                 }
@@ -487,7 +490,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     // gap still fits in what the path leaves of eps^2
                     int dlo, dhi;
                     budget_window(sh.gap2[w][J + 1], eps2 - off, r, tight, &dlo, &dhi);
-                    const long long g1 = sh.g[w][J + 1];
+                    const int g1 = sh.g[w][J + 1];
                     narrow_range(I.lv_key[J + 1], &clo, &chi, g1 + dlo, g1 + dhi);
                     ok = chi > clo;
                 }
