@@ -254,8 +254,8 @@ __device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* l
 // gap2, index delta + kMaxR, non-decreasing in |delta| on each side, 0 at
 // delta = 0) is within `rem`; lo >= 0 when `fwd` (a range on the query's own
 // path).  rem >= 0, so delta = 0 always qualifies.
-__device__ __forceinline__ void budget_window(const long long* gap2, long long rem, long long r, bool fwd, int* lo,
-                                              int* hi) {
+template <typename T>
+__device__ __forceinline__ void budget_window(const T* gap2, T rem, int r, bool fwd, int* lo, int* hi) {
     int h = 0, l = 0;
 #pragma unroll
     for (int t = 1; t <= kMaxR; ++t)
@@ -269,17 +269,21 @@ __device__ __forceinline__ void budget_window(const long long* gap2, long long r
     *hi = h;
 }
 
+// Offsets (partial sums of squared gaps) are 64-bit in general, 32-bit when
+// the batch's eps2 < 2^31: the table entries are then saturated at eps2 + 1
+// and a pushed path's offset is at most eps2, so no sum exceeds 2^32 - 1.
+template <typename T>
 struct WalkShared {
     int lo[kWalkWarps][kWalkStack];
     int hi[kWalkWarps][kWalkStack];
-    long long part[kWalkWarps][kWalkStack];
+    T part[kWalkWarps][kWalkStack];
     signed char lvl[kWalkWarps][kWalkStack];
     int qlo[kWalkWarps][kMaxD], qhi[kWalkWarps][kMaxD];  // query point box
     int g[kWalkWarps][kMaxD];                                    // query identifier
     // squared gap in dimension j between the query's point box and the cell
-    // at key offset delta = key - g_j, index delta + kMaxR (saturated at 2^62,
-    // which exceeds every eps2)
-    long long gap2[kWalkWarps][kMaxD][2 * kMaxR + 1];
+    // at key offset delta = key - g_j, index delta + kMaxR (saturated above
+    // eps2: at 2^62, or at eps2 + 1 for 32-bit offsets)
+    T gap2[kWalkWarps][kMaxD][2 * kMaxR + 1];
     int buf[kWalkWarps][64];  // kWalkPool: neighbours not yet flushed
 };
 
@@ -318,16 +322,16 @@ __device__ __forceinline__ bool pool_fits(const WalkPool& pool) {
     return (long long)(t & ((1ull << kPoolBits) - 1)) <= pool.cap && (long long)(t >> kPoolBits) <= pool.seg_cap;
 }
 
-template <int MODE>
+template <int MODE, typename T>
 __global__ void __launch_bounds__(32 * kWalkWarps)
     walk_kernel(const Inst* __restrict__ ins, Flat f, long long total, WalkPool pool) {
     total = flat_total(f);
     constexpr bool FILL = MODE == kWalkFill, POOL = MODE == kWalkPool;
-    __shared__ WalkShared sh;
+    __shared__ WalkShared<T> sh;
     const int lane = lane_id(), w = threadIdx.x >> 5;
     int* const slo = sh.lo[w];
     int* const shi = sh.hi[w];
-    long long* const spart = sh.part[w];
+    T* const spart = sh.part[w];
     signed char* const slvl = sh.lvl[w];
     const long long warps = (long long)gridDim.x * kWalkWarps;
     const unsigned lt = lanemask_lt();
@@ -341,8 +345,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         if (FILL && lists_dropped(I)) continue;
         const long long c = q - cur.lo;
         const int d = I.p.d;
-        const long long r = I.p.r, s = I.p.s, eps2 = I.p.eps2;
+        const long long r = I.p.r, s = I.p.s;
         const int ri = (int)r;  // <= kMaxR
+        const T eps2 = (T)I.p.eps2;  // < 2^31 when T is 32-bit
+        const long long sat = sizeof(T) == 8 ? (1ll << 62) : I.p.eps2 + 1;
         if (lane < d) {
             const int gi = I.cell_coord[c * d + lane];
             const long long g = gi, ql = I.pbox[c * 2 * d + lane], qh = I.pbox[c * 2 * d + d + lane];
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 long long gap = 0;
                 if (dl > 0) gap = cl + dl * s - qh;
                 else if (dl < 0) gap = ql - (cl + dl * s + s - 1);
-                sh.gap2[w][lane][t] = gap >= (1ll << 31) ? (1ll << 62) : gap * gap;
+                sh.gap2[w][lane][t] = (T)(gap >= (1ll << 31) ? sat : min(gap * gap, sat));
             }
         }
         __syncwarp();
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             // path), narrowed to the offsets whose gap alone is within eps
             int a0 = 0, b0 = I.small[kSmLevelCount];
             int dlo, dhi;
-            budget_window(sh.gap2[w][0], eps2, r, true, &dlo, &dhi);
+            budget_window<T>(sh.gap2[w][0], eps2, ri, true, &dlo, &dhi);
             narrow_range(I.lv_key[0], &a0, &b0, sh.g[w][0] + dlo, sh.g[w][0] + dhi);
             if (b0 > a0) {
                 if (lane == 0) {
@@ -394,7 +400,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const int ev = e >= 0 ? slvl[e] : -1;
             const bool in_group = e >= 0 && (ev & (kTight - 1)) == J;
             int elo = 0, sz = 0, etight = 0;
-            long long epart = 0;
+            T epart = 0;
             if (in_group) {
                 elo = slo[e];
                 sz = min(shi[e] - elo, 64);
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const int src = ei < 0 ? 0 : ei;
             const int my_lo = __shfl_sync(kFull, elo, src);
             const int my_start = __shfl_sync(kFull, start, src);
-            const long long my_part = __shfl_sync(kFull, epart, src);
+            const T my_part = __shfl_sync(kFull, epart, src);
             const int my_tight = __shfl_sync(kFull, etight, src);
             top -= consumed;
             nodes += taken;
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const bool act = lane < taken;
             const int u = my_lo + (lane - my_start);
             bool ok = false, tight = false;
-            long long off = 0;
+            T off = 0;
             // the node's child range is loaded with its key (one round trip)
             int clo = 0, chi = 0;
             if (act) {
@@ -489,7 +495,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     // on the query's own path, narrowed to the key offsets whose
                     // gap still fits in what the path leaves of eps^2
                     int dlo, dhi;
-                    budget_window(sh.gap2[w][J + 1], eps2 - off, r, tight, &dlo, &dhi);
+                    budget_window<T>(sh.gap2[w][J + 1], eps2 - off, ri, tight, &dlo, &dhi);
                     const int g1 = sh.g[w][J + 1];
                     narrow_range(I.lv_key[J + 1], &clo, &chi, g1 + dlo, g1 + dhi);
                     ok = chi > clo;
@@ -517,16 +523,21 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
 }
 
 cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
-                        cudaStream_t st) {
+                        bool small_eps, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     long long b = (total + kWalkWarps - 1) / kWalkWarps;
     if (b > blocks) b = blocks;
-    if (mode == kWalkFill)
-        walk_kernel<kWalkFill><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
-    else if (mode == kWalkPool)
-        walk_kernel<kWalkPool><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
-    else
-        walk_kernel<kWalkCount><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool);
+#define GD_WALK(M, T) walk_kernel<M, T><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool)
+    if (small_eps) {
+        if (mode == kWalkFill) GD_WALK(kWalkFill, unsigned);
+        else if (mode == kWalkPool) GD_WALK(kWalkPool, unsigned);
+        else GD_WALK(kWalkCount, unsigned);
+    } else {
+        if (mode == kWalkFill) GD_WALK(kWalkFill, long long);
+        else if (mode == kWalkPool) GD_WALK(kWalkPool, long long);
+        else GD_WALK(kWalkCount, long long);
+    }
+#undef GD_WALK
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

@@ -448,6 +448,7 @@ gd_status Run::go() {
     long long total_pts = 0;
     int dmax = 1;
     bool any_ldf = false, all_ldf = true;
+    bool small_eps = true;  // every instance's eps2 < 2^31: the walk's offsets fit 32 bits
     for (int k = 0; k < K; ++k) {
         const gd_instance& g = in[k];
         HI& h = hi[k];
@@ -483,6 +484,7 @@ gd_status Run::go() {
         if (g.d > dmax) dmax = g.d;
         if (p.ldf) any_ldf = true;
         else all_ldf = false;
+        if (p.eps2 >= (1ll << 31)) small_eps = false;
         if (queued) {
             const ShapePlan* sp = pc->find(g.n, g.d, p.eps2);
             if (!sp || sp->key_bits <= 0) {
@@ -727,7 +729,7 @@ gd_status Run::go() {
         }
         RUN_CUDA(launch_level_write(dins, cells, total_cells, st), "level write");
         mark(5);
-        RUN_CUDA(launch_walk(dins, cells, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, st),
+        RUN_CUDA(launch_walk(dins, cells, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, small_eps, st),
                  "walk");
         RUN_CUDA(launch_nbr_total(dins, cells, total_cells, st), "list lengths");
         RUN_TRY(scan(nseg, K, nseg_tiles));
@@ -823,7 +825,8 @@ gd_status Run::go() {
         // the lists: from the pool's runs, or (the pool too small, or none) by
         // a second, filling walk -- the device decides
         RUN_CUDA(launch_pool_scatter(dins, pool, st), "neighbour scatter");
-        if (need_fill) RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, st), "walk fill");
+        if (need_fill)
+            RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, small_eps, st), "walk fill");
         mark(7);
         RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
         return GD_OK;

@@ -14,12 +14,14 @@ from test_gpu_parity import refined_neighbours  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("d,eps", [(2, 700), (4, 900), (6, 1500), (7, 1800)])
-def test_sparse_lists_and_labels(d, eps):
+# scale 1000 puts eps2 above 2^31, where the query's offsets take 64 bits
+@pytest.mark.parametrize("d,eps,scale", [(2, 700, 1), (4, 900, 1), (6, 1500, 1), (7, 1800, 1), (4, 900, 1000),
+                                         (6, 1500, 1000)])
+def test_sparse_lists_and_labels(d, eps, scale):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    X = synth.blobs(12000, d, k=4, sigma=2500.0, noise=0.05, seed=100 + d)
-    eps2, minpts = eps * eps, 5
+    X = synth.blobs(12000, d, k=4, sigma=2500.0, noise=0.05, seed=100 + d) * np.int32(scale)
+    eps2, minpts = (eps * scale) ** 2, 5
     ctx = Context(0)
     Xd = torch.from_numpy(X).cuda()
     lab, core = ctx.dbscan(Xd, eps2, minpts)
