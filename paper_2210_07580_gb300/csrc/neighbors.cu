@@ -232,7 +232,29 @@ constexpr int kTight = 0x10;
 // bisections run side by side, so their loads overlap.
 __device__ __forceinline__ void narrow_range(const int* __restrict__ key, int* lo, int* hi, int vlo, int vhi) {
     const int a = *lo, b = *hi;
-    int l1 = a, h1 = b, l2 = a, h2 = b;  // first key >= vlo; first key > vhi
+    if (a >= b) return;
+    // The keys are distinct increasing integers, so key[a + t] >= key[a] + t
+    // and key[b - 1 - t] <= key[b - 1] - t: the two end keys bound where each
+    // answer can lie, to within the key gaps (dense child ranges leave a few
+    // candidates, sparse ones the whole range).
+    const int ka = __ldg(key + a), kb = __ldg(key + b - 1);
+    int l1, h1, l2, h2;  // first key >= vlo in [l1, h1]; first key > vhi in [l2, h2]
+    if (vlo <= ka) {
+        l1 = h1 = a;
+    } else if (vlo > kb) {
+        l1 = h1 = b;
+    } else {
+        l1 = max(a + 1, b - 1 - (kb - vlo));
+        h1 = min(b - 1, a + (vlo - ka));
+    }
+    if (vhi < ka) {
+        l2 = h2 = a;
+    } else if (vhi >= kb) {
+        l2 = h2 = b;
+    } else {
+        l2 = max(a + 1, b - (kb - vhi));
+        h2 = min(b - 1, a + (vhi - ka) + 1);
+    }
     while (l1 < h1 || l2 < h2) {
         const int m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1;
         const int k1 = l1 < h1 ? __ldg(key + m1) : 0;
