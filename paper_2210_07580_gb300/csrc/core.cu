@@ -111,6 +111,31 @@ cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaS
     return cudaGetLastError();
 }
 
+// After the scan of nf_start: the points counted one by one, listed by their
+// index in grid order (a thread per grid), so that a warp of
+// core_point_kernel finds its point and grid with two loads.
+__global__ void nf_index_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+    total = flat_total(f);
+    FlatCursor cur;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = i - cur.lo;
+        const int C = I.small[kSmCells];
+        const int lo = I.nf_start[c], hi = c + 1 < C ? I.nf_start[c + 1] : I.small[kSmNonfull];
+        const int b = I.cell_start[c];
+        for (int k = 0; k < hi - lo; ++k) I.nf_pts[lo + k] = b + k;
+    }
+}
+
+cudaError_t launch_nf_index(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    nf_index_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
+    GD_COUNT_LAUNCH();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
     nonfull_count_kernel<<<blocks_for(total), 256, 0, st>>>(ins, cells, total);
@@ -210,22 +235,11 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
         const Params& p = I.p;
         const long long eps2 = p.eps2;
         const int minpts = p.minpts;
-        const int C = I.small[kSmCells];
-        const int* nf_start = I.nf_start;
         const int* cell_start = I.cell_start;
         const int* pbox = I.pbox;
         const int* Xs = I.Xs;
-        // grid of flat position lw: last c with nf_start[c] <= lw
-        int lo = 0, hi = C - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (nf_start[mid] <= lw)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const int c = lo;
-        const long long i = (long long)cell_start[c] + (lw - nf_start[c]);
+        const long long i = I.nf_pts[lw];
+        const int c = I.pt_cell[i];
         long long x[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];

@@ -168,6 +168,7 @@ struct Inst {
     int* nbr_bwd;
     long long nbr_cap;  // entries the instance's list buffer holds (and its hard-pair buffer)
     int* nf_start;
+    int* nf_pts;  // [points counted one by one] their index in grid order (shares lv_E's space)
     int* core_start;
     int* bbox;
     int* ldf_grid;  // low-density-first order: the grid at each slot (core grids by core count first)
@@ -463,6 +464,7 @@ cudaError_t launch_nbr_total(const Inst* ins, Flat cells, long long total, cudaS
 
 // Core points (core.cu).
 cudaError_t launch_core_full(const Inst* ins, Flat cells, long long total, cudaStream_t st);
+cudaError_t launch_nf_index(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 cudaError_t launch_nonfull_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Statistics only: non-full points and the rows a per-grid count would stage.
 cudaError_t launch_core_stats(const Inst* ins, Flat cells, long long total, cudaStream_t st);

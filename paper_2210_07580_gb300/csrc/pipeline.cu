@@ -135,6 +135,7 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     }
     I.lv_E = (int*)take((size_t)d * (N + 1) * 4);
     I.lv_L = (int*)take(N * 4);
+    I.nf_pts = I.lv_E;  // the level scratch is free once the levels are written
     I.nbr_start = (int*)take((N + 1) * 4);
     I.nbr_fwd = (int*)take(N * 4);
     I.nbr_bwd = (int*)take(N * 4);
@@ -839,6 +840,9 @@ gd_status Run::go() {
         if (any_point_mode) {
             RUN_CUDA(launch_nonfull_count(dins, cells, total_cells, st), "non-full grids");
             RUN_TRY(scan(nfseg, K, nfseg_tiles));
+            for (int gi = 0; gi < ng; ++gi)
+                if (!knob(GD_KNOB_CORE_MODE, dgroups[gi], gn[gi]))
+                    RUN_CUDA(launch_nf_index(dins, g_cells[gi], g_cells_tot[gi], st), "non-full points");
         }
         for (int gi = 0; gi < ng; ++gi) {
             const int d = dgroups[gi], bands = knob(GD_KNOB_CORE_BANDS, d, gn[gi]);
