@@ -413,11 +413,21 @@ __global__ void __launch_bounds__(256, 4)  // latency-bound: four blocks per SM 
         const int t_begin = I.nbr_start[c];
         const int t_end = ldf ? I.nbr_start[c + 1] : t_begin + I.nbr_fwd[c];
         const int hard_base = wave == 0 ? 0 : I.small[kSmHard0];
+        // list entries and their core counts are loaded ahead (the entries two
+        // chunks, the counts one chunk before use), so that their latency
+        // overlaps the current chunk's union-find lookups
+        const int* nbr = I.nbr;
+        auto entry = [&](int t) { return t < t_end ? __ldg(nbr + t) : c; };
+        auto cores = [&](int j) { return j != c ? __ldg(core_start + j + 1) - __ldg(core_start + j) : 0; };
+        int j_next = entry(t_begin + lane);
+        int m_next = cores(j_next);
+        int j_after = entry(t_begin + 32 + lane);
         for (int t0 = t_begin; t0 < t_end; t0 += 32) {
             // ---- the lane's candidate pair (c, j2)
-            const int t = t0 + lane;
-            const int j2 = t < t_end ? I.nbr[t] : c;
-            const int mj = j2 != c ? core_start[j2 + 1] - core_start[j2] : 0;
+            const int j2 = j_next, mj = m_next;
+            j_next = j_after;
+            m_next = cores(j_after);
+            j_after = entry(t0 + 64 + lane);
             bool keep;
             if (ldf) {
                 keep = mj > 0 && (mc < mj || (mc == mj && c < j2));
