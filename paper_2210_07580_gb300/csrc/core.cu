@@ -149,18 +149,22 @@ struct BoxDist {
 
 // Squared distances from x to the nearest and farthest corner of grid cc's
 // point box (which holds every point of the grid).
+// Coordinates span less than 2^31 per dimension and a box's lower end lies
+// within the data, so the gap and x - lo fit in 32 bits; a large grid's box
+// is its identifier range, whose upper end may lie beyond the data, so
+// hi - x takes 64.
 template <int D>
-__device__ __forceinline__ BoxDist box_dist(const long long* x, const int* __restrict__ pbox, int cc) {
+__device__ __forceinline__ BoxDist box_dist(const int* x, const int* __restrict__ pbox, int cc) {
     BoxDist r{0, 0};
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const long long blo = pbox[(long long)cc * 2 * D + j];
-        const long long bhi = pbox[(long long)cc * 2 * D + D + j];
-        long long g = 0;
+        const int blo = __ldg(pbox + (long long)cc * 2 * D + j);
+        const int bhi = __ldg(pbox + (long long)cc * 2 * D + D + j);
+        int g = 0;
         if (blo > x[j]) g = blo - x[j];
         else if (x[j] > bhi) g = x[j] - bhi;
-        r.mind += g * g;
-        const long long a = x[j] - blo, b = bhi - x[j];
+        r.mind += (long long)g * g;
+        const long long a = x[j] - blo, b = (long long)bhi - x[j];
         const long long f = a > b ? a : b;
         r.maxd += f * f;
     }
@@ -172,7 +176,7 @@ __device__ __forceinline__ BoxDist box_dist(const long long* x, const int* __res
 // the chunk's t-th grid as (first row st, rows sz; sz = 0 for a grid that is
 // not straddling).  Adds the hits to cnt and stops once it reaches MinPts.
 template <int D, int DP>
-__device__ __forceinline__ void count_straddling(const int* __restrict__ Xs, const long long* x, int st, int sz,
+__device__ __forceinline__ void count_straddling(const int* __restrict__ Xs, const int* x, int st, int sz,
                                                  long long eps2, int minpts, int& cnt, unsigned& ndist) {
     const int lane = lane_id();
     const int incl = warp_inclusive_scan(sz);
@@ -196,8 +200,8 @@ __device__ __forceinline__ void count_straddling(const int* __restrict__ Xs, con
             long long dd = 0;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const long long t = (long long)Xs[qi * DP + j] - x[j];
-                dd += t * t;
+                const int t = Xs[qi * DP + j] - x[j];  // both points in the data: fits 32 bits
+                dd += (long long)t * t;
             }
             hit = dd <= eps2;
         }
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
         const int* Xs = I.Xs;
         const long long i = I.nf_pts[lw];
         const int c = I.pt_cell[i];
-        long long x[D];
+        int x[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) x[j] = Xs[i * DP + j];
         int cnt = 0;
@@ -248,12 +252,15 @@ __global__ void __launch_bounds__(256) core_point_kernel(const Inst* __restrict_
         unsigned ndist = 0;  // statistics: distances this warp evaluated
         const int t_begin = I.nbr_start[c], t_end = I.nbr_start[c + 1];
         const int* nbr = I.nbr;
-        // whole grids, and the size of the straddling ones
+        // whole grids, and the size of the straddling ones (each chunk's grid
+        // ids loaded one chunk ahead)
+        int cc_next = t_begin + lane < t_end ? __ldg(nbr + t_begin + lane) : -1;
         for (int t0 = t_begin; t0 < t_end && cnt < minpts; t0 += 32) {
             int whole = 0, part = 0;
-            if (t0 + lane < t_end) {
-                const int cc = nbr[t0 + lane];
-                const int a = cell_start[cc], b = cell_start[cc + 1];
+            const int cc = cc_next;
+            cc_next = t0 + 32 + lane < t_end ? __ldg(nbr + t0 + 32 + lane) : -1;
+            if (cc >= 0) {
+                const int a = __ldg(cell_start + cc), b = __ldg(cell_start + cc + 1);
                 const BoxDist bd = box_dist<D>(x, pbox, cc);
                 if (bd.maxd <= eps2) whole = b - a;
                 else if (bd.mind <= eps2) part = b - a;
@@ -363,8 +370,9 @@ __global__ void __launch_bounds__(32 * kCoreWarps)
                         long long maxd = 0;
 #pragma unroll
                         for (int j = 0; j < D; ++j) {
-                            const long long x = sx[wib][p][j];
-                            const long long a = x - sbox[wib][j][lane], bb = sbox[wib][D + j][lane] - x;
+                            // x - lo fits 32 bits; hi - x takes 64 (box_dist)
+                            const int x = sx[wib][p][j];
+                            const long long a = x - sbox[wib][j][lane], bb = (long long)sbox[wib][D + j][lane] - x;
                             const long long fm = a > bb ? a : bb;
                             maxd += fm * fm;
                         }
@@ -387,7 +395,7 @@ __global__ void __launch_bounds__(32 * kCoreWarps)
                     const int sz0 = load_entries(t0, &st0);
                     for (unsigned pp = pend; pp; pp &= pp - 1) {
                         const int p = __ffs(pp) - 1;
-                        long long x[D];
+                        int x[D];
 #pragma unroll
                         for (int j = 0; j < D; ++j) x[j] = sx[wib][p][j];
                         int cp = __shfl_sync(kFull, cnt, p);
@@ -396,12 +404,12 @@ __global__ void __launch_bounds__(32 * kCoreWarps)
                             long long mind = 0, maxd = 0;
 #pragma unroll
                             for (int j = 0; j < D; ++j) {
-                                const long long l = sbox[wib][j][lane], h = sbox[wib][D + j][lane];
-                                long long g = 0;
+                                const int l = sbox[wib][j][lane], h = sbox[wib][D + j][lane];
+                                int g = 0;
                                 if (l > x[j]) g = l - x[j];
                                 else if (x[j] > h) g = x[j] - h;
-                                mind += g * g;
-                                const long long a = x[j] - l, bb = h - x[j];
+                                mind += (long long)g * g;
+                                const long long a = x[j] - l, bb = (long long)h - x[j];
                                 const long long fm = a > bb ? a : bb;
                                 maxd += fm * fm;
                             }
@@ -428,8 +436,8 @@ __global__ void __launch_bounds__(32 * kCoreWarps)
                                 long long dd = 0;
 #pragma unroll
                                 for (int j = 0; j < D; ++j) {
-                                    const long long t = (long long)Xs[qi * DP + j] - x[j];
-                                    dd += t * t;
+                                    const int t = Xs[qi * DP + j] - x[j];
+                                    dd += (long long)t * t;
                                 }
                                 hit = dd <= eps2;
                             }
