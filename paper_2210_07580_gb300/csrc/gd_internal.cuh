@@ -161,7 +161,8 @@ struct Inst {
     // Neighbour lists: list(c) holds the grids g' >= c the walk found from c
     // (forward part, nbr_fwd[c] entries) followed by the grids g < c whose
     // walks found c (backward part); nbr_bwd counts the backward entries,
-    // then serves as the cursor that places them.
+    // then (from the list check on) holds the absolute position of the next
+    // backward entry of c.
     int* nbr_start;
     int* nbr;
     int* nbr_fwd;

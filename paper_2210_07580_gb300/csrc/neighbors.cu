@@ -324,11 +324,12 @@ __device__ __forceinline__ void pool_flush(const WalkPool& pool, const int* buf,
 }
 
 // The backward entry c in the list of grid u > c (fill mode and the pool
-// scatter): after the forward part, at the next free slot.  Writes stay
-// inside the list buffer whatever the counts say.
+// scatter): after the forward part, at the next free slot (nbr_bwd[u] holds
+// that slot's absolute position from the list check on: one atomic, no
+// other lookup).  Writes stay inside the list buffer whatever the counts say.
 __device__ __forceinline__ void put_backward(const Inst& I, int u, int c) {
-    const long long at = (long long)I.nbr_start[u] + I.nbr_fwd[u] + atomicAdd(I.nbr_bwd + u, 1);
-    if (at < I.nbr_cap) I.nbr[at] = c;
+    const long long at = atomicAdd(I.nbr_bwd + u, 1);
+    if (at >= 0 && at < I.nbr_cap) I.nbr[at] = c;
 }
 
 // Whether the neighbour lists of an instance were given up (see nbr_check).
@@ -599,14 +600,17 @@ __global__ void nbr_check_kernel(const Inst* __restrict__ ins, Flat f, long long
     GD_FOR_FLAT(i, total) {
         cur.seek(f, i);
         const Inst& I = ins[f.idx[cur.k]];
-        if ((long long)(unsigned)I.small[kSmNnbr] <= I.nbr_cap) continue;
         const long long c = i - cur.lo;
-        I.nbr_start[c] = 0;
-        I.nbr_fwd[c] = 0;
-        if (c == 0) {
-            I.nbr_start[I.small[kSmCells]] = 0;
-            set_status(I, kDevOverflow);
+        if ((long long)(unsigned)I.small[kSmNnbr] > I.nbr_cap) {
+            I.nbr_start[c] = 0;
+            I.nbr_fwd[c] = 0;
+            if (c == 0) {
+                I.nbr_start[I.small[kSmCells]] = 0;
+                set_status(I, kDevOverflow);
+            }
         }
+        // the cursor that places the backward entries: their first position
+        I.nbr_bwd[c] = I.nbr_start[c] + I.nbr_fwd[c];
     }
 }
 
@@ -627,7 +631,6 @@ __global__ void nbr_total_kernel(const Inst* __restrict__ ins, Flat f, long long
         const Inst& I = ins[f.idx[cur.k]];
         const long long c = i - cur.lo;
         I.nbr_start[c] = I.nbr_fwd[c] + I.nbr_bwd[c];
-        I.nbr_bwd[c] = 0;
     }
 }
 
