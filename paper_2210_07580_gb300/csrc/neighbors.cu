@@ -454,19 +454,28 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
             const int u = my_lo + (lane - my_start);
             bool ok = false, tight = false;
             T off = 0;
-            // the node's child range is loaded with its key (one round trip)
+            // Every range on the stack was narrowed to the keys whose gap fits
+            // the budget its path left (the budget windows), so on consistent
+            // data each node passes its key test: a leaf needs only its box
+            // test.  An inner node needs its offset (for its children's
+            // window), loaded with its child range (one round trip); its key
+            // is still checked against the window, which keeps the table
+            // index in bounds when the levels are inconsistent (a run whose
+            // key layout did not fit its plan, discarded and run again).
             int clo = 0, chi = 0;
             if (act) {
-                const int key = __ldg(I.lv_key[J] + u);
                 if (J < d - 1) {
+                    const int key = __ldg(I.lv_key[J] + u);
                     clo = __ldg(I.lv_cb[J] + u);
                     chi = __ldg(I.lv_cb[J] + u + 1);
-                }
-                const int dl = key - sh.g[w][J];
-                if (dl >= -ri && dl <= ri) {
-                    off = my_part + sh.gap2[w][J][dl + kMaxR];
-                    ok = off <= eps2;
-                    tight = my_tight && dl == 0;
+                    const int dl = key - sh.g[w][J];
+                    if (dl >= -ri && dl <= ri) {
+                        off = my_part + sh.gap2[w][J][dl + kMaxR];
+                        ok = off <= eps2;
+                        tight = my_tight && dl == 0;
+                    }
+                } else {
+                    ok = true;
                 }
             }
             if (J == d - 1) {
