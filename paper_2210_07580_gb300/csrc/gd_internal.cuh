@@ -452,7 +452,7 @@ struct WalkPool {
 };
 enum WalkMode { kWalkCount = 0, kWalkFill = 1, kWalkPool = 2 };
 cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
-                        bool small_eps, cudaStream_t st);
+                        bool small_eps, int d, cudaStream_t st);
 // The pool's runs into the lists (nothing when the pool overflowed; the
 // filling walk, kWalkFill, runs only then -- or always without a pool).
 cudaError_t launch_pool_scatter(const Inst* ins, WalkPool pool, cudaStream_t st);

@@ -345,7 +345,7 @@ __device__ __forceinline__ bool pool_fits(const WalkPool& pool) {
     return (long long)(t & ((1ull << kPoolBits) - 1)) <= pool.cap && (long long)(t >> kPoolBits) <= pool.seg_cap;
 }
 
-template <int MODE, typename T>
+template <int MODE, typename T, int D>
 __global__ void __launch_bounds__(32 * kWalkWarps)
     walk_kernel(const Inst* __restrict__ ins, Flat f, long long total, WalkPool pool) {
     total = flat_total(f);
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
         const Inst& I = ins[kin];
         if (FILL && lists_dropped(I)) continue;
         const long long c = q - cur.lo;
-        const int d = I.p.d;
+        constexpr int d = D;
         const long long r = I.p.r, s = I.p.s;
         const int ri = (int)r;  // <= kMaxR
         const T eps2 = (T)I.p.eps2;  // < 2^31 when T is 32-bit
@@ -482,12 +482,34 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                 // leaf: the two grids' boxes (a forward neighbour u >= c)
                 if (ok) {
                     const int* ub = pbox + (long long)u * 2 * d;
+                    // the box row (2d ints at 8d-byte steps from a 256-byte
+                    // aligned base) by 16-byte loads for even d, 8-byte ones
+                    // for odd d
+                    int row[2 * D];
+                    if constexpr (D % 2 == 0) {
+#pragma unroll
+                        for (int v = 0; v < D / 2; ++v) {
+                            const int4 q = __ldg(reinterpret_cast<const int4*>(ub) + v);
+                            row[4 * v] = q.x;
+                            row[4 * v + 1] = q.y;
+                            row[4 * v + 2] = q.z;
+                            row[4 * v + 3] = q.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < D; ++v) {
+                            const int2 q = __ldg(reinterpret_cast<const int2*>(ub) + v);
+                            row[2 * v] = q.x;
+                            row[2 * v + 1] = q.y;
+                        }
+                    }
                     // coordinates span less than 2^31 per dimension (the
                     // range check), so each gap fits in 32 bits; its square
                     // and the sum take 64
                     long long g2 = 0;
+#pragma unroll
                     for (int t = 0; t < d; ++t) {
-                        const int bl = __ldg(ub + t), bh = __ldg(ub + d + t);
+                        const int bl = row[t], bh = row[d + t];
                         const int ql = sh.qlo[w][t], qh = sh.qhi[w][t];
                         int gg = 0;
                         if (bl > qh) gg = bl - qh;
@@ -554,12 +576,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
     }
 }
 
-cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
-                        bool small_eps, cudaStream_t st) {
-    if (total <= 0) return cudaSuccess;
-    long long b = (total + kWalkWarps - 1) / kWalkWarps;
-    if (b > blocks) b = blocks;
-#define GD_WALK(M, T) walk_kernel<M, T><<<(int)b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool)
+template <int D>
+static void walk_d(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int b, bool small_eps,
+                   cudaStream_t st) {
+#define GD_WALK(M, T) walk_kernel<M, T, D><<<b, 32 * kWalkWarps, 0, st>>>(ins, cells, total, pool)
     if (small_eps) {
         if (mode == kWalkFill) GD_WALK(kWalkFill, unsigned);
         else if (mode == kWalkPool) GD_WALK(kWalkPool, unsigned);
@@ -570,6 +590,20 @@ cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, 
         else GD_WALK(kWalkCount, long long);
     }
 #undef GD_WALK
+}
+
+cudaError_t launch_walk(const Inst* ins, Flat cells, long long total, int mode, WalkPool pool, int blocks,
+                        bool small_eps, int d, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    long long b = (total + kWalkWarps - 1) / kWalkWarps;
+    if (b > blocks) b = blocks;
+    switch (d) {
+#define GD_WD(DD) \
+    case DD: walk_d<DD>(ins, cells, total, mode, pool, (int)b, small_eps, st); break;
+        GD_WD(1) GD_WD(2) GD_WD(3) GD_WD(4) GD_WD(5) GD_WD(6) GD_WD(7) GD_WD(8)
+#undef GD_WD
+        default: return cudaErrorInvalidValue;
+    }
     GD_COUNT_LAUNCH();
     return cudaGetLastError();
 }

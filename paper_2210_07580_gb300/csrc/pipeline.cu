@@ -668,6 +668,22 @@ gd_status Run::go() {
     // --------------------------- phase 3: levels, walk, list sizes
     long long total_cells = 0;  // bound of the grids (points)
     const Flat cells = gflat(members, K, &total_cells);
+    // the walk is specialised on the dimension: one launch per dimension
+    // present (the grids of all instances when there is one)
+    Flat wflat[kMaxD + 1];
+    long long wtot[kMaxD + 1] = {};
+    for (int dd = 1; dd <= kMaxD; ++dd) {
+        int m = 0;
+        for (int k = 0; k < K; ++k)
+            if (hi[k].dev.p.d == dd) members2[m++] = k;
+        if (m == 0) continue;
+        if (m == K) {
+            wflat[dd] = cells;
+            wtot[dd] = total_cells;
+        } else {
+            wflat[dd] = gflat(members2, m, &wtot[dd]);
+        }
+    }
     Flat lflat[kMaxD];
     long long ltot[kMaxD] = {};
     const ScanSeg* lseg[kMaxD] = {};
@@ -712,6 +728,12 @@ gd_status Run::go() {
         }
     }
     const bool pooled = pool.data != nullptr;
+    auto walk_all = [&](int mode) -> gd_status {
+        for (int dd = 1; dd <= kMaxD; ++dd)
+            if (wtot[dd] > 0)
+                RUN_CUDA(launch_walk(dins, wflat[dd], wtot[dd], mode, pool, walk_blocks, small_eps, dd, st), "walk");
+        return GD_OK;
+    };
     // whether the lists need the filling walk (the pool was too small or
     // absent): known after phase 3 on the synchronous path, else always
     // launched (it returns at once when the pool held the walk)
@@ -730,8 +752,7 @@ gd_status Run::go() {
         }
         RUN_CUDA(launch_level_write(dins, cells, total_cells, st), "level write");
         mark(5);
-        RUN_CUDA(launch_walk(dins, cells, total_cells, pooled ? kWalkPool : kWalkCount, pool, walk_blocks, small_eps, st),
-                 "walk");
+        RUN_TRY(walk_all(pooled ? kWalkPool : kWalkCount));
         RUN_CUDA(launch_nbr_total(dins, cells, total_cells, st), "list lengths");
         RUN_TRY(scan(nseg, K, nseg_tiles));
         RUN_CUDA(launch_nbr_check(dins, cells, total_cells, st), "list capacity");
@@ -826,8 +847,7 @@ gd_status Run::go() {
         // the lists: from the pool's runs, or (the pool too small, or none) by
         // a second, filling walk -- the device decides
         RUN_CUDA(launch_pool_scatter(dins, pool, st), "neighbour scatter");
-        if (need_fill)
-            RUN_CUDA(launch_walk(dins, cells, total_cells, kWalkFill, pool, walk_blocks, small_eps, st), "walk fill");
+        if (need_fill) RUN_TRY(walk_all(kWalkFill));
         mark(7);
         RUN_CUDA(launch_core_full(dins, cells, total_cells, st), "core (full grids)");
         return GD_OK;
