@@ -431,18 +431,20 @@ cudaError_t launch_level_diff(const Inst* ins, Flat cells, long long total, cuda
 cudaError_t launch_level_flag(const Inst* ins, Flat cells, long long total, int level, cudaStream_t st);
 cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cudaStream_t st);
 // Single-pass neighbour walk: the walk counts and, in the same pass, appends
-// each query's neighbours to a pool in runs of at most 32 (segments); after
+// each query's neighbours to a pool in runs of at most kPoolRun (segments;
+// long runs keep the shared counter's atomics few); after
 // the counts are scanned, the segments are scattered into the lists.  One
 // 64-bit counter hands out both: pool entries in its low kPoolBits bits,
 // segments above them.  A pool that overflows is discarded (the lists are then
 // filled by a second walk).
 constexpr int kPoolBits = 37;
+constexpr int kPoolRun = 96;
 struct PoolSeg {
     long long pos;  // first pool entry
     int inst;       // instance (index into the Inst array)
     int c;          // query grid
     int off;        // offset of the run in the grid's list
-    int len;        // 1..32
+    int len;        // 1..kPoolRun
 };
 struct WalkPool {
     int* data;

@@ -213,7 +213,7 @@ cudaError_t launch_level_write(const Inst* ins, Flat cells, long long total, cud
 // their child range narrowed to the child window (so no pushed node fails
 // its key test), surviving leaves are the forward neighbours g' >= c: counted
 // into nbr_fwd[c] and written -- at nbr + nbr_start[c] once the counts are
-// scanned (kWalkFill), or to the pool in runs of up to 32 (kWalkPool, see
+// scanned (kWalkFill), or to the pool in runs of up to kPoolRun (kWalkPool, see
 // WalkPool) -- while each g' > c also counts (count and pool modes) or
 // receives (fill mode) the backward entry c.  Every mode visits the nodes in
 // the same order.
@@ -306,7 +306,7 @@ struct WalkShared {
     // at key offset delta = key - g_j, index delta + kMaxR (saturated above
     // eps2: at 2^62, or at eps2 + 1 for 32-bit offsets)
     T gap2[kWalkWarps][kMaxD][2 * kMaxR + 1];
-    int buf[kWalkWarps][64];  // kWalkPool: neighbours not yet flushed
+    int buf[kWalkWarps][kPoolRun + 32];  // kWalkPool: neighbours not yet flushed
 };
 
 // kWalkPool: hand `len` buffered neighbours of query c (instance k), the run
@@ -318,7 +318,7 @@ __device__ __forceinline__ void pool_flush(const WalkPool& pool, const int* buf,
     t = __shfl_sync(kFull, t, 0);
     const long long pos = (long long)(t & ((1ull << kPoolBits) - 1)), si = (long long)(t >> kPoolBits);
     if (pos + len <= pool.cap && si < pool.seg_cap) {
-        if (lane < len) pool.data[pos + lane] = buf[lane];
+        for (int i = lane; i < len; i += 32) pool.data[pos + i] = buf[i];
         if (lane == 0) pool.seg[si] = PoolSeg{pos, k, c, off, len};
     }
 }
@@ -534,11 +534,11 @@ __global__ void __launch_bounds__(32 * kWalkWarps)
                     if (ok) buf[nbuf + __popc(m & lt)] = u;
                     nbuf += __popc(m);
                     __syncwarp();
-                    if (nbuf >= 32) {
-                        pool_flush(pool, buf, 32, kin, (int)c, flushed, lane);
-                        flushed += 32;
-                        nbuf -= 32;
-                        const int rest = lane < nbuf ? buf[32 + lane] : 0;
+                    if (nbuf >= kPoolRun) {
+                        pool_flush(pool, buf, kPoolRun, kin, (int)c, flushed, lane);
+                        flushed += kPoolRun;
+                        nbuf -= kPoolRun;  // < 32 left
+                        const int rest = lane < nbuf ? buf[kPoolRun + lane] : 0;
                         __syncwarp();
                         if (lane < nbuf) buf[lane] = rest;
                     }
@@ -623,10 +623,10 @@ __global__ void __launch_bounds__(256) pool_scatter_kernel(const Inst* __restric
         const PoolSeg sg = pool.seg[sgi];
         const Inst& I = ins[sg.inst];
         if (lists_dropped(I)) continue;
-        if (lane < sg.len) {
-            const int u = pool.data[sg.pos + lane];
-            const long long at = (long long)I.nbr_start[sg.c] + sg.off + lane;
-            if (at < I.nbr_cap) I.nbr[at] = u;
+        const long long base = (long long)I.nbr_start[sg.c] + sg.off;
+        for (int i = lane; i < sg.len; i += 32) {
+            const int u = pool.data[sg.pos + i];
+            if (base + i < I.nbr_cap) I.nbr[base + i] = u;
             if (u != sg.c) put_backward(I, u, sg.c);
         }
     }
