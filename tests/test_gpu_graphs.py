@@ -46,7 +46,7 @@ def test_graph_phases_match_direct_launches():
     graphed.set_timing(True)
     graphed.dbscan(Xd, e, m)
     times = graphed.stage_times()
-    assert len(times) == 12 and all(v >= 0 for v in times.values()) and sum(times.values()) > 0
+    assert len(times) == 13 and all(v >= 0 for v in times.values()) and sum(times.values()) > 0
     assert 0 < times["sort_downsweep"] <= times["sort"]
     # a small call runs without graphs
     X, e, m = synth.workload("tiny", n=8000, seed=4)
