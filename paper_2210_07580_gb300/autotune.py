@@ -129,15 +129,22 @@ def main():
     ap.add_argument("--k", type=int, default=256, help="instances of the batched workload to tune on")
     ap.add_argument("--seed", type=int, default=21)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true",
+                    help="tune on the batched instances only (by default the single-instance workloads "
+                         "tiny, ss3d_2m, ss3d_10m, skew3d_10m and skew5d_10m join them, each in its own group)")
     args = ap.parse_args()
     import torch
 
     from . import synth
     jobs = synth.batch_instances(args.k, seed=args.seed)
+    what = f"{args.k} batched instances (synth.batch_instances seed {args.seed})"
+    if not args.no_plain:
+        plain = ["tiny", "ss3d_2m", "ss3d_10m", "skew3d_10m", "skew5d_10m"]
+        jobs = jobs + [synth.workload(w, seed=1) for w in plain]
+        what += " + " + ", ".join(plain)
     t0 = time.time()
     res = tune(jobs, args.device, args.reps)
-    doc = {"device": torch.cuda.get_device_name(args.device),
-           "workload": f"{args.k} batched instances (synth.batch_instances seed {args.seed})",
+    doc = {"device": torch.cuda.get_device_name(args.device), "workload": what,
            "seconds": round(time.time() - t0, 1), **res}
     with open(args.out, "w") as f:
         json.dump(doc, f, indent=1)
