@@ -138,7 +138,7 @@ __device__ __forceinline__ int border_label(const Inst& I, long long q, int c, u
 constexpr int kLabelChunk = 128;
 
 template <int D>
-__global__ void __launch_bounds__(256) labels_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
+__global__ void __launch_bounds__(256, D >= 5 ? 4 : 1) labels_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     total = flat_total(f);
     constexpr int U = 4;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
