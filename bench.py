@@ -532,10 +532,10 @@ def bench_serve(dev, args):
     rate = None
     for name, kw in configs:
         with Server(device=dev.index or 0, **kw) as srv:
-            # warm-up: two passes, so that every slot's workspace has grown to
-            # the jobs it will see (growth reallocates, once)
+            # warm-up: every pool job on every slot (workspaces grow to the mix,
+            # once), then one pass through the queue
+            srv.warm(pool)
             res, _ = _replay(srv, pool, None)
-            _replay(srv, pool, None)
             results[name] = res
             caps, batch = [], []
             for _ in range(3):

@@ -300,6 +300,18 @@ class Server:
                 else:
                     j.future.set_result(results[k])
 
+    def warm(self, jobs):
+        """Run every given job once on every slot, outside the queue (call it
+        before submitting), so that each slot's device workspace and staging
+        buffers have grown to the job mix: workspaces only grow, and growing
+        one reallocates it, which a timed run should not include.  The
+        results are dropped."""
+        ests = [Job(np.ascontiguousarray(X, dtype=np.int32), int(e), int(m), 0, 0.0) for X, e, m in jobs]
+        ests.sort(key=lambda j: -j.X.size)
+        for slot in range(len(self.workers)):
+            for j in ests:
+                self.backend.run(slot, [j])
+
     # --------------------------------------------------------------- stats
     def reset_stats(self):
         """Forget the finished jobs (e.g. after a warm-up pass)."""

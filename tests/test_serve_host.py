@@ -161,3 +161,22 @@ def test_staging_round_trip():
         assert gl.dtype == np.int32 and gc.dtype == bool
         np.testing.assert_array_equal(gl, wl)
         np.testing.assert_array_equal(gc, wc)
+
+
+def test_warm_runs_every_job_on_every_slot_before_the_queue():
+    class SlotBackend(FakeBackend):
+        def run(self, slot, jobs, gate=None):
+            with self.lock:
+                self.slots = getattr(self, "slots", []) + [(slot, jobs[0].n)]
+            return super().run(slot, jobs, gate)
+
+    fb = SlotBackend()
+    jobs = [(job(n, n), 100, 3) for n in (5, 700, 40)]
+    srv = Server(slots=3, hbm_budget=10 ** 9, backend=fb)
+    srv.warm(jobs)
+    # largest first, on each slot in turn; nothing reached the statistics
+    assert fb.slots == [(s, n) for s in range(3) for n in (700, 40, 5)]
+    assert srv.stats() == {"jobs": 0}
+    res = [srv.submit(X, e, m).result(timeout=10) for X, e, m in jobs]
+    assert [int(r[0][0]) for r in res] == [5, 700, 40]
+    srv.close()
