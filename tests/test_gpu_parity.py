@@ -408,3 +408,26 @@ def test_labels_without_core_flags(ctx):
         if core is not None:
             np.testing.assert_array_equal(core.cpu().numpy().astype(bool), wc.astype(bool),
                                           err_msg=f"instance {i} core")
+
+
+def test_batched_workload_at_full_size_vs_oracle(ctx):
+    """The bench's batched workload itself (256 instances, n up to 5e5,
+    d in {2,3,5,7}) in one call; the largest instance of each dimension and
+    a spread of others are checked against the oracle element by element,
+    and every instance against its own single call."""
+    jobs = synth.batch_instances(256, seed=7)
+    dev_jobs = [(torch.from_numpy(X).cuda(), e, m) for X, e, m in jobs]
+    res = ctx.dbscan_batched(dev_jobs)
+    torch.cuda.synchronize()
+    pick = set(range(0, 256, 23))
+    for dd in (2, 3, 5, 7):
+        ids = [i for i, (X, _, _) in enumerate(jobs) if X.shape[1] == dd]
+        pick.add(max(ids, key=lambda i: len(jobs[i][0])))
+    for i in sorted(pick):
+        X, e, m = jobs[i]
+        want = oracle.grid(X, e, m)
+        assert_same((res[i][0].cpu().numpy(), res[i][1].cpu().numpy()), want,
+                    f"batched instance {i} (n={len(X)}, d={X.shape[1]})")
+    for i, (X, e, m) in enumerate(jobs):
+        single = run_gpu(ctx, X, e, m)
+        np.testing.assert_array_equal(single[0], res[i][0].cpu().numpy(), err_msg=f"instance {i}")
