@@ -116,6 +116,18 @@ gd_status gd_dbscan_host(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, i
                          int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
                          gd_stream_t stream);
 
+/* As gd_dbscan_host, asynchronous (no counterpart in the paper): the copy in,
+ * the run and the copies out are queued on `stream` and the call returns;
+ * labels_host / is_core_host hold the results once gd_sync(ctx, stream)
+ * returns GD_OK (which waits for the copies out, and queues them again after
+ * a run that had to be repeated with exact sizes).  X_host must stay
+ * unchanged until then.  The next call on the context finishes this one
+ * first, so calls alternating between two contexts on two streams overlap
+ * one call's copies with the other's kernels. */
+gd_status gd_dbscan_host_async(gd_ctx *ctx, const int32_t *X_host, int64_t n, int d, int64_t eps2,
+                               int32_t minpts, int32_t *labels_host, uint8_t *is_core_host,
+                               gd_stream_t stream);
+
 /* One instance of a batch: device pointers and parameters as for gd_dbscan.
  *
  * eps2_yes selects approximate FastMerging (the Remark after Alg. 5, O(1)

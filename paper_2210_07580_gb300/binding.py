@@ -74,6 +74,8 @@ def load_library(path: str | None = None):
         lib.gd_sync.restype = ctypes.c_int
         lib.gd_dbscan_host.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
         lib.gd_dbscan_host.restype = ctypes.c_int
+        lib.gd_dbscan_host_async.argtypes = [vp, vp, i64, ctypes.c_int, i64, i32, vp, vp, vp]
+        lib.gd_dbscan_host_async.restype = ctypes.c_int
         lib.gd_status_str.argtypes = [ctypes.c_int]
         lib.gd_status_str.restype = ctypes.c_char_p
         lib.gd_last_error.argtypes = [vp]
@@ -275,9 +277,11 @@ class Context:
             self.sync(stream)
         return [(lab, core.view(torch.bool) if core.dtype == torch.uint8 else core) for lab, core in outs]
 
-    def dbscan_host(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None):
+    def dbscan_host(self, X, eps2: int, minpts: int, labels=None, is_core=None, stream=None, sync: bool = True):
         """Cluster host points (numpy or CPU torch int32 [n, d]; pinned memory
-        is fastest).  Copies in, clusters and copies the results out."""
+        is fastest).  Copies in, clusters and copies the results out.  With
+        sync=False the work is only queued (gd_dbscan_host_async): X must stay
+        unchanged and the outputs are final after sync()."""
         import torch
         if isinstance(X, np.ndarray):
             X = torch.from_numpy(np.ascontiguousarray(X, dtype=np.int32))
@@ -289,8 +293,9 @@ class Context:
             labels = torch.empty(n, dtype=torch.int32)
         if is_core is None:
             is_core = torch.empty(n, dtype=torch.uint8)
-        st = self._lib.gd_dbscan_host(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(),
-                                      is_core.data_ptr(), _stream_handle(stream))
+        fn = self._lib.gd_dbscan_host if sync else self._lib.gd_dbscan_host_async
+        st = fn(self._h, X.data_ptr(), n, d, int(eps2), int(minpts), labels.data_ptr(), is_core.data_ptr(),
+                _stream_handle(stream))
         self._check(st)
         return labels, is_core
 

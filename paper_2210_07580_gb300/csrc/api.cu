@@ -152,6 +152,17 @@ struct gd_ctx {
     // host staging sets (calls alternate) and their last-upload events
     int next_set = 0;
     cudaEvent_t stage_ev[2] = {};
+    // results of a host-buffer call still to reach the host: the copies are
+    // queued after the run (and queued again after a run with exact sizes)
+    struct HostOut {
+        bool active = false;
+        void* lab = nullptr;
+        void* core = nullptr;
+        const void* dlab = nullptr;
+        const void* dcore = nullptr;
+        size_t lb = 0, cb = 0;
+        cudaStream_t st = nullptr;
+    } out;
 };
 
 namespace {
@@ -230,14 +241,28 @@ gd_status finish(gd_ctx* ctx) {
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
     const int k = (int)ctx->pend_inst.size();
     gd_status s = finish_batch(ctx->mem, k, ctx->pend_inst.data(), ctx->pend_st, &ctx->info);
+    bool rerun = false;
     if (s == kGdRerun) {
         ctx->pending = false;
+        rerun = true;
         const std::vector<gd_instance> again = ctx->pend_inst;  // queue() replaces pend_inst
         s = queue(ctx, k, again.data(), ctx->pend_caller, false);
         if (s == GD_OK) s = finish_batch(ctx->mem, k, again.data(), ctx->pend_st, &ctx->info);
         if (s == kGdRerun) s = (ctx->info.error = "device buffers overflowed on a run with exact sizes", GD_ECUDA);
     }
     ctx->pending = false;
+    if (ctx->out.active) {
+        // a host-buffer call: its copies out follow the (last) run
+        gd_ctx::HostOut& o = ctx->out;
+        if (s == GD_OK && rerun) {
+            if (cudaMemcpyAsync(o.lab, o.dlab, o.lb, cudaMemcpyDeviceToHost, o.st) != cudaSuccess ||
+                (o.core && cudaMemcpyAsync(o.core, o.dcore, o.cb, cudaMemcpyDeviceToHost, o.st) != cudaSuccess))
+                s = (ctx->info.error = "copy out failed", GD_ECUDA);
+        }
+        if (cudaStreamSynchronize(o.st) != cudaSuccess && s == GD_OK)
+            s = (ctx->info.error = "synchronise failed", GD_ECUDA);
+        o.active = false;
+    }
     if (s != GD_OK) {
         ctx->err = ctx->info.error;
         return s;
@@ -356,14 +381,24 @@ gd_status gd_dbscan_batched(gd_ctx* ctx, int k, const gd_instance* inst, gd_stre
     return run_ctx(ctx, k, inst, (cudaStream_t)stream);
 }
 
-gd_status gd_dbscan_host(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, int64_t eps2, int32_t minpts,
-                         int32_t* labels_host, uint8_t* is_core_host, gd_stream_t stream) {
+gd_status gd_dbscan_host_async(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, int64_t eps2, int32_t minpts,
+                               int32_t* labels_host, uint8_t* is_core_host, gd_stream_t stream) {
     if (!ctx) return GD_EINVAL;
     ctx->err.clear();
     gd_instance g{X_host, n, d, eps2, minpts, labels_host, is_core_host};
     gd_status s = validate_one(g, &ctx->err);
     if (s != GD_OK || n == 0) return s;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ctx->err = "cudaSetDevice failed", GD_ECUDA;
+    // the previous call (and its copies out) are done before the device
+    // copies are reused; its failure is kept for the next gd_sync
+    if (ctx->pending) {
+        const gd_status p = finish(ctx);
+        if (p != GD_OK && ctx->deferred == GD_OK) {
+            ctx->deferred = p;
+            ctx->deferred_err = ctx->err;
+        }
+        ctx->err.clear();
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t xb = (size_t)n * d * 4, lb = (size_t)n * 4, cb = (size_t)n;
     const size_t lo = (xb + 255) & ~(size_t)255, co = (lo + lb + 255) & ~(size_t)255;
@@ -388,15 +423,28 @@ gd_status gd_dbscan_host(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, i
         return ctx->err = "copy in failed", GD_ECUDA;
     s = run_ctx(ctx, 1, &dg, st);
     if (s != GD_OK) return s;
-    // the result is final only once the call is finished (it may run again)
-    s = gd_sync(ctx, stream);
-    if (s != GD_OK) return s;
-    if (cudaMemcpyAsync(labels_host, dg.labels, lb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    // copies out behind the run (queued again by gd_sync if the run must be
+    // repeated with exact sizes)
+    gd_ctx::HostOut& o = ctx->out;
+    o.lab = labels_host;
+    o.core = is_core_host;
+    o.dlab = dg.labels;
+    o.dcore = dg.is_core;
+    o.lb = lb;
+    o.cb = cb;
+    o.st = st;
+    o.active = true;
+    if (cudaMemcpyAsync(labels_host, dg.labels, lb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        (is_core_host && cudaMemcpyAsync(is_core_host, dg.is_core, cb, cudaMemcpyDeviceToHost, st) != cudaSuccess))
         return ctx->err = "copy out failed", GD_ECUDA;
-    if (is_core_host && cudaMemcpyAsync(is_core_host, dg.is_core, cb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return ctx->err = "copy out failed", GD_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return ctx->err = "synchronise failed", GD_ECUDA;
     return GD_OK;
+}
+
+gd_status gd_dbscan_host(gd_ctx* ctx, const int32_t* X_host, int64_t n, int d, int64_t eps2, int32_t minpts,
+                         int32_t* labels_host, uint8_t* is_core_host, gd_stream_t stream) {
+    gd_status s = gd_dbscan_host_async(ctx, X_host, n, d, eps2, minpts, labels_host, is_core_host, stream);
+    if (s != GD_OK || n == 0) return s;
+    return gd_sync(ctx, stream);
 }
 
 size_t gd_ctx_bytes(const gd_ctx* ctx) {

@@ -118,3 +118,35 @@ def test_calls_back_to_back_then_one_sync(gpu):
     for lab, core in outs:
         same((lab.cpu().numpy(), core.cpu().numpy()), want, "back to back")
     ctx.close()
+
+
+def test_host_buffers_async_on_two_contexts(gpu):
+    """gd_dbscan_host_async alternating between two contexts and streams:
+    every call's host outputs equal the oracle's after its context's sync,
+    including a call whose neighbour lists outgrew the plan (its copies out
+    are queued again after the run with exact sizes)."""
+    rng = np.random.default_rng(31)
+    n, eps2, minpts = 60000, 900 ** 2, 5
+    sparse = rng.integers(0, 100000, size=(n, 3)).astype(np.int32)
+    dense = rng.integers(0, 8000, size=(n, 3)).astype(np.int32)
+    seq = [sparse, sparse, dense, sparse, dense, dense]
+    want = {id(sparse): oracle.grid(sparse, eps2, minpts), id(dense): oracle.grid(dense, eps2, minpts)}
+    pinned = {k: torch.from_numpy(X).pin_memory() for k, X in ((id(sparse), sparse), (id(dense), dense))}
+    ctxs = [Context(0), Context(0)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [(torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory())
+            for _ in seq]
+    for i, X in enumerate(seq):
+        c = i % 2
+        if i >= 2:  # this context's previous call is finished by the next one; check it now
+            ctxs[c].sync(streams[c])
+            j = i - 2
+            same((outs[j][0].numpy(), outs[j][1].numpy().astype(bool)), want[id(seq[j])], f"call {j}")
+        ctxs[c].dbscan_host(pinned[id(X)], eps2, minpts, labels=outs[i][0], is_core=outs[i][1],
+                            stream=streams[c], sync=False)
+    for c in (0, 1):
+        ctxs[c].sync(streams[c])
+    for j in (len(seq) - 2, len(seq) - 1):
+        same((outs[j][0].numpy(), outs[j][1].numpy().astype(bool)), want[id(seq[j])], f"call {j}")
+    for c in ctxs:
+        c.close()
