@@ -76,11 +76,16 @@ def stage_bandwidth(stages: dict, n: int, d: int, sizes: dict, peak: float, stat
     val_b = 0 if kc == 0 else 4
     P = sizes["sort_passes"]
     first_hist = kc != 2  # quantisation writes the first pass's tile histograms for 64-bit keys
+    # packed keys whose in-cell offsets fit one 32-bit word: quantisation
+    # writes that word, and the compaction reads it instead of the input row
+    xw = (int(sizes["side"]) - 1).bit_length() if kc == 0 else -1
+    rebuild = kc == 0 and d * xw <= 32
+    off_b = 4 if rebuild and xw > 0 else 0
     bytes_ = {
         "bounds": 4 * d * n,
-        "quantise": (4 * d + key_b + val_b) * n,
+        "quantise": (4 * d + key_b + val_b + off_b) * n,
         "sort": (P * 2 * (key_b + val_b) + (P - (1 if first_hist else 0)) * key_b) * n,
-        "compact": (2 * key_b + val_b + 4 + 4 + 4 * d + 4 * dp) * n,
+        "compact": (2 * key_b + val_b + 4 + 4 + (off_b if rebuild else 4 * d) + 4 * dp) * n,
     }
     # the lists: the walk's forward entries (each pair once, self included)
     # read from its pool, every entry written into the scanned lists

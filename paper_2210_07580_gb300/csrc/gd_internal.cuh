@@ -71,6 +71,12 @@ struct Params {
     // index values, 2 = 128-bit key plus index values.
     int key_class;
     int pack_bits;
+    // Width of each dimension's in-cell offset (x - mn) - id * s when the d
+    // offsets of a point fit one 32-bit word (packed keys only), else -1.
+    // Quantisation then writes that word per point, and the compaction
+    // rebuilds each grid-order row from its identifiers and the word instead
+    // of gathering the input row.
+    int xoff_w;
     int ldf;          // merge order: 0 = touching pairs first, 1 = low density first (Section 5.2)
     int uf_cap;       // iterations a union-find loop may take before it gives up
     int mn[kMaxD];    // per-dimension minimum coordinate
@@ -146,7 +152,7 @@ struct Inst {
     void* keyA;
     void* keyB;
     int* valA;
-    int* valB;
+    int* valB;  // packed keys: the sorted permutation in one of valA/valB, the in-cell offsets in the other
     int* Xs;  // [n][dp] coordinates in grid order
     int* pt_cell;
     unsigned char* core_s;
@@ -329,6 +335,11 @@ __device__ __forceinline__ const int* core_rows(const Inst& I, int c, int dp) {
     const int b = I.cell_start[c];
     return I.cell_start[c + 1] - b >= I.p.minpts ? I.Xs + (long long)b * dp : I.Xc + (long long)I.core_start[c] * dp;
 }
+
+// Packed keys: the sort leaves the permutation in valA after an even number
+// of passes, in valB after an odd number; the other one holds each point's
+// in-cell offset word (input order) from quantisation to the compaction.
+__device__ __forceinline__ int* in_cell_offsets(const Inst& I) { return (I.passes & 1) ? I.valA : I.valB; }
 
 __device__ __forceinline__ void set_status(const Inst& I, unsigned bits) {
     atomicOr(reinterpret_cast<unsigned*>(I.small + kSmStatus), bits);

@@ -420,34 +420,50 @@ template <typename K, bool PACKED> __device__ __forceinline__ K grid_key(const K
         return keys[q];
 }
 
+// Both kernels take a tile's positions warp by warp: warp w owns
+// kCompactItems * 32 consecutive positions and item i of lane l is position
+// wbase + i * 32 + l, so every load and store of a warp instruction is
+// contiguous; a grid start is a lane whose key differs from the position
+// before it, and the grid ids follow from ballots of those flags.
+constexpr int kCompactWarps = kCompactBlock / 32;
+
+template <typename K, bool PACKED>
+__device__ __forceinline__ bool grid_starts(const K* keys, long long q, int n, int pb) {
+    return q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb)));
+}
+
 template <typename K, bool PACKED>
 __global__ void __launch_bounds__(kCompactBlock) compact_count_kernel(const Inst* __restrict__ ins, Flat f) {
-    __shared__ int sm[33];
+    __shared__ int s_cnt[kCompactWarps];
     const int k = flat_find(f, blockIdx.x);
     const Inst& I = ins[f.idx[k]];
     const long long tile = blockIdx.x - f.off[k];
     const int n = I.p.n;
     const K* keys = sorted_keys<K>(I);
     const int pb = I.p.pack_bits;
-    const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const long long wbase = tile * kCompactTile + (long long)warp * 32 * kCompactItems;
     int c = 0;
 #pragma unroll
-    for (int i = 0; i < kCompactItems; ++i) {
-        const long long q = base + i;
-        if (q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb))))
-            c++;
+    for (int i = 0; i < kCompactItems; ++i) c += grid_starts<K, PACKED>(keys, wbase + i * 32 + lane, n, pb);
+    c = __reduce_add_sync(kFull, (unsigned)c);
+    if (lane == 0) s_cnt[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int total = 0;
+#pragma unroll
+        for (int w = 0; w < kCompactWarps; ++w) total += s_cnt[w];
+        I.bcnt[tile] = total;
     }
-    int total;
-    block_exclusive_scan(c, sm, &total);
-    if (threadIdx.x == 0) I.bcnt[tile] = total;
 }
 
 // Writes cell_start, identifiers (decoded from the key), pt_cell and the
-// grid-order coordinates Xs (gathered through the sorted permutation; packed
-// keys also write the permutation out).
+// grid-order coordinates Xs (gathered through the sorted permutation, or
+// rebuilt from the in-cell offsets; packed keys also write the permutation
+// out).
 template <typename K, bool PACKED>
 __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst* __restrict__ ins, Flat f) {
-    __shared__ int sm[33];
+    __shared__ int s_cnt[kCompactWarps];
     const int k = flat_find(f, blockIdx.x);
     const Inst& I = ins[f.idx[k]];
     const long long tile = blockIdx.x - f.off[k];
@@ -455,30 +471,36 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
     const K* keys = sorted_keys<K>(I);
     int* vals = sorted_vals(I);
     const int pb = I.p.pack_bits;
-    const long long base = tile * kCompactTile + (long long)threadIdx.x * kCompactItems;
-    bool fl[kCompactItems];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const long long wbase = tile * kCompactTile + (long long)warp * 32 * kCompactItems;
+    // The items' sources (random reads) are all requested before the block
+    // exchange, so that their latency overlaps it.  With in-cell offset words
+    // the random read is that word (4 bytes of an array a quarter or less the
+    // size of the rows, which the cache keeps) and the row is rebuilt from
+    // the identifiers: x_j = mn_j + id_j * s + offset_j.
+    const bool rebuild = PACKED && I.p.xoff_w >= 0;
+    const int* xoff = in_cell_offsets(I);
+    unsigned starts[kCompactItems];
+    int src[kCompactItems];
+    int4 row4[kCompactItems];
+    unsigned ow[kCompactItems];
     int c = 0;
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
-        const long long q = base + i;
-        fl[i] = q < n && (q == 0 || !key_eq(grid_key<K, PACKED>(keys, q, pb), grid_key<K, PACKED>(keys, q - 1, pb)));
-        c += fl[i];
-    }
-    // the items' source rows (random reads) are all requested before the
-    // block scan, so that their latency overlaps it
-    int src[kCompactItems];
-    int4 row4[kCompactItems];
-#pragma unroll
-    for (int i = 0; i < kCompactItems; ++i) {
-        const long long q = base + i;
+        const long long q = wbase + i * 32 + lane;
+        starts[i] = __ballot_sync(kFull, grid_starts<K, PACKED>(keys, q, n, pb));
+        c += __popc(starts[i]);
         src[i] = 0;
+        ow[i] = 0;
         row4[i] = make_int4(0, 0, 0, 0);
         if (q < n) {
             if constexpr (PACKED)
                 src[i] = (int)(keys[q] & ((1ull << pb) - 1ull));
             else
                 src[i] = vals[q];
-            if (dp == 4) {
+            if (rebuild) {
+                if (I.p.xoff_w > 0) ow[i] = (unsigned)__ldg(xoff + src[i]);
+            } else if (dp == 4) {
                 const int* row = I.X + (long long)src[i] * d;
                 row4[i].x = __ldg(row);
                 if (d > 1) row4[i].y = __ldg(row + 1);
@@ -487,31 +509,63 @@ __global__ void __launch_bounds__(kCompactBlock) compact_write_kernel(const Inst
             }
         }
     }
-    int total;
-    int cid = I.bcnt[tile] + block_exclusive_scan(c, sm, &total) - 1;
+    if (lane == 0) s_cnt[warp] = c;
+    __syncthreads();
+    // id of the grid holding the position before the warp's first
+    int cid = I.bcnt[tile] - 1;
+#pragma unroll
+    for (int w = 0; w < kCompactWarps; ++w)
+        if (w < warp) cid += s_cnt[w];
+    const unsigned le = lanemask_lt() | (1u << lane);
 #pragma unroll
     for (int i = 0; i < kCompactItems; ++i) {
-        const long long q = base + i;
-        if (q >= n) break;
-        if (fl[i]) {
-            cid++;
-            I.cell_start[cid] = (int)q;
+        const long long q = wbase + i * 32 + lane;
+        const int my = cid + __popc(starts[i] & le);
+        cid += __popc(starts[i]);
+        if (q >= n) continue;
+        if ((starts[i] >> lane) & 1u) {
+            I.cell_start[my] = (int)q;
             const K key = grid_key<K, PACKED>(keys, q, pb);
             for (int j = 0; j < d; ++j)
-                I.cell_coord[(long long)cid * d + j] = (int)key_field(key, I.p.shift[j], I.p.bits[j]);
+                I.cell_coord[(long long)my * d + j] = (int)key_field(key, I.p.shift[j], I.p.bits[j]);
         }
-        I.pt_cell[q] = cid;
-        if constexpr (PACKED) vals[q] = src[i];
+        // streaming stores (evict first): the outputs are written once here,
+        // and the offset words still to be read stay in the cache
+        __stcs(I.pt_cell + q, my);
+        if constexpr (PACKED) __stcs(vals + q, src[i]);
         const int* row = I.X + (long long)src[i] * d;
         int* out = I.Xs + q * dp;
-        if (dp == 4) {
+        if (rebuild) {
+            // unsigned arithmetic: x - mn_j < 2^32 and the sum wraps back to x
+            const K key = grid_key<K, PACKED>(keys, q, pb);
+            const int w = I.p.xoff_w;
+            const unsigned om = w > 0 ? (1u << w) - 1u : 0u;
+            int v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = 0;
+                if (j < d)
+                    v[j] = (int)((unsigned)I.p.mn[j] + key_field(key, I.p.shift[j], I.p.bits[j]) * (unsigned)I.p.s +
+                                 (w > 0 ? (ow[i] >> (j * w)) & om : 0u));
+            }
+            if (dp == 8) {
+                __stcs(reinterpret_cast<int4*>(out), make_int4(v[0], v[1], v[2], v[3]));
+                __stcs(reinterpret_cast<int4*>(out) + 1, make_int4(v[4], v[5], v[6], v[7]));
+            } else if (dp == 4) {
+                __stcs(reinterpret_cast<int4*>(out), make_int4(v[0], v[1], v[2], v[3]));
+            } else if (dp == 2) {
+                __stcs(reinterpret_cast<int2*>(out), make_int2(v[0], v[1]));
+            } else {
+                __stcs(out, v[0]);
+            }
+        } else if (dp == 4) {
             *reinterpret_cast<int4*>(out) = row4[i];
         } else {
             for (int j = 0; j < dp; ++j) out[j] = j < d ? __ldg(row + j) : 0;
         }
         if (q == n - 1) {
-            I.cell_start[cid + 1] = n;
-            I.small[kSmCells] = cid + 1;
+            I.cell_start[my + 1] = n;
+            I.small[kSmCells] = my + 1;
         }
     }
 }

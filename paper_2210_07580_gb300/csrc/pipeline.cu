@@ -162,6 +162,9 @@ void set_plan(HI& h, int key_words, int key_class, int key_bits) {
     p.key_class = key_class;
     const int ib = p.n > 1 ? bit_length((unsigned long long)(p.n - 1)) : 1;
     p.pack_bits = key_class == 0 ? ib : 0;
+    // an in-cell offset is below s: d fields of bit_length(s - 1) bits each
+    const int w = bit_length((unsigned long long)(p.s - 1));
+    p.xoff_w = key_class == 0 && p.d * w <= 32 ? w : -1;
     const SortPlan sp = sort_plan(p.n, key_words, key_bits);
     h.dev.passes = sp.passes;
     h.dev.digit_bits = sp.bits;

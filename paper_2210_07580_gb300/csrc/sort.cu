@@ -100,7 +100,8 @@ __device__ __forceinline__ void zero_key(unsigned long long& k) { k = 0; }
 __device__ __forceinline__ void zero_key(Key2& k) { k.lo = k.hi = 0; }
 
 // One block per tile of kQuantTile points of one instance: the keys and (for
-// unpacked keys) the values, the input index.  For 64-bit keys a quantise tile
+// unpacked keys) the values, the input index; for packed keys whose in-cell
+// offsets fit a word (Params::xoff_w > 0), that word.  For 64-bit keys a quantise tile
 // is a sort tile, so the block also writes the tile's histogram of the first
 // digit position (the first pass then needs no upsweep).
 template <typename K, bool PACKED>
@@ -128,12 +129,20 @@ __global__ void __launch_bounds__(256) quantise_kernel(const Inst* __restrict__ 
         zero_key(key);
         if (valid) {
             const int* row = I.X + i * d;
+            unsigned xoff = 0;
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
-                if (j < d) pack_key(key, identifier(__ldg(row + j), p.mn[j], p.s_mul), p.shift[j]);
+                if (j < d) {
+                    const int x = __ldcs(row + j);
+                    const unsigned id = identifier(x, p.mn[j], p.s_mul);
+                    pack_key(key, id, p.shift[j]);
+                    if constexpr (PACKED)
+                        if (p.xoff_w > 0) xoff |= ((unsigned)(x - p.mn[j]) - id * (unsigned)p.s) << (j * p.xoff_w);
+                }
             if constexpr (PACKED) {
                 // key above the point index: one word carries both
                 keys[i] = (unsigned long long)key << p.pack_bits | (unsigned long long)i;
+                if (p.xoff_w > 0) __stcs(in_cell_offsets(I) + i, (int)xoff);  // read after the sort
             } else {
                 keys[i] = key;
                 I.valA[i] = (int)i;
