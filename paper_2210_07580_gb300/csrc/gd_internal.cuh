@@ -105,6 +105,7 @@ enum SmallSlot {
     kSmKeyBits = 29,    // ... key bits (the device's layout when it computes it),
     kSmKeyWords = 30,   // ... key words
     kSmLevelCount = 32, // [8] nodes per grid-tree level
+    kSmSortChunks = 40, // sort tile scan: chunks of the current pass done (the last one resets it)
     kSmallInts = 64
 };
 
@@ -185,8 +186,8 @@ struct Inst {
     int* cid_root;
     int* cell_cid;
     int* bcnt;  // compaction: per-tile grid starts (scanned)
-    int* sort_tcnt;    // [tiles][R] per-tile digit counts, then offsets over the tiles
-    int* sort_dtot;    // [R] digit totals of the current pass
+    int* sort_tcnt;    // [tiles][R] per-tile digit counts, then offsets within the tile's chunk
+    int* sort_ctot;    // [chunks][R] per-chunk digit totals, then offsets over the chunks
     int* sort_dstart;  // [R] digit starts of the current pass
 };
 
@@ -421,18 +422,21 @@ SortPlan sort_plan(int n, int key_words, int key_bits);
 // ints of workspace for one instance's sort (tile histograms, digit totals
 // and starts); layout in sort.cu.
 size_t sort_tmp_ints(int n, int key_words, int key_bits);
-void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** dtot, int** dstart);
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** ctot, int** dstart);
 constexpr int kQuantTile = 4096;  // points per quantise block
 // Keys (and, unpacked, index values) of every point, over quantisation tiles.
 cudaError_t launch_quantise(const Inst* ins, Flat tiles, long long total, int key_class, cudaStream_t st);
 // Sets the downsweep kernels' shared-memory limit on the current device (once
 // per device; before any stream capture).
 cudaError_t prepare_sort();
-// One radix-sort pass (upsweep, tile scan, digit starts, downsweep) of digit
-// position `pass` over the sort tiles of the instances of one key class.
-// ev_a / ev_b, when set, are recorded just before and after the downsweep.
-cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                             cudaStream_t st, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr);
+// One radix-sort pass (upsweep, tile scan, downsweep) of digit position
+// `pass` over the sort tiles of the instances of one key class; `chunks` is
+// the flat space of their tile-scan chunks (kSortChunk tiles each).  ev_a /
+// ev_b, when set, are recorded just before and after the downsweep.
+constexpr int kSortChunk = 32;
+cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, Flat chunks, long long chunk_total,
+                             int key_class, int pass, int max_buckets, cudaStream_t st, cudaEvent_t ev_a = nullptr,
+                             cudaEvent_t ev_b = nullptr);
 // Records ev on st; inside a stream capture, as an external graph node.
 void record_event(cudaEvent_t ev, cudaStream_t st);
 

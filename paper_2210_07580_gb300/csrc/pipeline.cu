@@ -149,7 +149,7 @@ size_t carve(Inst& I, char* base, int n, int d, int key_words, int key_bits) {
     I.cell_cid = (int*)take(N * 4);
     I.bcnt = (int*)take(((N + kCompactTile - 1) / kCompactTile + 1) * 4);
     int* sort_base = (int*)take(sort_tmp_ints(n, key_words, key_bits) * 4);
-    if (base) sort_tmp_layout(sort_base, n, key_words, key_bits, &I.sort_tcnt, &I.sort_dtot, &I.sort_dstart);
+    if (base) sort_tmp_layout(sort_base, n, key_words, key_bits, &I.sort_tcnt, &I.sort_ctot, &I.sort_dstart);
     return align256(off) + 256;
 }
 
@@ -609,8 +609,8 @@ gd_status Run::go() {
     // one group per key class (packed 64-bit, 64-bit + values, 128-bit + values)
     Flat qflat[3], cflat[3];
     long long qtot[3] = {0, 0, 0}, ctot[3] = {0, 0, 0};
-    Flat oflat[3][16];
-    long long otot[3][16] = {};
+    Flat oflat[3][16], chflat[3][16];
+    long long otot[3][16] = {}, chtot[3][16] = {};
     int gpasses[3] = {0, 0, 0};
     for (int w = 0; w < 3; ++w) {
         int m = 0;
@@ -625,6 +625,9 @@ gd_status Run::go() {
             for (int t = 0; t < m; ++t)
                 if (hi[members2[t]].dev.passes > ps) members[m2++] = members2[t];
             oflat[w][ps] = flat(members, m2, [&](int k) { return (long long)hi[k].dev.tiles; }, &otot[w][ps]);
+            chflat[w][ps] = flat(
+                members, m2, [&](int k) { return (long long)(hi[k].dev.tiles + kSortChunk - 1) / kSortChunk; },
+                &chtot[w][ps]);
         }
     }
     for (int k = 0; k < K; ++k) members[k] = k;
@@ -654,7 +657,8 @@ gd_status Run::go() {
                     b2 = sort_ev[2 * pairs + 1];
                     ++pairs;
                 }
-                RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], w, ps, max_buckets, st, a, b2),
+                RUN_CUDA(launch_sort_pass(dins, oflat[w][ps], otot[w][ps], chflat[w][ps], chtot[w][ps], w, ps,
+                                          max_buckets, st, a, b2),
                          "sort pass");
             }
         if (info) info->sort_event_pairs = pairs;

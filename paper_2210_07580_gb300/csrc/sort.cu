@@ -6,8 +6,9 @@
 // by digits of up to 9 bits.  Quantisation computes the keys; then every
 // digit position is one pass of three steps over tiles of consecutive keys:
 //   1. upsweep: each tile's digit histogram;
-//   2. tile scan: per digit, exclusive offsets over the tiles and the digit's
-//      total; digit starts: exclusive scan of the totals;
+//   2. tile scan: per digit, exclusive offsets over the tiles (within chunks
+//      of tiles, then over the chunks) and the digit starts, the exclusive
+//      scan of the digit totals;
 //   3. downsweep: each tile ranks its keys stably in shared memory and writes
 //      each digit run to its start plus the tile's offset.
 // No tile waits for another.  When the key and the point index fit in 64
@@ -59,19 +60,22 @@ SortPlan sort_plan(int n, int key_words, int key_bits) {
     return sp;
 }
 
-// One instance's sort workspace (ints): per-tile digit counts (then offsets)
-// [tiles][R], digit totals [R], digit starts [R].  Nothing needs clearing:
+// One instance's sort workspace (ints): per-tile digit counts (then offsets
+// within the tile's chunk) [tiles][R], per-chunk digit totals (then offsets
+// over the chunks) [chunks][R], digit starts [R].  Nothing needs clearing:
 // every pass writes all of it before reading it.
+static size_t sort_chunks(const SortPlan& sp) { return (size_t)(sp.tiles + kSortChunk - 1) / kSortChunk; }
+
 size_t sort_tmp_ints(int n, int key_words, int key_bits) {
     const SortPlan sp = sort_plan(n, key_words, key_bits);
-    return (size_t)sp.tiles * sp.buckets + 2 * (size_t)sp.buckets + 64;
+    return ((size_t)sp.tiles + sort_chunks(sp)) * sp.buckets + (size_t)sp.buckets + 64;
 }
 
-void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** dtot, int** dstart) {
+void sort_tmp_layout(int* base, int n, int key_words, int key_bits, int** tcnt, int** ctot, int** dstart) {
     const SortPlan sp = sort_plan(n, key_words, key_bits);
     *tcnt = base;
-    *dtot = base + (size_t)sp.tiles * sp.buckets;
-    *dstart = *dtot + sp.buckets;
+    *ctot = base + (size_t)sp.tiles * sp.buckets;
+    *dstart = *ctot + sort_chunks(sp) * sp.buckets;
 }
 
 // ------------------------------------------------------------- quantise
@@ -216,62 +220,66 @@ __global__ void __launch_bounds__(kOsBlock) upsweep_kernel(const Inst* __restric
     for (int b = threadIdx.x; b < R; b += kOsBlock) out[b] = hist[b];
 }
 
-// Tile scan: one block per (member instance, digit < max_buckets): exclusive offsets of the
-// digit over the tiles, in place, and the digit's total.  Each thread takes a
-// run of consecutive tiles (its loads are independent), then one block scan
-// joins the runs.
-constexpr int kTileScanBlock = 256;
-constexpr int kTileScanRun = 16;  // tiles per thread held in registers
+// Tile scan: one block per chunk of kSortChunk consecutive tiles, a thread
+// per digit: the digit's exclusive offsets over the chunk's tiles, in place
+// (the rows are read and written whole, so every access is contiguous), and
+// the chunk's digit totals.  The block that finishes an instance's last chunk
+// (counted in small[kSmSortChunks]) turns the chunk totals into offsets over
+// the chunks and writes the digit starts: the exclusive scan of the digit
+// totals.  A tile's offset of digit b is then
+// dstart[b] + ctot[chunk][b] + tcnt[tile][b].  No block waits for another.
+constexpr int kTileScanBlock = kMaxBuckets;
 
-__global__ void __launch_bounds__(kTileScanBlock)
-    tile_scan_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int m, int pass, int max_buckets) {
+__global__ void __launch_bounds__(kTileScanBlock) tile_scan_kernel(const Inst* __restrict__ ins, Flat f, int pass) {
     __shared__ int sm[33];
-    const int t = blockIdx.x / max_buckets, dg = blockIdx.x % max_buckets;
-    if (t >= m) return;
-    const Inst& I = ins[idx[t]];
-    const int R = 1 << I.digit_bits;
-    if (pass >= I.passes || dg >= R) return;
-    const int tiles = I.tiles;
-    int* col = I.sort_tcnt + dg;
-    int carry = 0;
-    // chunks of kTileScanBlock * kTileScanRun tiles (one chunk up to 1M keys)
-    for (int c0 = 0; c0 < tiles; c0 += kTileScanBlock * kTileScanRun) {
-        const int r0 = c0 + threadIdx.x * kTileScanRun;
-        int v[kTileScanRun];
-        int sum = 0;
+    __shared__ int s_last;
+    const int kk = flat_find(f, blockIdx.x);
+    const Inst& I = ins[f.idx[kk]];
+    if (pass >= I.passes) return;  // block-uniform
+    const int c = blockIdx.x - (int)f.off[kk];
+    const int R = 1 << I.digit_bits, tiles = I.tiles;
+    const int nch = (tiles + kSortChunk - 1) / kSortChunk;
+    const int b = threadIdx.x;
+    const int t0 = c * kSortChunk, rows = min(kSortChunk, tiles - t0);
+    int* tcnt = I.sort_tcnt;
+    int* ctot = I.sort_ctot;
+    if (b < R) {
+        int v[kSortChunk];
 #pragma unroll
-        for (int u = 0; u < kTileScanRun; ++u) {
-            v[u] = r0 + u < tiles ? col[(long long)(r0 + u) * R] : 0;
-            sum += v[u];
-        }
-        int total;
-        int ex = carry + block_exclusive_scan(sum, sm, &total);
+        for (int i = 0; i < kSortChunk; ++i) v[i] = i < rows ? tcnt[(long long)(t0 + i) * R + b] : 0;
+        int run = 0;
 #pragma unroll
-        for (int u = 0; u < kTileScanRun; ++u)
-            if (r0 + u < tiles) {
-                col[(long long)(r0 + u) * R] = ex;
-                ex += v[u];
+        for (int i = 0; i < kSortChunk; ++i)
+            if (i < rows) {
+                tcnt[(long long)(t0 + i) * R + b] = run;
+                run += v[i];
             }
-        carry += total;
+        ctot[(long long)c * R + b] = run;
     }
-    if (threadIdx.x == 0) I.sort_dtot[dg] = carry;
-}
-
-// Digit starts: one block per member instance, exclusive scan of the totals.
-__global__ void digit_start_kernel(const Inst* __restrict__ ins, const int* __restrict__ idx, int pass) {
-    __shared__ int sm[33];
-    const Inst& I = ins[idx[blockIdx.x]];
-    if (pass >= I.passes) return;
-    const int R = 1 << I.digit_bits;
-    int carry = 0;
-    for (int base = 0; base < R; base += blockDim.x) {
-        const int b = base + threadIdx.x;
-        const int v = b < R ? I.sort_dtot[b] : 0;
-        int total;
-        const int ex = block_exclusive_scan(v, sm, &total);
-        if (b < R) I.sort_dstart[b] = carry + ex;
-        carry += total;
+    // the last chunk done: its block sees every chunk's totals
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(I.small + kSmSortChunks, 1) == nch - 1;
+    __syncthreads();
+    if (!s_last) return;
+    int run = 0;
+    if (b < R) {
+        for (int c0 = 0; c0 < nch; c0 += kSortChunk) {
+            int v[kSortChunk];
+#pragma unroll
+            for (int i = 0; i < kSortChunk; ++i) v[i] = c0 + i < nch ? __ldcg(ctot + (long long)(c0 + i) * R + b) : 0;
+#pragma unroll
+            for (int i = 0; i < kSortChunk; ++i)
+                if (c0 + i < nch) {
+                    ctot[(long long)(c0 + i) * R + b] = run;
+                    run += v[i];
+                }
+        }
     }
+    int total;
+    const int ex = block_exclusive_scan(b < R ? run : 0, sm, &total);
+    if (b < R) I.sort_dstart[b] = ex;
+    if (threadIdx.x == 0) I.small[kSmSortChunks] = 0;  // the next pass counts again
 }
 
 // Downsweep: one block per tile ranks its keys stably in shared memory and
@@ -305,8 +313,9 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kOsWarps * R; i += kOsBlock) wcount[i] = 0;
     // the tile's global start of each digit
+    const int* ctot = I.sort_ctot + (long long)(tile / kSortChunk) * R;
     for (int b = threadIdx.x; b < R; b += kOsBlock)
-        goff[b] = I.sort_dstart[b] + I.sort_tcnt[(long long)tile * R + b];
+        goff[b] = I.sort_dstart[b] + ctot[b] + I.sort_tcnt[(long long)tile * R + b];
     __syncthreads();
     const long long base = (long long)tile * kTile;
     const int count = (int)min((long long)kTile, (long long)n - base);
@@ -470,16 +479,13 @@ void record_event(cudaEvent_t ev, cudaStream_t st) {
 }
 
 template <typename K, bool PACKED>
-static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, int max_buckets, cudaStream_t st,
-                        cudaEvent_t ev_a, cudaEvent_t ev_b) {
+static void pass_launch(const Inst* ins, Flat tiles, long long total, Flat chunks, long long chunk_total, int pass,
+                        int max_buckets, cudaStream_t st, cudaEvent_t ev_a, cudaEvent_t ev_b) {
     if (pass > 0 || os_tile<K>() != kQuantTile) {  // quantisation wrote the first histograms
         upsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, 0, st>>>(ins, tiles, pass);
         GD_COUNT_LAUNCH();
     }
-    tile_scan_kernel<<<(unsigned)((long long)tiles.K * max_buckets), kTileScanBlock, 0, st>>>(ins, tiles.idx,
-                                                                                          tiles.K, pass, max_buckets);
-    GD_COUNT_LAUNCH();
-    digit_start_kernel<<<(unsigned)tiles.K, 256, 0, st>>>(ins, tiles.idx, pass);
+    tile_scan_kernel<<<(unsigned)chunk_total, kTileScanBlock, 0, st>>>(ins, chunks, pass);
     GD_COUNT_LAUNCH();
     if (ev_a) record_event(ev_a, st);
     downsweep_kernel<K, PACKED><<<(unsigned)total, kOsBlock, downsweep_smem<K, PACKED>(max_buckets), st>>>(ins, tiles,
@@ -488,15 +494,18 @@ static void pass_launch(const Inst* ins, Flat tiles, long long total, int pass, 
     if (ev_b) record_event(ev_b, st);
 }
 
-cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, int key_class, int pass, int max_buckets,
-                             cudaStream_t st, cudaEvent_t ev_a, cudaEvent_t ev_b) {
-    if (total <= 0 || tiles.K <= 0) return cudaSuccess;
+cudaError_t launch_sort_pass(const Inst* ins, Flat tiles, long long total, Flat chunks, long long chunk_total,
+                             int key_class, int pass, int max_buckets, cudaStream_t st, cudaEvent_t ev_a,
+                             cudaEvent_t ev_b) {
+    if (total <= 0 || tiles.K <= 0 || chunk_total <= 0) return cudaSuccess;
     if (key_class == 0)
-        pass_launch<unsigned long long, true>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
+        pass_launch<unsigned long long, true>(ins, tiles, total, chunks, chunk_total, pass, max_buckets, st, ev_a,
+                                              ev_b);
     else if (key_class == 1)
-        pass_launch<unsigned long long, false>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
+        pass_launch<unsigned long long, false>(ins, tiles, total, chunks, chunk_total, pass, max_buckets, st, ev_a,
+                                               ev_b);
     else
-        pass_launch<Key2, false>(ins, tiles, total, pass, max_buckets, st, ev_a, ev_b);
+        pass_launch<Key2, false>(ins, tiles, total, chunks, chunk_total, pass, max_buckets, st, ev_a, ev_b);
     return cudaGetLastError();
 }
 

@@ -320,6 +320,30 @@ def clustered(rng, n, d, hi, sigma, k=6):
     return np.ascontiguousarray(X.clip(0, hi - 1).astype(np.int32))
 
 
+@pytest.mark.parametrize("key_class,n,d,hi,eps2,kind", [
+    (0, 600_000, 3, 1 << 20, 5000 ** 2, "uniform"),    # packed keys, 147 sort tiles, most grids distinct
+    (0, 600_000, 3, 1 << 20, 5000 ** 2, "clustered"),  # long runs of equal digits in every tile
+    (1, 300_000, 6, 1 << 24, 6 << 28, "clustered"),    # 64-bit key + index values, 74 sort tiles
+])
+def test_sort_order_over_many_tiles(ctx, key_class, n, d, hi, eps2, kind):
+    """Over many sort tiles (each tile takes its digit offsets from the tiles
+    before it), the sort gives the oracle's stable grid order (Alg. 1: ties
+    in input order) and its grids."""
+    rng = np.random.default_rng(n + d)
+    if kind == "uniform":
+        X = rng.integers(0, hi, size=(n, d)).astype(np.int32)
+    else:
+        X = clustered(rng, n, d, hi, sigma=float(np.sqrt(eps2)) * 0.5)
+    run_gpu(ctx, X, eps2, 4)
+    sz = ctx.last_sizes()
+    assert sz["key_class"] == key_class
+    gs = oracle.grid_structure(X, eps2)
+    np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_PERM, np.int32, n), gs["order"])
+    C = sz["grids"]
+    assert C == len(gs["cell_start"]) - 1
+    np.testing.assert_array_equal(ctx.copy_view(binding.VIEW_CELL_START, np.int32, C + 1), gs["cell_start"])
+
+
 @pytest.mark.parametrize("key_class,n,d,hi,eps2", [
     (0, 5000, 2, 100_000, 800 ** 2),         # 16 key bits + 13 index bits: packed
     (1, 5000, 6, 1 << 24, 6 << 28),          # 60 key bits + 13 index bits: 64-bit key + index
