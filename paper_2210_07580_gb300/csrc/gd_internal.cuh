@@ -494,7 +494,9 @@ cudaError_t launch_core_grid(const Inst* ins, Flat cells, long long total, int d
 
 // Merging (merge.cu).
 cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cudaStream_t st);
-cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st);
+// Core points of non-full grids packed, and every grid's core box, a thread
+// per grid of `cells` (the instances of dimension d).
+cudaError_t launch_core_pack(const Inst* ins, Flat cells, long long total, int d, cudaStream_t st);
 // Low-density-first order of the grids (instances with p.ldf set): core
 // grids by ascending core-point count (buckets: exact counts below 64, then
 // powers of two), non-core grids last.

@@ -19,8 +19,7 @@ static int blocks_for(long long total) {
 
 // ------------------------------------------------- core points per grid
 
-// m_c (core points per grid, into core_start before its scan) and reset of
-// the grid's core bounding box.
+// m_c (core points per grid, into core_start before its scan).
 __global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     total = flat_total(f);
     FlatCursor cur;
@@ -39,10 +38,6 @@ __global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long lon
         I.core_start[c] = m;
         if (c == 0)
             for (int b = 0; b < kLdfBuckets; ++b) I.ldf_ctr[b] = 0;
-        for (int j = 0; j < d; ++j) {
-            I.bbox[c * 2 * d + j] = 0x7fffffff;
-            I.bbox[c * 2 * d + d + j] = (int)0x80000000;
-        }
     }
 }
 
@@ -55,125 +50,74 @@ cudaError_t launch_core_count(const Inst* ins, Flat cells, long long total, cuda
 
 // Core points of the grids that are not full packed contiguously (s_i of
 // Section 4.3.1; a full grid's core points are its rows in Xs, see
-// core_rows), one thread per point in grid order (a point counts the core
-// points of its grid before it), and the bounding box of each grid's core
-// points by atomics.  A warp walks kPackRounds rounds of 32 consecutive
-// points; while whole rounds are points of one full grid (all core: the
-// common case in dense data) the lanes only fold them into per-lane boxes,
-// reduced in the warp and applied with one atomic per bound when the run
-// ends.  Other rounds apply their core points' bounds directly (reduced in
-// the warp first when all 32 are core points of one grid).
-constexpr int kPackRounds = 16;
-
-template <int D>
-__device__ __forceinline__ void box_flush(int* box, const int* lo, const int* hi, int lane) {
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const int l = __reduce_min_sync(kFull, lo[j]), h = __reduce_max_sync(kFull, hi[j]);
-        if (lane == 0) {
-            atomicMin(box + j, l);
-            atomicMax(box + D + j, h);
-        }
-    }
-}
-
+// core_rows), and the box of each grid's core points, a thread per grid.  A
+// full grid (all core, G13) takes its point box from the grid tree's build:
+// the exact box for grids of at most 1024 points, the identifier range for
+// larger ones.  Either holds all the grid's points, which is what the
+// merge's box tests and the border search need (a larger box decides fewer
+// pairs by box alone, never a pair wrongly), and dense grids fill their
+// range.  So only the points of grids that are not full are read.  A grid
+// without core points keeps an empty box (minima above maxima).
 template <int D>
 __global__ void __launch_bounds__(256) core_pack_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     total = flat_total(f);
     constexpr int DP = Padded<D>::value;
-    const int lane = lane_id();
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long wid = (((long long)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5);
     FlatCursor cur;
-    for (long long beg = wid * 32 * kPackRounds; beg < total; beg += nwarps * 32 * kPackRounds) {
-        const long long end = min(total, beg + 32 * kPackRounds);
-        int acc_c = -1, acc_k = -1;  // the full grid (and instance) being folded: warp-uniform
+    GD_FOR_FLAT(i, total) {
+        cur.seek(f, i);
+        const Inst& I = ins[f.idx[cur.k]];
+        const long long c = i - cur.lo;
+        const int b = I.cell_start[c], e = I.cell_start[c + 1];
+        int* box = I.bbox + c * 2 * D;
+        if (e - b >= I.p.minpts) {
+            const int* pb = I.pbox + c * 2 * D;
+#pragma unroll
+            for (int j = 0; j < 2 * D; ++j) box[j] = pb[j];
+            continue;
+        }
         int lo[D], hi[D];
-        for (long long r0 = beg; r0 < end; r0 += 32) {
-            const long long i = r0 + lane;
-            const bool valid = i < end;
-            int k = -1, c = -1;
-            long long q = 0;
-            bool core = false;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            lo[j] = 0x7fffffff;
+            hi[j] = (int)0x80000000;
+        }
+        int* out = I.Xc + (long long)I.core_start[c] * DP;
+        for (int q = b; q < e; ++q) {
+            if (!I.core_s[q]) continue;
             int x[DP];
+            if constexpr (DP == 4) {
+                const int4 v = *reinterpret_cast<const int4*>(I.Xs + (long long)q * 4);
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            } else {
 #pragma unroll
-            for (int j = 0; j < DP; ++j) x[j] = 0;
-            if (valid) {
-                cur.seek(f, i);
-                k = f.idx[cur.k];
-                const Inst& I = ins[k];
-                q = i - cur.lo;
-                core = I.core_s[q] != 0;
-                c = I.pt_cell[q];
-                if constexpr (DP == 4) {
-                    const int4 v = *reinterpret_cast<const int4*>(I.Xs + q * 4);
-                    x[0] = v.x;
-                    x[1] = v.y;
-                    x[2] = v.z;
-                    x[3] = v.w;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < DP; ++j) x[j] = I.Xs[q * DP + j];
-                }
+                for (int j = 0; j < DP; ++j) x[j] = I.Xs[(long long)q * DP + j];
             }
-            if (__all_sync(kFull, valid && c == acc_c && k == acc_k)) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    lo[j] = min(lo[j], x[j]);
-                    hi[j] = max(hi[j], x[j]);
-                }
-                continue;
-            }
-            if (acc_c >= 0) {
-                box_flush<D>(ins[acc_k].bbox + (long long)acc_c * 2 * D, lo, hi, lane);
-                acc_c = -1;
-                acc_k = -1;
-            }
-            bool full = false;
-            if (core) {
-                const Inst& I = ins[k];
-                const int b = I.cell_start[c];
-                // a full grid's core rows are its rows in Xs (core_rows)
-                full = I.cell_start[c + 1] - b >= I.p.minpts;
-                if (!full) {
-                    int rk = 0;
-                    for (long long t = b; t < q; ++t) rk += I.core_s[t];
-                    int* out = I.Xc + (long long)(I.core_start[c] + rk) * DP;
+            for (int j = 0; j < DP; ++j) out[j] = x[j];
+            out += DP;
 #pragma unroll
-                    for (int j = 0; j < DP; ++j) out[j] = x[j];
-                }
-            }
-            const int c0 = __shfl_sync(kFull, c, 0), k0 = __shfl_sync(kFull, k, 0);
-            const bool same = __all_sync(kFull, core && c == c0 && k == k0);
-            if (same && full) {  // (full is uniform when same) a run of a full grid starts
-                acc_c = c0;
-                acc_k = k0;
-#pragma unroll
-                for (int j = 0; j < D; ++j) lo[j] = hi[j] = x[j];
-            } else if (same) {
-                int lo1[D], hi1[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) lo1[j] = hi1[j] = x[j];
-                box_flush<D>(ins[k0].bbox + (long long)c0 * 2 * D, lo1, hi1, lane);
-            } else if (core) {
-                int* box = ins[k].bbox + (long long)c * 2 * D;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    atomicMin(box + j, x[j]);
-                    atomicMax(box + D + j, x[j]);
-                }
+            for (int j = 0; j < D; ++j) {
+                lo[j] = min(lo[j], x[j]);
+                hi[j] = max(hi[j], x[j]);
             }
         }
-        if (acc_c >= 0) box_flush<D>(ins[acc_k].bbox + (long long)acc_c * 2 * D, lo, hi, lane);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            box[j] = lo[j];
+            box[D + j] = hi[j];
+        }
     }
 }
 
-cudaError_t launch_core_pack(const Inst* ins, Flat pts, long long total, int d, cudaStream_t st) {
+cudaError_t launch_core_pack(const Inst* ins, Flat cells, long long total, int d, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    const int nb = blocks_for((total + kPackRounds - 1) / kPackRounds);
+    const int nb = blocks_for(total);
     switch (d) {
 #define GD_CP(DD) \
-    case DD: core_pack_kernel<DD><<<nb, 256, 0, st>>>(ins, pts, total); break;
+    case DD: core_pack_kernel<DD><<<nb, 256, 0, st>>>(ins, cells, total); break;
         GD_CP(1) GD_CP(2) GD_CP(3) GD_CP(4) GD_CP(5) GD_CP(6) GD_CP(7) GD_CP(8)
 #undef GD_CP
         default: return cudaErrorInvalidValue;

@@ -19,7 +19,7 @@
 // Nei(g) that still holds every grid with a point within eps of a point of g
 // (in sparse, high-dimensional data, where grids hold about one point, it is
 // an order of magnitude smaller).  Grids of more than kBoxPoints points use
-// their identifier range as their box (dense grids fill their range).
+// their identifier range as their box (such dense grids fill their range).
 //
 // The relation "boxes within eps" is symmetric, so each pair is found once:
 // the walk from grid c enumerates only the grids g' >= c (lexicographic
@@ -43,11 +43,14 @@ static int blocks_for(long long total) {
 }
 
 // Grids of more than kBoxPoints points keep their identifier range as their
-// box (it holds all their points; refining dense grids gains nothing).
-constexpr int kBoxPoints = 32;
+// box (it holds all their points).  Below that the exact box pays: the core
+// boxes of full grids are these boxes, and the border search and the merge
+// prune by them (a grid at a cluster's edge fills only part of its range).
+constexpr int kBoxPoints = 1024;
 
 // Box of every grid: one warp per grid; the lanes reduce the points of grids
-// of at most kBoxPoints points, larger grids take their identifier range.
+// of at most kBoxPoints points (d <= 4: eight 16-byte rows per lane in
+// flight), larger grids take their identifier range.
 __global__ void __launch_bounds__(256) point_box_kernel(const Inst* __restrict__ ins, Flat f, long long total) {
     total = flat_total(f);
     const int lane = lane_id();
@@ -73,7 +76,25 @@ __global__ void __launch_bounds__(256) point_box_kernel(const Inst* __restrict__
             lo[j] = 0x7fffffff;
             hi[j] = (int)0x80000000;
         }
-        for (int q = b + lane; q < e; q += 32) {
+        int q = b + lane;
+        if (dp == 4)  // eight rows per lane in flight (the dense, low-dimensional grids)
+            for (; q + 224 < e; q += 256) {
+                int4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = *reinterpret_cast<const int4*>(I.Xs + (long long)(q + 32 * u) * 4);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    lo[0] = min(lo[0], v[u].x);
+                    hi[0] = max(hi[0], v[u].x);
+                    lo[1] = min(lo[1], v[u].y);
+                    hi[1] = max(hi[1], v[u].y);
+                    lo[2] = min(lo[2], v[u].z);
+                    hi[2] = max(hi[2], v[u].z);
+                    lo[3] = min(lo[3], v[u].w);
+                    hi[3] = max(hi[3], v[u].w);
+                }
+            }
+        for (; q < e; q += 32) {
 #pragma unroll
             for (int j = 0; j < kMaxD; ++j)
                 if (j < d) {

@@ -885,7 +885,7 @@ gd_status Run::go() {
         RUN_CUDA(launch_core_count(dins, cells, total_cells, st), "core count");
         RUN_TRY(scan(coreseg, K, coreseg_tiles));
         for (int gi = 0; gi < ng; ++gi)
-            RUN_CUDA(launch_core_pack(dins, g_pts[gi], g_pts_tot[gi], dgroups[gi], st), "core pack");
+            RUN_CUDA(launch_core_pack(dins, g_cells[gi], g_cells_tot[gi], dgroups[gi], st), "core pack");
         mark(9);
         if (any_ldf) RUN_CUDA(launch_ldf_order(dins, idx, K, cells, total_cells, st), "low-density-first order");
         RUN_CUDA(launch_uf_init(dins, cells, total_cells, st), "union-find init");

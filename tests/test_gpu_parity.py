@@ -126,12 +126,12 @@ def refined_neighbours(X, eps2, gs):
     """The GPU's neighbour lists from the oracle's grid-level Nei(g): the grids
     of Nei(g) whose boxes are within eps of g's box, where a grid's box is the
     box of its points, or its whole identifier range when it holds more than
-    32 points (a symmetric relation)."""
+    1024 points (a symmetric relation)."""
     cs, ns, nei, order = gs["cell_start"], gs["nei_start"], gs["nei"], gs["order"]
     Xs = X[order].astype(np.int64)
     lo = np.minimum.reduceat(Xs, cs[:-1], axis=0)
     hi = np.maximum.reduceat(Xs, cs[:-1], axis=0)
-    big = np.diff(cs) > 32
+    big = np.diff(cs) > 1024
     if big.any():
         s = oracle.cell_side(eps2, X.shape[1])
         base = X.min(0).astype(np.int64) + gs["cell_coord"][big] * s
