@@ -320,6 +320,31 @@ def clustered(rng, n, d, hi, sigma, k=6):
     return np.ascontiguousarray(X.clip(0, hi - 1).astype(np.int32))
 
 
+@pytest.mark.parametrize("d,eps2,width", [
+    (4, 260400, 8),             # s = 256: four 8-bit offsets fill the 32-bit word
+    (2, 2 * 40000 ** 2, 16),    # s = 40001: two 16-bit offsets
+    (3, 3 * 1000 ** 2, 10),     # s = 1001: 30 bits
+    (3, 3 * 1500 ** 2, 11),     # s = 1501: 33 bits, past the word: the input rows are gathered
+])
+def test_grid_order_rows_from_in_cell_offsets(ctx, d, eps2, width):
+    """The compaction rebuilds each grid-order row from its identifiers and
+    the point's in-cell offsets (Eq. 1: x_j = mn_j + id_j * s + offset_j)
+    when the d offsets fit one 32-bit word, and gathers the input row
+    otherwise; the labels equal the oracle's either way, on coordinates far
+    below zero."""
+    s = oracle.cell_side(eps2, d)
+    assert (s - 1).bit_length() == width
+    rng = np.random.default_rng(100 + d + width)
+    X = np.vstack([clustered(rng, 24000, d, 60 * s, sigma=3 * s), rand_points(rng, 6000, d, 60 * s)])
+    X = np.ascontiguousarray((X.astype(np.int64) - (1 << 30) - 12345).astype(np.int32))
+    got = run_gpu(ctx, X, eps2, 20)
+    assert ctx.last_sizes()["key_class"] == 0
+    want = oracle.grid(X, eps2, 20)
+    assert_same(got, want, f"d={d} offset width {width}")
+    # clusters, border points and noise all present
+    assert len(np.unique(want[0][want[0] >= 0])) > 1 and (want[0] < 0).any() and (want[1] == 0).any()
+
+
 @pytest.mark.parametrize("key_class,n,d,hi,eps2,kind", [
     (0, 600_000, 3, 1 << 20, 5000 ** 2, "uniform"),    # packed keys, 147 sort tiles, most grids distinct
     (0, 600_000, 3, 1 << 20, 5000 ** 2, "clustered"),  # long runs of equal digits in every tile
