@@ -28,7 +28,6 @@ __global__ void core_count_kernel(const Inst* __restrict__ ins, Flat f, long lon
         const int k = cur.k;
         const Inst& I = ins[f.idx[k]];
         const long long c = i - cur.lo;
-        const int d = I.p.d;
         const int b = I.cell_start[c], e = I.cell_start[c + 1];
         int m = e - b;
         if (m < I.p.minpts) {

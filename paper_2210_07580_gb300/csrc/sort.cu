@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kOsBlock, PACKED ? 3 : 2)
         // Warp w owns items [w*32*kItems, (w+1)*32*kItems) of the tile in index
         // order; item i of lane l is at w*32*kItems + i*32 + l.
         K key[kItems];
-        int val[kItems];
+        [[maybe_unused]] int val[PACKED ? 1 : kItems];  // index values (unpacked keys only)
         int rk[kItems];  // rank within the warp (low 16 bits) | digit << 16
         const int wbase = warp * 32 * kItems;
 #pragma unroll
